@@ -1,0 +1,358 @@
+"""FP64 CPU oracle of GIFT's on-line query path (Bai et al., GIFT, CVPR 2016).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import or call this
+module; only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it. It shares no code with the CUDA library.
+
+Every float is widened to float64. Loops are plain; numpy matrix products serve
+as library steps. What each function computes, with the passage it follows:
+
+* ``cosine``               s(a, b), the cosine similarity used in Eq. 3 (Sec. 2.3)
+* ``quantize``             c(x) = argmin_k ||x - b_k||^2 (Sec. 2.3, after Eq. 4),
+                           with multiple assignment (Sec. 2.3, last paragraph)
+* ``build_fif``            the first inverted file (Sec. 2.3, Fig. 2)
+* ``exact_scores``         S(x_q, x_p), Eq. 3
+* ``fif_scores``           the approximate match of Eq. 4, literally (Kronecker delta)
+* ``fif_scores_lists``     Eq. 4 evaluated by walking the inverted file
+* ``rank``                 the ranked list, order (score desc, id asc)
+* ``membership``           the sparse activation F_q of Eq. 7
+* ``contextual``           S'(x_q, x_p) of Eq. 8
+* ``build_sif``/``sif_scores_inverted``  Eq. 13 / Eq. 14 over the second
+                           inverted file (Sec. 2.4.2, Fig. 3)
+* ``rerank``               the re-ranked list by (S' desc, S desc, id asc)
+* ``match_forward``/``match_backward``  Eq. 3 after a linear view projection
+                           u = W q, and its gradient through the argmax view
+
+Readings where the paper is silent (each also listed in the design notes):
+* the normaliser of Eq. 3/4 is the query's own view count |V(x_q)|;
+* Eq. 4 is taken literally: the max runs over all database views, so a view
+  whose code differs contributes a 0 candidate;
+* quantiser ties go to the lowest codeword index; multiple assignment returns
+  the m nearest codewords ordered by (distance, index); database views use one
+  assignment, queries ``ma``;
+* ranking ties go to the lower shape id; re-ranking orders by
+  (S' desc, S desc, id asc); S' = 0 when both F vectors are zero;
+* a database shape's neighbour set N_k1 includes the shape itself;
+* the squared distance is evaluated as ||x||^2 - 2 x.b + ||b||^2 in float64
+  (an algebraic identity; its rounding, about 1e-15 of ||x||^2 + ||b||^2,
+  is far below any margin at which codes are compared).
+
+Parity pins for every function are in tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# rows of the database processed per float64 chunk (bounds host memory)
+_CHUNK_ROWS = 8192
+
+
+def _f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def cosine(A, B):
+    """Matrix of s(a_i, b_j) = a_i . b_j / (||a_i|| ||b_j||); 0 when a norm is 0.
+
+    The similarity s of Eq. 3 is the cosine (Sec. 2.3, sentence after Eq. 3).
+    """
+    A = _f64(A)
+    B = _f64(B)
+    na = np.sqrt((A * A).sum(axis=1))
+    nb = np.sqrt((B * B).sum(axis=1))
+    G = A @ B.T
+    den = np.outer(na, nb)
+    out = np.zeros_like(G)
+    nz = den > 0
+    out[nz] = G[nz] / den[nz]
+    return out
+
+
+def sq_distances(X, Bk):
+    """||x_i - b_k||^2 for all pairs, float64 [n, K] (expanded form, see header)."""
+    X = _f64(X)
+    Bk = _f64(Bk)
+    xx = (X * X).sum(axis=1)
+    bb = (Bk * Bk).sum(axis=1)
+    return xx[:, None] - 2.0 * (X @ Bk.T) + bb[None, :]
+
+
+def quantize(X, codebook, ma=1):
+    """Codes int64 [n, ma]: the ma nearest codewords of each row, by (distance, index).
+
+    c(x) = argmin_{1<=i<=K} ||x - b_i||^2 (Sec. 2.3); multiple assignment keeps
+    several nearest codewords (Sec. 2.3, last paragraph).
+    """
+    X = _f64(X)
+    out = np.empty((X.shape[0], ma), np.int64)
+    for lo in range(0, X.shape[0], _CHUNK_ROWS):
+        d = sq_distances(X[lo:lo + _CHUNK_ROWS], codebook)
+        # a stable sort on distance puts equal distances in index order
+        out[lo:lo + _CHUNK_ROWS] = np.argsort(d, axis=1, kind="stable")[:, :ma]
+    return out
+
+
+def build_fif(db_codes, n_codewords):
+    """First inverted file (Fig. 2): list k holds every (shape, view) whose code is k.
+
+    ``db_codes`` is int [N, N_v] (one assignment per database view). Each list
+    is in ascending (shape, view) order. Returns a list of K int64 arrays of
+    shape [L_k, 2].
+    """
+    db_codes = np.asarray(db_codes)
+    N, Nv = db_codes.shape
+    lists = [[] for _ in range(n_codewords)]
+    for p in range(N):
+        for j in range(Nv):
+            lists[int(db_codes[p, j])].append((p, j))
+    return [np.asarray(l, np.int64).reshape(-1, 2) for l in lists]
+
+
+def _db_rows(X):
+    X = np.asarray(X)
+    N, Nv, D = X.shape
+    return X.reshape(N * Nv, D), N, Nv
+
+
+def exact_scores(Q, q_off, X):
+    """Eq. 3: S(x_q, x_p) = (1/|V(x_q)|) sum_i max_j s(q_i, p_j), float64 [B, N]."""
+    rows, N, Nv = _db_rows(X)
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    S = np.zeros((B, N))
+    for b in range(B):
+        Qb = _f64(Q[q_off[b]:q_off[b + 1]])
+        V = Qb.shape[0]
+        for lo in range(0, N, max(1, _CHUNK_ROWS // Nv)):
+            hi = min(N, lo + max(1, _CHUNK_ROWS // Nv))
+            s = cosine(Qb, rows[lo * Nv:hi * Nv]).reshape(V, hi - lo, Nv)
+            S[b, lo:hi] = s.max(axis=2).sum(axis=0) / V
+    return S
+
+
+def fif_scores(Q, q_off, q_codes, X, db_codes):
+    """Eq. 4 taken literally, float64 [B, N].
+
+    S(x_q, x_p) = (1/|V(x_q)|) sum_i max_j s(q_i, p_j) * delta(c(q_i), c(p_j)),
+    where delta is 1 when c(p_j) is one of q_i's assigned codewords (multiple
+    assignment, Sec. 2.3) and 0 otherwise. The max runs over all j, so an
+    unmatched view contributes the candidate value 0.
+    """
+    rows, N, Nv = _db_rows(X)
+    dbc = np.asarray(db_codes).reshape(N, Nv)
+    q_codes = np.asarray(q_codes)
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    S = np.zeros((B, N))
+    step = max(1, _CHUNK_ROWS // Nv)
+    for b in range(B):
+        Qb = _f64(Q[q_off[b]:q_off[b + 1]])
+        cb = q_codes[q_off[b]:q_off[b + 1]]
+        V = Qb.shape[0]
+        for lo in range(0, N, step):
+            hi = min(N, lo + step)
+            s = cosine(Qb, rows[lo * Nv:hi * Nv]).reshape(V, hi - lo, Nv)
+            # delta[i, p, j] = 1 iff c(p_j) is among q_i's codewords
+            delta = (dbc[None, lo:hi, :, None] == cb[:, None, None, :]).any(axis=3)
+            S[b, lo:hi] = (s * delta).max(axis=2).sum(axis=0) / V
+    return S
+
+
+def fif_scores_lists(Q, q_off, q_codes, X, lists):
+    """Eq. 4 evaluated through the first inverted file, float64 [B, N].
+
+    For each query view q_i, only the lists of its codewords are visited; per
+    shape the max over the visited entries is taken, and 0 joins that max when
+    some view of the shape was not visited (those products are 0 in Eq. 4).
+    Shapes never visited score 0 for q_i.
+    """
+    X = np.asarray(X)
+    N, Nv, D = X.shape
+    q_codes = np.asarray(q_codes)
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    S = np.zeros((B, N))
+    for b in range(B):
+        V = q_off[b + 1] - q_off[b]
+        for i in range(q_off[b], q_off[b + 1]):
+            best = {}
+            seen = {}
+            for c in q_codes[i]:
+                ent = lists[int(c)]
+                if len(ent) == 0:
+                    continue
+                s = cosine(Q[i:i + 1], X[ent[:, 0], ent[:, 1]])[0]
+                for (p, _j), v in zip(ent, s):
+                    p = int(p)
+                    best[p] = max(best.get(p, -np.inf), v)
+                    seen[p] = seen.get(p, 0) + 1
+            for p, v in best.items():
+                if seen[p] < Nv:
+                    v = max(v, 0.0)
+                S[b, p] += v / V
+    return S
+
+
+def rank(scores, k):
+    """Top-k of one score row: (ids int64 [k], scores [k]) ordered by (score desc, id asc)."""
+    s = _f64(scores)
+    order = np.lexsort((np.arange(s.shape[0]), -s))[:k]
+    return order, s[order]
+
+
+def membership(scores, k1):
+    """Sparse activation F_q of Eq. 7: F[i] = S(x_q, x_i) if x_i in N_k1(x_q) else 0.
+
+    N_k1 is the first k1 entries of the ranking of ``scores`` (float64 [N]).
+    """
+    ids, vals = rank(scores, k1)
+    F = np.zeros(np.asarray(scores).shape[0])
+    F[ids] = vals
+    return F
+
+
+def contextual(Fq, Fp):
+    """Eq. 8: S'(x_q, x_p) = sum_i min(F_q[i], F_p[i]) / sum_i max(F_q[i], F_p[i]).
+
+    Returns 0 when the denominator is 0 (both vectors zero).
+    """
+    Fq = _f64(Fq)
+    Fp = _f64(Fp)
+    den = np.maximum(Fq, Fp).sum()
+    if den == 0:
+        return 0.0
+    return float(np.minimum(Fq, Fp).sum() / den)
+
+
+def db_memberships(S_db, k1):
+    """Dense F_p for every database shape p (rows of float64 [N, N]).
+
+    ``S_db[p]`` is the score row of shape p used as a query (self included).
+    """
+    S_db = _f64(S_db)
+    return np.stack([membership(S_db[p], k1) for p in range(S_db.shape[0])])
+
+
+def build_sif(F_db):
+    """Second inverted file (Fig. 3): N entries; entry i stores ||F_i||_1 and the
+    pairs (p, F_p[i]) of every shape p whose activation at i is non-zero, p ascending.
+
+    Returns (card float64 [N], entries: list of (ids int64, values float64)).
+    """
+    F_db = _f64(F_db)
+    N = F_db.shape[0]
+    card = F_db.sum(axis=1)
+    entries = []
+    for i in range(N):
+        ps = np.nonzero(F_db[:, i])[0]
+        entries.append((ps.astype(np.int64), F_db[ps, i]))
+    return card, entries
+
+
+def sif_scores_inverted(Fq, card, entries):
+    """S'(x_q, .) over all N shapes through the second inverted file.
+
+    Numerator, Eq. 13: sum over i with F_q[i] != 0 and F_p[i] != 0 of
+    min(F_q[i], F_p[i]), gathered by walking entry i for each non-zero F_q[i].
+    Denominator, Eq. 14: ||F_q||_1 + ||F_p||_1 - numerator.
+    """
+    Fq = _f64(Fq)
+    N = Fq.shape[0]
+    num = np.zeros(N)
+    for i in np.nonzero(Fq)[0]:
+        ps, vals = entries[i]
+        for p, v in zip(ps, vals):
+            num[p] += min(Fq[i], v)
+    den = Fq.sum() + card - num
+    out = np.zeros(N)
+    nz = den > 0
+    out[nz] = num[nz] / den[nz]
+    return out
+
+
+def rerank(S_q, F_db, k1, k):
+    """Re-ranked top-k of each query, ordered by (S' desc, S desc, id asc).
+
+    S' (Eq. 8) is computed densely over all N shapes from F_q (Eq. 7, built from
+    the query's first k1 neighbours) and the database rows F_db.
+    Returns (ids int64 [B, k], S' float64 [B, k]).
+    """
+    S_q = np.atleast_2d(_f64(S_q))
+    B, N = S_q.shape
+    ids = np.zeros((B, k), np.int64)
+    sp = np.zeros((B, k))
+    for b in range(B):
+        Fq = membership(S_q[b], k1)
+        Sprime = np.array([contextual(Fq, F_db[p]) for p in range(N)])
+        order = np.lexsort((np.arange(N), -S_q[b], -Sprime))[:k]
+        ids[b] = order
+        sp[b] = Sprime[order]
+    return ids, sp
+
+
+def match_forward(Q, q_off, P, W=None):
+    """Eq. 3 after a linear view projection u = W q, v = W p.
+
+    Returns (S float64 [B, Np], jstar int64 [sum V_q, Np]) where jstar[i, p] is
+    the first j attaining max_j s(u_i, v_j) (lowest index on ties).
+    """
+    Q = _f64(Q)
+    P = _f64(P)
+    Np, nv, din = P.shape
+    Wm = np.eye(din) if W is None else _f64(W)
+    U = Q @ Wm.T
+    V = P.reshape(Np * nv, din) @ Wm.T
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    S = np.zeros((B, Np))
+    jstar = np.zeros((Q.shape[0], Np), np.int64)
+    for b in range(B):
+        lo, hi = q_off[b], q_off[b + 1]
+        s = cosine(U[lo:hi], V).reshape(hi - lo, Np, nv)
+        jstar[lo:hi] = s.argmax(axis=2)
+        S[b] = s.max(axis=2).sum(axis=0) / (hi - lo)
+    return S, jstar
+
+
+def match_backward(Q, q_off, P, W, G):
+    """Gradient of L = sum_{b,p} G[b,p] S(x_b, x_p) through ``match_forward``.
+
+    With u_i = W q_i, v_j = W p_j and s_ij = u_i.v_j / (|u_i||v_j|), the max of
+    Eq. 3 picks j* per (i, p), and
+      dS/du_i     = (v_j*/|v_j*| - s u_i/|u_i|) / |u_i|,
+      dS/dv_j*    = (u_i/|u_i|  - s v_j*/|v_j*|) / |v_j*|,
+    each scaled by G[b, p] / |V(x_b)|; then dW = sum dU q^T + sum dV p^T,
+    dQ = dU W, dP = dV W (W = identity when None).
+    Returns (dW or None, dQ [sum V_q, din], dP [Np, nv, din]).
+    """
+    Q = _f64(Q)
+    P = _f64(P)
+    G = _f64(G)
+    Np, nv, din = P.shape
+    Wm = np.eye(din) if W is None else _f64(W)
+    U = Q @ Wm.T
+    V = P.reshape(Np * nv, din) @ Wm.T
+    nu = np.linalg.norm(U, axis=1)
+    nvv = np.linalg.norm(V, axis=1)
+    dU = np.zeros_like(U)
+    dV = np.zeros_like(V)
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    for b in range(B):
+        lo, hi = q_off[b], q_off[b + 1]
+        Vb = hi - lo
+        for i in range(lo, hi):
+            ui = U[i] / nu[i]
+            for p in range(Np):
+                blk = V[p * nv:(p + 1) * nv]
+                s = blk @ ui / nvv[p * nv:(p + 1) * nv]
+                j = int(np.argmax(s))
+                r = p * nv + j
+                vj = V[r] / nvv[r]
+                c = G[b, p] / Vb
+                dU[i] += c * (vj - s[j] * ui) / nu[i]
+                dV[r] += c * (ui - s[j] * vj) / nvv[r]
+    dQ = dU @ Wm
+    dP = (dV @ Wm).reshape(Np, nv, din)
+    dW = None if W is None else dU.T @ Q + dV.T @ P.reshape(Np * nv, din)
+    return dW, dQ, dP

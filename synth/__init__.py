@@ -1,0 +1,15 @@
+"""Seeded synthetic inputs shaped like the paper's retrieval workloads.
+
+This package only draws numbers (view features, query view counts, a codebook
+fixture). It holds none of the matching method's arithmetic; the oracle tests
+and the CUDA path both take their inputs from here.
+"""
+from .workload import (  # noqa: F401
+    CONFIGS,
+    Config,
+    class_centres,
+    shape_views,
+    query_views,
+    kmeans_codebook,
+    make_config_inputs,
+)

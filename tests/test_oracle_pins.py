@@ -1,0 +1,374 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these re-types an oracle formula: each compares the oracle with an
+independent brute force (explicit Python loops), a closed form worked by hand,
+a special case where Eq. 4 must reduce to Eq. 3, an invariant, or finite
+differences. A dropped term, a wrong index, sign or normaliser in the oracle
+fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gift_oracle as O
+from synth import shape_views, query_views, kmeans_codebook
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ----------------------------------------------------------------- helpers
+def py_cos(a, b):
+    dot = sum(x * y for x, y in zip(a, b))
+    na = math.sqrt(sum(x * x for x in a))
+    nb = math.sqrt(sum(y * y for y in b))
+    return 0.0 if na == 0 or nb == 0 else dot / (na * nb)
+
+
+def py_exact(Q, q_off, X):
+    """Eq. 3 by explicit loops over i, p, j."""
+    N, Nv, _ = X.shape
+    out = []
+    for b in range(len(q_off) - 1):
+        rows = [list(map(float, Q[i])) for i in range(q_off[b], q_off[b + 1])]
+        out.append([sum(max(py_cos(q, list(map(float, X[p, j]))) for j in range(Nv)) for q in rows) / len(rows)
+                    for p in range(N)])
+    return np.array(out)
+
+
+def py_codes(X, Bk, ma):
+    """Nearest codewords by explicit squared differences, ties to the lower index."""
+    out = []
+    for x in X:
+        d = [(sum((float(a) - float(c)) ** 2 for a, c in zip(x, b)), k) for k, b in enumerate(Bk)]
+        d.sort()
+        out.append([k for _, k in d[:ma]])
+    return np.array(out)
+
+
+def py_fif(Q, q_off, qc, X, dbc):
+    """Eq. 4 by explicit loops: product with the Kronecker delta, max over all j."""
+    N, Nv, _ = X.shape
+    out = []
+    for b in range(len(q_off) - 1):
+        row = []
+        for p in range(N):
+            tot = 0.0
+            for i in range(q_off[b], q_off[b + 1]):
+                tot += max(py_cos(Q[i], X[p, j]) * (1.0 if dbc[p, j] in set(qc[i]) else 0.0)
+                           for j in range(Nv))
+            row.append(tot / (q_off[b + 1] - q_off[b]))
+        out.append(row)
+    return np.array(out)
+
+
+def rand_case(seed, N=5, Nv=4, D=6, B=3, signed=True, vq=(2, 3, 5)):
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((N, Nv, D))
+    counts = g.choice(vq, size=B)
+    q_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    Q = g.standard_normal((q_off[-1], D))
+    if not signed:
+        X, Q = np.abs(X), np.abs(Q)
+    return Q, q_off, X
+
+
+# ----------------------------------------------------------------- cosine
+def test_cosine_matches_explicit_loops_and_zero_norm():
+    g = np.random.default_rng(0)
+    A = g.standard_normal((4, 7))
+    Bm = g.standard_normal((5, 7))
+    A[2] = 0.0
+    got = O.cosine(A, Bm)
+    for i, j in itertools.product(range(4), range(5)):
+        assert got[i, j] == pytest.approx(py_cos(A[i], Bm[j]), abs=1e-14)
+    assert np.all(got[2] == 0.0)
+
+
+def test_cosine_scale_invariance_and_self():
+    g = np.random.default_rng(1)
+    A = g.standard_normal((3, 9))
+    assert np.allclose(np.diag(O.cosine(A, A)), 1.0, atol=1e-15)
+    assert np.allclose(O.cosine(3.5 * A, 0.25 * A), O.cosine(A, A), atol=1e-15)
+
+
+# ----------------------------------------------------------------- quantiser
+@pytest.mark.parametrize("ma", [1, 2, 3])
+def test_quantize_matches_brute_force(ma):
+    g = np.random.default_rng(2 + ma)
+    X = g.standard_normal((40, 3))
+    Bk = g.standard_normal((6, 3))
+    assert np.array_equal(O.quantize(X, Bk, ma), py_codes(X, Bk, ma))
+
+
+def test_quantize_ties_go_to_lowest_index():
+    Bk = np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 0.0], [0.0, -1.0]])
+    X = np.array([[1.0, 1.0], [2.0, 0.0], [0.0, 0.0]])
+    # (1,1): d = 1,1,1,5 -> 0,1,2 ; (2,0): d = 1,5,1,5 -> 0,2,1 ; (0,0): all 1
+    assert O.quantize(X, Bk, 1)[:, 0].tolist() == [0, 0, 0]
+    assert O.quantize(X, Bk, 3).tolist() == [[0, 1, 2], [0, 2, 1], [0, 1, 2]]
+
+
+# ----------------------------------------------------------------- hand-worked example
+def test_hand_example_eq3_eq4():
+    """Closed form worked by hand in 2-D.
+
+    q = {(1,0), (0,1)}, p = {(1,1), (2,0), (0,-3)}; codebook (1,0), (0,1), (0,-1).
+    Eq. 3: q1 -> max(1/sqrt2, 1, 0) = 1; q2 -> max(1/sqrt2, 0, -1) = 1/sqrt2;
+           S = (1 + 1/sqrt2) / 2.
+    Codes: q1 -> 0, q2 -> 1; p1 = (1,1) ties 0 and 1 -> 0; p2 -> 0; p3 -> 2.
+    Eq. 4, MA=1: q1 meets p1, p2 -> 1; q2 meets nothing -> 0; S = 1/2.
+    Eq. 4, MA=2: q1 -> {0, 1}, q2 -> {1, 0}; q2 meets p1, p2 -> 1/sqrt2;
+           S = (1 + 1/sqrt2) / 2, equal to Eq. 3.
+    """
+    Q = np.array([[1.0, 0.0], [0.0, 1.0]])
+    X = np.array([[[1.0, 1.0], [2.0, 0.0], [0.0, -3.0]]])
+    Bk = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, -1.0]])
+    off = np.array([0, 2])
+    r2 = 1.0 / math.sqrt(2.0)
+    assert O.exact_scores(Q, off, X)[0, 0] == pytest.approx((1 + r2) / 2, abs=1e-15)
+    dbc = O.quantize(X.reshape(-1, 2), Bk, 1).reshape(1, 3)
+    assert dbc.tolist() == [[0, 0, 2]]
+    q1 = O.quantize(Q, Bk, 1)
+    assert q1[:, 0].tolist() == [0, 1]
+    assert O.fif_scores(Q, off, q1, X, dbc)[0, 0] == pytest.approx(0.5, abs=1e-15)
+    q2 = O.quantize(Q, Bk, 2)
+    assert q2.tolist() == [[0, 1], [1, 0]]
+    assert O.fif_scores(Q, off, q2, X, dbc)[0, 0] == pytest.approx((1 + r2) / 2, abs=1e-15)
+    lists = O.build_fif(dbc, 3)
+    assert O.fif_scores_lists(Q, off, q1, X, lists)[0, 0] == pytest.approx(0.5, abs=1e-15)
+
+
+# ----------------------------------------------------------------- Eq. 3 / Eq. 4 brute force
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_exact_matches_brute_force(seed):
+    Q, off, X = rand_case(seed)
+    assert np.allclose(O.exact_scores(Q, off, X), py_exact(Q, off, X), atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("seed,K,ma", [(0, 3, 1), (1, 4, 2), (2, 5, 3), (3, 2, 1)])
+def test_fif_matches_brute_force_and_lists(seed, K, ma):
+    Q, off, X = rand_case(seed, N=6, Nv=5, D=4)
+    g = np.random.default_rng(100 + seed)
+    Bk = g.standard_normal((K, 4))
+    dbc = O.quantize(X.reshape(-1, 4), Bk, 1).reshape(6, 5)
+    qc = O.quantize(Q, Bk, ma)
+    lit = O.fif_scores(Q, off, qc, X, dbc)
+    assert np.allclose(lit, py_fif(Q, off, qc, X, dbc), atol=1e-13, rtol=0)
+    lists = O.build_fif(dbc, K)
+    assert np.allclose(O.fif_scores_lists(Q, off, qc, X, lists), lit, atol=1e-13, rtol=0)
+
+
+# ----------------------------------------------------------------- special cases of Eq. 4
+@pytest.mark.parametrize("signed", [True, False])
+def test_one_codeword_fif_equals_exact(signed):
+    """K = 1: every delta is 1, so Eq. 4 is Eq. 3."""
+    Q, off, X = rand_case(7, N=8, Nv=6, D=5, signed=signed)
+    Bk = np.ones((1, 5))
+    dbc = np.zeros((8, 6), np.int64)
+    qc = O.quantize(Q, Bk, 1)
+    ex = O.exact_scores(Q, off, X)
+    assert np.allclose(O.fif_scores(Q, off, qc, X, dbc), ex, atol=1e-14, rtol=0)
+    assert np.allclose(O.fif_scores_lists(Q, off, qc, X, O.build_fif(dbc, 1)), ex, atol=1e-13, rtol=0)
+
+
+def test_full_multiple_assignment_equals_exact():
+    """MA = K: every query view owns every codeword, so Eq. 4 is Eq. 3."""
+    Q, off, X = rand_case(8, N=7, Nv=5, D=4)
+    Bk = np.random.default_rng(9).standard_normal((4, 4))
+    dbc = O.quantize(X.reshape(-1, 4), Bk, 1).reshape(7, 5)
+    qc = O.quantize(Q, Bk, 4)
+    assert np.allclose(O.fif_scores(Q, off, qc, X, dbc), O.exact_scores(Q, off, X), atol=1e-14, rtol=0)
+
+
+def _small_mixture(n_shapes=30, nv=16, dim=24, classes=5, seed=11):
+    X = shape_views(0, n_shapes, nv, dim, classes, 1000 + seed, 4000 + seed)
+    Bk = kmeans_codebook(X.reshape(-1, dim), 12, 3000 + seed, 10)
+    return X, Bk
+
+
+def test_self_match_scores_one_and_ranks_first():
+    X, Bk = _small_mixture()
+    N, Nv, D = X.shape
+    dbc = O.quantize(X.reshape(-1, D), Bk, 1).reshape(N, Nv)
+    for p in (0, 7, 29):
+        Q = X[p]
+        off = np.array([0, Nv])
+        qc = O.quantize(Q, Bk, 1)
+        ex = O.exact_scores(Q, off, X)[0]
+        fi = O.fif_scores(Q, off, qc, X, dbc)[0]
+        assert ex[p] == pytest.approx(1.0, abs=1e-12)
+        assert fi[p] == pytest.approx(1.0, abs=1e-12)
+        assert O.rank(ex, 1)[0][0] == p and O.rank(fi, 1)[0][0] == p
+
+
+def test_score_bounds_non_negative_features():
+    """0 <= Eq.4 (MA=1) <= Eq.4 (MA=2) <= Eq.3 <= 1 for non-negative views."""
+    X, Bk = _small_mixture(seed=12)
+    N, Nv, D = X.shape
+    Q, off, _ = query_views(4, (5, 9, 16), D, 5, 2012, 4012, max_views=16)
+    dbc = O.quantize(X.reshape(-1, D), Bk, 1).reshape(N, Nv)
+    f1 = O.fif_scores(Q, off, O.quantize(Q, Bk, 1), X, dbc)
+    f2 = O.fif_scores(Q, off, O.quantize(Q, Bk, 2), X, dbc)
+    ex = O.exact_scores(Q, off, X)
+    eps = 1e-14
+    assert np.all(f1 >= -eps) and np.all(f1 <= f2 + eps)
+    assert np.all(f2 <= ex + eps) and np.all(ex <= 1 + eps)
+    assert np.any(f1 < f2 - 1e-6)  # the pin is not vacuous
+
+
+def test_posting_lists_partition_the_views():
+    X, Bk = _small_mixture(seed=13)
+    N, Nv, D = X.shape
+    dbc = O.quantize(X.reshape(-1, D), Bk, 1).reshape(N, Nv)
+    lists = O.build_fif(dbc, Bk.shape[0])
+    allent = np.concatenate([l for l in lists if len(l)])
+    assert len(allent) == N * Nv
+    assert len({(int(p), int(j)) for p, j in allent}) == N * Nv
+    for k, l in enumerate(lists):
+        assert all(dbc[p, j] == k for p, j in l)
+        keys = [int(p) * Nv + int(j) for p, j in l]
+        assert keys == sorted(keys)
+
+
+# ----------------------------------------------------------------- ranking
+def test_rank_matches_sorted_with_ties():
+    s = np.array([0.3, 0.9, 0.3, 0.1, 0.9, 0.0, 0.3])
+    ids, vals = O.rank(s, 5)
+    ref = sorted(range(len(s)), key=lambda i: (-s[i], i))[:5]
+    assert ids.tolist() == ref == [1, 4, 0, 2, 6]
+    assert vals.tolist() == [s[i] for i in ref]
+
+
+# ----------------------------------------------------------------- S-IF (Eqs. 5-8, 12-14)
+def test_membership_vector_eq7():
+    s = np.array([0.2, 0.8, 0.5, 0.8, 0.1])
+    F = O.membership(s, 3)
+    assert F.tolist() == [0.0, 0.8, 0.5, 0.8, 0.0]
+
+
+def test_contextual_reduces_to_crisp_jaccard():
+    """With all memberships 1, Eq. 8 is the set Jaccard index of Eq. 5."""
+    g = np.random.default_rng(3)
+    for _ in range(20):
+        a = set(g.choice(30, 8, replace=False).tolist())
+        b = set(g.choice(30, 8, replace=False).tolist())
+        Fa = np.zeros(30)
+        Fb = np.zeros(30)
+        Fa[list(a)] = 1.0
+        Fb[list(b)] = 1.0
+        assert O.contextual(Fa, Fb) == pytest.approx(len(a & b) / len(a | b), abs=1e-15)
+
+
+def test_contextual_properties():
+    g = np.random.default_rng(4)
+    for _ in range(20):
+        Fa = np.where(g.random(25) < 0.3, g.random(25), 0.0)
+        Fb = np.where(g.random(25) < 0.3, g.random(25), 0.0)
+        v = O.contextual(Fa, Fb)
+        assert 0.0 <= v <= 1.0
+        assert v == pytest.approx(O.contextual(Fb, Fa), abs=1e-15)
+        if Fa.any():
+            assert O.contextual(Fa, Fa) == pytest.approx(1.0, abs=1e-15)
+        # explicit loops of Eq. 6 over the union / intersection of supports
+        inter = [i for i in range(25) if Fa[i] > 0 and Fb[i] > 0]
+        union = [i for i in range(25) if Fa[i] > 0 or Fb[i] > 0]
+        ref = (sum(min(Fa[i], Fb[i]) for i in inter) / sum(max(Fa[i], Fb[i]) for i in union)) if union else 0.0
+        assert v == pytest.approx(ref, abs=1e-14)
+    assert O.contextual(np.zeros(4), np.zeros(4)) == 0.0
+
+
+def test_inverted_file_route_equals_dense_eq8():
+    X, Bk = _small_mixture(n_shapes=40, seed=14)
+    N, Nv, D = X.shape
+    dbc = O.quantize(X.reshape(-1, D), Bk, 1).reshape(N, Nv)
+    S_db = O.fif_scores(X.reshape(-1, D), np.arange(0, N * Nv + 1, Nv), O.quantize(X.reshape(-1, D), Bk, 1), X, dbc)
+    F_db = O.db_memberships(S_db, 6)
+    # self is in every database neighbour set
+    assert all(F_db[p, p] > 0 for p in range(N))
+    card, entries = O.build_sif(F_db)
+    assert sum(len(e[0]) for e in entries) == N * 6
+    Q, off, _ = query_views(5, (16,), D, 5, 2014, 4014, max_views=16)
+    S_q = O.fif_scores(Q, off, O.quantize(Q, Bk, 1), X, dbc)
+    for b in range(5):
+        Fq = O.membership(S_q[b], 6)
+        dense = np.array([O.contextual(Fq, F_db[p]) for p in range(N)])
+        inv = O.sif_scores_inverted(Fq, card, entries)
+        assert np.allclose(inv, dense, atol=1e-14, rtol=0)
+
+
+def test_rerank_order_brute_force():
+    g = np.random.default_rng(5)
+    N = 12
+    S_db = g.random((N, N))
+    np.fill_diagonal(S_db, 1.0)
+    F_db = O.db_memberships(S_db, 4)
+    S_q = g.random((2, N))
+    ids, sp = O.rerank(S_q, F_db, 4, 6)
+    for b in range(2):
+        Fq = O.membership(S_q[b], 4)
+        spv = [O.contextual(Fq, F_db[p]) for p in range(N)]
+        ref = sorted(range(N), key=lambda p: (-spv[p], -S_q[b, p], p))[:6]
+        assert ids[b].tolist() == ref
+
+
+# ----------------------------------------------------------------- differentiation
+def _tie_free(seed, B=2, Np=4, nv=8, din=16, dout=6, margin=1e-3):
+    g = np.random.default_rng(seed)
+    while True:
+        Q = g.standard_normal((B * nv, din))
+        P = g.standard_normal((Np, nv, din))
+        W = g.standard_normal((dout, din)) / 4
+        U = Q @ W.T
+        V = P.reshape(-1, din) @ W.T
+        s = O.cosine(U, V).reshape(B * nv, Np, nv)
+        top2 = np.sort(s, axis=2)[:, :, -2:]
+        if np.min(top2[:, :, 1] - top2[:, :, 0]) > margin:
+            return Q, np.arange(0, B * nv + 1, nv), P, W, g.standard_normal((B, Np))
+
+
+def test_backward_matches_central_differences():
+    Q, off, P, W, G = _tie_free(21)
+    dW, dQ, dP = O.match_backward(Q, off, P, W, G)
+    h = 1e-6
+
+    def L(Q_, P_, W_):
+        return float((O.match_forward(Q_, off, P_, W_)[0] * G).sum())
+
+    g = np.random.default_rng(0)
+    for _ in range(12):
+        i, d = g.integers(Q.shape[0]), g.integers(Q.shape[1])
+        Qp, Qm = Q.copy(), Q.copy()
+        Qp[i, d] += h
+        Qm[i, d] -= h
+        assert dQ[i, d] == pytest.approx((L(Qp, P, W) - L(Qm, P, W)) / (2 * h), abs=2e-7)
+        p, j, d = g.integers(P.shape[0]), g.integers(P.shape[1]), g.integers(P.shape[2])
+        Pp, Pm = P.copy(), P.copy()
+        Pp[p, j, d] += h
+        Pm[p, j, d] -= h
+        assert dP[p, j, d] == pytest.approx((L(Q, Pp, W) - L(Q, Pm, W)) / (2 * h), abs=2e-7)
+        r, c = g.integers(W.shape[0]), g.integers(W.shape[1])
+        Wp, Wm = W.copy(), W.copy()
+        Wp[r, c] += h
+        Wm[r, c] -= h
+        assert dW[r, c] == pytest.approx((L(Q, P, Wp) - L(Q, P, Wm)) / (2 * h), abs=2e-7)
+
+
+def test_backward_scale_invariants():
+    """Cosine is scale-invariant: <q_i, dS/dq_i> = 0, <p_j, dS/dp_j> = 0, <W, dS/dW> = 0."""
+    Q, off, P, W, G = _tie_free(22)
+    dW, dQ, dP = O.match_backward(Q, off, P, W, G)
+    assert np.allclose((Q * dQ).sum(1), 0.0, atol=1e-12)
+    assert np.allclose((P * dP).sum(2), 0.0, atol=1e-12)
+    assert abs((W * dW).sum()) < 1e-12
+    assert np.abs(dQ).max() > 1e-3  # not vacuous
+
+
+def test_backward_identity_projection():
+    Q, off, P, W, G = _tie_free(23, dout=16)
+    _, dQ0, dP0 = O.match_backward(Q, off, P, None, G)
+    _, dQ1, dP1 = O.match_backward(Q, off, P, np.eye(16), G)
+    assert np.allclose(dQ0, dQ1, atol=1e-14) and np.allclose(dP0, dP1, atol=1e-14)
+    S0, j0 = O.match_forward(Q, off, P, None)
+    assert np.allclose(S0, O.exact_scores(Q, off, P), atol=1e-14)
