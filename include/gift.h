@@ -1,0 +1,259 @@
+/*
+ * gift.h -- C ABI of the GB300 (sm_103a) implementation of GIFT's on-line
+ * query path: multi-view matching through the first inverted file (F-IF),
+ * top-k selection, and re-ranking through the second inverted file (S-IF)
+ * (Bai et al., "GIFT: A Real-time and Scalable 3D Shape Search Engine",
+ * CVPR 2016), with the exact set-to-set match as the plain path.
+ *
+ * Conventions shared by every call:
+ *  - A shape x has a set of view features V(x) = {x_1..x_{N_v}}, each a row of
+ *    D floats (Sec. 2.3). Feature matrices are row-major, one view per row,
+ *    views of a shape consecutive, shapes in id order.
+ *  - The caller owns every buffer it passes; the library owns the memory of an
+ *    index and of its per-call scratch. No call keeps a caller pointer after
+ *    the work it enqueued has run.
+ *  - Work is enqueued on `stream` (0 = legacy default stream). Unless stated
+ *    otherwise a call returns once its work is enqueued; results are valid
+ *    after the stream is synchronised. Pointers documented as "device or host"
+ *    may be either: host memory is staged through the library (pinned host
+ *    memory keeps the copies asynchronous).
+ *  - Every call returns a gift_status. No exception or abort crosses the ABI.
+ *    gift_last_error() gives a message for the last failing call of the
+ *    calling thread. GIFT_ECUDA leaves the index usable unless the CUDA
+ *    context itself was lost.
+ *  - A built index is read-only: calls on one index from several host threads
+ *    or streams may run concurrently; each call has its own scratch.
+ *  - D must be a positive multiple of 16 (16-byte rows for every storage type).
+ */
+#ifndef GIFT_H
+#define GIFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define GIFT_API __attribute__((visibility("default")))
+#else
+#define GIFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GIFT_OK = 0,
+  GIFT_EINVAL = 1,       /* an argument is out of range or inconsistent       */
+  GIFT_ENOMEM = 2,       /* device or pinned host memory could not be reserved */
+  GIFT_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed        */
+  GIFT_ETIMEOUT = 4,     /* a bounded wait ran out (serving loop)             */
+  GIFT_EUNSUPPORTED = 5, /* the index was built without what the call needs   */
+  GIFT_ESTATE = 6        /* the object is in the wrong state for this call    */
+} gift_status;
+
+/* Storage type of the F-IF feature store. */
+typedef enum { GIFT_F32 = 0, GIFT_BF16 = 1, GIFT_FP8_E4M3 = 2 } gift_dtype;
+
+/* Matching mode of gift_query. */
+typedef enum {
+  GIFT_MATCH_EXACT = 0, /* Eq. 3 over all view pairs                           */
+  GIFT_MATCH_FIF = 1    /* Eq. 4 through the first inverted file               */
+} gift_mode;
+
+/* Maximum query-side multiple assignment. */
+#define GIFT_MAX_MA 8
+
+typedef struct {
+  int32_t n_shapes;        /* N: database shapes                                 */
+  int32_t views_per_shape; /* N_v: views of every database shape                 */
+  int32_t dim;             /* D: feature dimension, multiple of 16               */
+  int32_t n_codewords;     /* K: size of the vocabulary B (Sec. 2.3)             */
+  int32_t storage;         /* gift_dtype of the list-ordered feature store       */
+  int32_t query_ma;        /* query views go to this many codewords, 1..8        */
+  int32_t sif_k1;          /* k1: neighbour-set size of the S-IF (Sec. 2.4); 0 = no S-IF */
+  int32_t rescore_r;       /* FP32 rescore of the top-R F-IF candidates; 0 = off */
+  int32_t keep_exact;      /* 1 = keep the FP32 feature master (exact match, rescore) */
+} gift_index_params;
+
+typedef struct gift_index gift_index; /* opaque; owns all its device memory */
+
+/* Sizes of a built index (gift_index_info). */
+typedef struct {
+  size_t device_bytes;      /* device memory held by the index            */
+  int64_t n_rows;           /* N * N_v database views                      */
+  int32_t n_lists_nonempty; /* non-empty F-IF lists                        */
+  int32_t max_list_len;     /* longest F-IF list                           */
+  int64_t n_runs;           /* runs of equal shape id over all lists       */
+  int32_t max_runs;         /* most runs in one list                       */
+  int32_t max_sif_entry;    /* longest S-IF entry                          */
+} gift_index_info_t;
+
+/* Per-stage device times of the last timed gift_query / gift_rerank call
+ * (milliseconds, CUDA events on the call's stream), see gift_set_timing. */
+typedef struct {
+  float assign_ms;   /* quantiser of the query views                        */
+  float bucket_ms;   /* grouping of query views by codeword                 */
+  float scan_ms;     /* posting-list scan (or the exact all-pairs kernel)   */
+  float combine_ms;  /* per-view max over assignments, sum into S           */
+  float topk_ms;     /* top-R / top-k selections                            */
+  float rescore_ms;  /* FP32 rescore of the candidates                      */
+  float rerank_ms;   /* S-IF re-rank (gift_rerank)                          */
+  float total_ms;    /* whole call                                          */
+  int64_t scan_bytes;   /* algorithmic bytes of the scan: touched list rows
+                           + their scales and ids + query rows              */
+  int64_t rescore_bytes;/* algorithmic bytes of the rescore                  */
+  int64_t scan_pairs;   /* (query view, list entry) pairs scanned           */
+} gift_timing_t;
+
+/*
+ * Build an index (off-line stage, Sec. 3.4 "building two inverted files").
+ *  - db_feats: device or host, float [N * N_v * D], database views.
+ *  - codebook: device or host, float [K * D], the vocabulary B (Sec. 2.3);
+ *    trained by the caller (the paper uses k-means).
+ * Steps: quantise every database view to its nearest codeword c(x) (one
+ * assignment); F-IF (Fig. 2): per codeword, the (shape id, view feature) of
+ * every view assigned to it, in ascending (shape, view) order, features
+ * converted to `storage`; S-IF (Fig. 3), when sif_k1 > 0: every database shape
+ * is matched as a query (F-IF, FP32 rescore when rescore_r > 0), its first k1
+ * neighbours (itself included) give F_p (Eq. 7), and entry i stores ||F_i||_1
+ * and the pairs (p, F_p[i]) with F_p[i] != 0, p ascending. Memberships are
+ * stored as uint32 fixed point round(S * 2^31).
+ * Synchronises `stream`; returns after the build is complete.
+ * Errors: EINVAL (sizes, D % 16, query_ma, storage), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_build_index(const gift_index_params* params, const float* db_feats,
+                             const float* codebook, cudaStream_t stream, gift_index** out);
+
+/* Release the index and all its device memory (synchronises the device). */
+GIFT_API void gift_destroy_index(gift_index* index);
+
+/*
+ * Query a batch of B shapes and return each query's top-k database shapes.
+ *  - q_feats: device or host, float [sum V_q * D], views of all queries.
+ *  - q_view_offsets: HOST int32 [B + 1]; query b owns views
+ *    [q_view_offsets[b], q_view_offsets[b+1]); V_q >= 1. (Host side because
+ *    the launch is sized from it; no device-to-host read is needed.)
+ *  - mode GIFT_MATCH_EXACT: S(x_q, x_p) of Eq. 3 with the cosine similarity,
+ *    (1/|V(x_q)|) sum_i max_j s(q_i, p_j), over all N shapes (needs keep_exact).
+ *    mode GIFT_MATCH_FIF: Eq. 4: each query view is quantised to its query_ma
+ *    nearest codewords, only the F-IF lists of those codewords are scanned,
+ *    and a shape's view contributes only when its codeword is one of them;
+ *    the per-(query view, shape) maximum is floored at 0 (the value Eq. 4
+ *    gives a shape that has any non-matching view). With rescore_r > 0 the
+ *    top rescore_r shapes are rescored with FP32 features (same Eq. 4).
+ *  - out_ids: device or host int32 [B * topk]; out_scores: device or host
+ *    float [B * topk]; each row ordered by (score desc, shape id asc). When
+ *    N < topk the tail holds id -1 and score -INFINITY.
+ * Errors: EINVAL, EUNSUPPORTED (EXACT without keep_exact; topk > rescore_r
+ * when rescoring; topk > 1024), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q_view_offsets,
+                       int32_t B, int32_t mode, int32_t topk, int32_t* out_ids, float* out_scores,
+                       cudaStream_t stream);
+
+/*
+ * S-IF re-ranking (Sec. 2.4, Eqs. 7, 8, 13, 14).
+ *  - cand_ids / cand_scores: device or host [B * n_cand], each row a query's
+ *    ranked list from gift_query (score desc, id asc), n_cand >= k1.
+ *  - The first k1 entries give F_q (Eq. 7). The numerator of Eq. 8 is taken
+ *    over the co-non-zero entries only (Eq. 13) by walking S-IF entry i for
+ *    each non-zero F_q[i]; the denominator is ||F_q||_1 + ||F_p||_1 minus the
+ *    numerator (Eq. 14). Sums are exact in integer fixed point; S' is divided
+ *    in FP32.
+ *  - Output rows are ordered by (S' desc, S desc, id asc) over all N shapes,
+ *    with S taken from the candidate list (shapes outside it rank after those
+ *    inside at equal S').
+ *  - out_ids: int32 [B * topk]; out_sprime: float [B * topk] (device or host).
+ * Errors: EINVAL, EUNSUPPORTED (index built with sif_k1 == 0 or
+ * k1 != sif_k1 is allowed but k1 must be <= n_cand), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, const float* cand_scores,
+                        int32_t B, int32_t n_cand, int32_t k1, int32_t topk, int32_t* out_ids,
+                        float* out_sprime, cudaStream_t stream);
+
+/*
+ * The quantiser alone (Sec. 2.3): out_codes[v * ma + a] is the a-th nearest
+ * codeword of row v by (squared distance, index), c(x) = argmin_k ||x - b_k||^2.
+ *  - feats: device float [n * D]; out_codes: device int32 [n * ma]; 1 <= ma <= 8.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_assign(gift_index* index, const float* feats, int64_t n, int32_t ma,
+                        int32_t* out_codes, cudaStream_t stream);
+
+/*
+ * Copy the F-IF of a built index to caller buffers (device or host):
+ * db_codes int32 [N * N_v] (codeword of each database view), list_offsets
+ * int64 [K + 1], list_rows int32 [N * N_v] (row = shape * N_v + view, list
+ * order). Any pointer may be NULL to skip it. Synchronises `stream`.
+ */
+GIFT_API gift_status gift_export_fif(const gift_index* index, int32_t* db_codes, int64_t* list_offsets,
+                            int32_t* list_rows, cudaStream_t stream);
+
+/*
+ * Copy the S-IF of a built index (device or host): entry_offsets int64 [N + 1],
+ * entry_ids int32 [N * k1] (shape p of each pair), entry_members uint32
+ * [N * k1] (F_p[i] in fixed point 2^31), card uint64 [N] (||F_i||_1 in the same
+ * fixed point). Any pointer may be NULL. Synchronises `stream`.
+ * Errors: EUNSUPPORTED when the index has no S-IF.
+ */
+GIFT_API gift_status gift_export_sif(const gift_index* index, int64_t* entry_offsets, int32_t* entry_ids,
+                            uint32_t* entry_members, uint64_t* card, cudaStream_t stream);
+
+/* Sizes of a built index. */
+GIFT_API gift_status gift_index_info(const gift_index* index, gift_index_info_t* out);
+
+/*
+ * Per-stage timing of gift_query / gift_rerank calls on this index: when
+ * enabled, each call records CUDA events around its stages on its stream;
+ * gift_get_timing synchronises on the last call's final event and returns the
+ * stage times. Timing is off by default.
+ */
+GIFT_API gift_status gift_set_timing(gift_index* index, int32_t enable);
+GIFT_API gift_status gift_get_timing(gift_index* index, gift_timing_t* out);
+
+/*
+ * Set-to-set matching score of Eq. 3 after a linear view projection
+ * u = W q (W may be NULL for the identity), for training the projection:
+ *   S[b, p] = (1/|V(x_b)|) sum_i max_j s(W q_i, W p_j).
+ *  - q: device float [sum V_q * d_in]; q_view_offsets: HOST int32 [Bq + 1].
+ *  - p: device float [Np * nv_p * d_in]; W: device float [d_out * d_in] or NULL
+ *    (then d_out must equal d_in).
+ *  - S: device float [Bq * Np]; argmax: device int16 [sum V_q * Np], the first
+ *    j attaining the max for every (query view, database shape), saved for the
+ *    backward pass; nv_p <= 32767.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_match_forward(const float* q, const int32_t* q_view_offsets, int32_t Bq,
+                               const float* p, int32_t Np, int32_t nv_p, const float* W,
+                               int32_t d_in, int32_t d_out, float* S, int16_t* argmax,
+                               cudaStream_t stream);
+
+/*
+ * Gradient of L = sum_{b,p} grad_S[b,p] * S[b,p] through gift_match_forward,
+ * taken through the saved argmax view pair (the max of Eq. 3 is piecewise
+ * linear in the selected pair):
+ *   dS/du_i = (v_j/|v_j| - s u_i/|u_i|) / |u_i|, dS/dv_j = (u_i/|u_i| - s v_j/|v_j|) / |v_j|,
+ * each scaled by grad_S[b,p] / |V(x_b)|; dW = dU^T Q + dV^T P, dQ = dU W, dP = dV W.
+ *  - grad_S: device float [Bq * Np]; argmax from the forward call.
+ *  - dW: device float [d_out * d_in] or NULL (skipped; must be NULL when W is);
+ *    dQ: device float [sum V_q * d_in] or NULL; dP: device float
+ *    [Np * nv_p * d_in] or NULL. Outputs are overwritten.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, int32_t Bq,
+                                const float* p, int32_t Np, int32_t nv_p, const float* W,
+                                int32_t d_in, int32_t d_out, const float* grad_S,
+                                const int16_t* argmax, float* dW, float* dQ, float* dP,
+                                cudaStream_t stream);
+
+/* Message of the last failing call on the calling thread ("" if none). */
+GIFT_API const char* gift_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+GIFT_API int32_t gift_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIFT_H */

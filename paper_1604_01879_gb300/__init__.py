@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) implementation of GIFT's on-line query path.
+
+A thin binding over the C ABI of ``libgift.so`` (declared in include/gift.h):
+argument marshalling only. Every step of the path runs in the library's CUDA
+kernels; PyTorch supplies device memory and the current stream. There is no
+CPU fallback: without the built library every call raises.
+
+    import paper_1604_01879_gb300 as gift
+    ix = gift.Index(db, codebook, n_shapes=N, views_per_shape=64, n_codewords=K,
+                    storage="bf16", rescore_r=200, sif_k1=50)
+    ids, scores = ix.query(q, q_offsets, topk=100)            # Eq. 4 (F-IF)
+    ids2, sprime = ix.rerank(ids, scores, k1=50, topk=100)     # S-IF (Eqs. 7-14)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "GiftError", "load", "lib_path", "Index", "match_forward", "match_backward", "GiftMatch",
+    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF",
+]
+
+F32, BF16, FP8_E4M3 = 0, 1, 2
+MATCH_EXACT, MATCH_FIF = 0, 1
+_STORAGE = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8_E4M3, "fp8_e4m3": FP8_E4M3}
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED", 6: "ESTATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+class GiftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", "libgift.so")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_shapes", "views_per_shape", "dim", "n_codewords", "storage", "query_ma", "sif_k1",
+        "rescore_r", "keep_exact")]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("n_rows", ctypes.c_int64),
+                ("n_lists_nonempty", ctypes.c_int32), ("max_list_len", ctypes.c_int32),
+                ("n_runs", ctypes.c_int64), ("max_runs", ctypes.c_int32),
+                ("max_sif_entry", ctypes.c_int32)]
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in (
+        "assign_ms", "bucket_ms", "scan_ms", "combine_ms", "topk_ms", "rescore_ms", "rerank_ms",
+        "total_ms")] + [("scan_bytes", ctypes.c_int64), ("rescore_bytes", ctypes.c_int64),
+                        ("scan_pairs", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I32, _I64 = ctypes.c_int32, ctypes.c_int64
+_SIGS = {
+    "gift_build_index": (_I32, [ctypes.POINTER(_Params), _P, _P, _P, ctypes.POINTER(_P)]),
+    "gift_destroy_index": (None, [_P]),
+    "gift_query": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
+    "gift_export_fif": (_I32, [_P, _P, _P, _P, _P]),
+    "gift_export_sif": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "gift_index_info": (_I32, [_P, ctypes.POINTER(_Info)]),
+    "gift_set_timing": (_I32, [_P, _I32]),
+    "gift_get_timing": (_I32, [_P, ctypes.POINTER(_Timing)]),
+    "gift_match_forward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "gift_match_backward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P, _P,
+                                   _P]),
+    "gift_last_error": (ctypes.c_char_p, []),
+    "gift_version": (_I32, []),
+}
+SYMBOLS = tuple(_SIGS)
+
+
+def load(path: str | None = None):
+    """Load libgift.so (built in-tree by ``build.build()``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgift.so not built ({path}); run paper_1604_01879_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise GiftError(status, _lib.gift_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor (device or host) or a numpy array (host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if not x.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _host_offsets(q_off):
+    a = np.ascontiguousarray(np.asarray(
+        q_off.cpu().numpy() if hasattr(q_off, "cpu") else q_off, dtype=np.int32))
+    return a
+
+
+class Index:
+    """A built GIFT index resident on the current CUDA device."""
+
+    def __init__(self, db_feats, codebook, n_shapes: int, views_per_shape: int, n_codewords: int,
+                 storage="f32", query_ma: int = 1, sif_k1: int = 0, rescore_r: int = 0,
+                 keep_exact: bool = True, stream=None):
+        lib = load()
+        dim = int(codebook.shape[-1])
+        self.params = _Params(int(n_shapes), int(views_per_shape), dim, int(n_codewords),
+                              _STORAGE[storage] if isinstance(storage, str) else int(storage),
+                              int(query_ma), int(sif_k1), int(rescore_r), int(bool(keep_exact)))
+        self._h = ctypes.c_void_p()
+        _check(lib.gift_build_index(ctypes.byref(self.params), _ptr(db_feats), _ptr(codebook),
+                                    _stream(stream), ctypes.byref(self._h)))
+        self.n_shapes, self.views_per_shape, self.dim = int(n_shapes), int(views_per_shape), dim
+        self.n_codewords, self.query_ma, self.sif_k1 = int(n_codewords), int(query_ma), int(sif_k1)
+        self.rescore_r = int(rescore_r)
+
+    # -- queries -----------------------------------------------------------
+    def query(self, q_feats, q_offsets, mode="fif", topk: int = 10, out=None, stream=None):
+        """Top-k (ids int32, scores float32) [B, topk] of each query (Eq. 4 or Eq. 3)."""
+        import torch
+        offs = _host_offsets(q_offsets)
+        B = len(offs) - 1
+        m = MATCH_FIF if mode in ("fif", MATCH_FIF) else MATCH_EXACT
+        if out is None:
+            dev = q_feats.device if hasattr(q_feats, "device") and q_feats.is_cuda else torch.device("cuda")
+            out = (torch.empty((B, topk), dtype=torch.int32, device=dev),
+                   torch.empty((B, topk), dtype=torch.float32, device=dev))
+        _check(load().gift_query(self._h, _ptr(q_feats), ctypes.c_void_p(offs.ctypes.data), B, m, int(topk),
+                                 _ptr(out[0]), _ptr(out[1]), _stream(stream)))
+        return out
+
+    def rerank(self, cand_ids, cand_scores, k1: int | None = None, topk: int = 10, out=None, stream=None):
+        """S-IF re-ranking of candidate rows: (ids int32, S' float32) [B, topk]."""
+        import torch
+        B, n_cand = cand_ids.shape
+        k1 = self.sif_k1 if k1 is None else int(k1)
+        if out is None:
+            dev = cand_ids.device if hasattr(cand_ids, "is_cuda") and cand_ids.is_cuda else torch.device("cuda")
+            out = (torch.empty((B, topk), dtype=torch.int32, device=dev),
+                   torch.empty((B, topk), dtype=torch.float32, device=dev))
+        _check(load().gift_rerank(self._h, _ptr(cand_ids), _ptr(cand_scores), int(B), int(n_cand), k1, int(topk),
+                                  _ptr(out[0]), _ptr(out[1]), _stream(stream)))
+        return out
+
+    def assign(self, feats, ma: int = 1, stream=None):
+        """Codewords [n, ma] (int32) of device rows ``feats`` (the quantiser)."""
+        import torch
+        n = feats.shape[0]
+        out = torch.empty((n, ma), dtype=torch.int32, device=feats.device)
+        _check(load().gift_assign(self._h, _ptr(feats), int(n), int(ma), _ptr(out), _stream(stream)))
+        return out
+
+    # -- inspection ----------------------------------------------------------
+    def export_fif(self):
+        """(db_codes [N*Nv], list_offsets [K+1], list_rows [N*Nv]) as numpy arrays."""
+        n = self.n_shapes * self.views_per_shape
+        codes = np.empty(n, np.int32)
+        off = np.empty(self.n_codewords + 1, np.int64)
+        rows = np.empty(n, np.int32)
+        _check(load().gift_export_fif(self._h, _ptr(codes), _ptr(off), _ptr(rows), _stream()))
+        return codes, off, rows
+
+    def export_sif(self):
+        """(entry_offsets [N+1], entry_ids, entry_members uint32, card uint64 [N]) as numpy arrays."""
+        N = self.n_shapes
+        off = np.empty(N + 1, np.int64)
+        ids = np.empty(N * self.sif_k1, np.int32)
+        mem = np.empty(N * self.sif_k1, np.uint32)
+        card = np.empty(N, np.uint64)
+        _check(load().gift_export_sif(self._h, _ptr(off), _ptr(ids), _ptr(mem), _ptr(card), _stream()))
+        return off, ids, mem, card
+
+    def info(self) -> dict:
+        i = _Info()
+        _check(load().gift_index_info(self._h, ctypes.byref(i)))
+        return {n: getattr(i, n) for n, _ in _Info._fields_}
+
+    def set_timing(self, on: bool = True):
+        _check(load().gift_set_timing(self._h, int(bool(on))))
+
+    def timing(self) -> dict:
+        t = _Timing()
+        _check(load().gift_get_timing(self._h, ctypes.byref(t)))
+        return {n: getattr(t, n) for n, _ in _Timing._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().gift_destroy_index(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- differentiation
+def match_forward(q, q_offsets, p, W=None, stream=None):
+    """S [B, Np] of Eq. 3 after the projection u = W q, and the saved argmax [sum V_q, Np] (int16)."""
+    import torch
+    offs = _host_offsets(q_offsets)
+    Bq = len(offs) - 1
+    Np, nv, din = p.shape
+    dout = W.shape[0] if W is not None else din
+    S = torch.empty((Bq, Np), dtype=torch.float32, device=q.device)
+    am = torch.empty((q.shape[0], Np), dtype=torch.int16, device=q.device)
+    _check(load().gift_match_forward(_ptr(q), ctypes.c_void_p(offs.ctypes.data), Bq, _ptr(p), Np, nv, _ptr(W),
+                                     din, dout, _ptr(S), _ptr(am), _stream(stream)))
+    return S, am
+
+
+def match_backward(q, q_offsets, p, W, grad_S, argmax, need=(True, True, True), stream=None):
+    """(dW or None, dQ, dP) of sum(grad_S * S) through the saved argmax pair."""
+    import torch
+    offs = _host_offsets(q_offsets)
+    Bq = len(offs) - 1
+    Np, nv, din = p.shape
+    dout = W.shape[0] if W is not None else din
+    dW = torch.empty_like(W) if (W is not None and need[0]) else None
+    dQ = torch.empty_like(q) if need[1] else None
+    dP = torch.empty_like(p) if need[2] else None
+    _check(load().gift_match_backward(_ptr(q), ctypes.c_void_p(offs.ctypes.data), Bq, _ptr(p), Np, nv, _ptr(W), din,
+                                      dout, _ptr(grad_S.contiguous()), _ptr(argmax), _ptr(dW), _ptr(dQ), _ptr(dP),
+                                      _stream(stream)))
+    return dW, dQ, dP
+
+
+def _autograd_function():
+    import torch
+
+    class GiftMatch(torch.autograd.Function):
+        """S = GiftMatch.apply(q, q_offsets, p, W): Eq. 3 after u = W q, differentiable in q, p, W."""
+
+        @staticmethod
+        def forward(ctx, q, q_offsets, p, W):
+            q = q.contiguous()
+            p = p.contiguous()
+            Wc = W.contiguous() if W is not None else None
+            S, am = match_forward(q, q_offsets, p, Wc)
+            ctx.save_for_backward(q, p, Wc if Wc is not None else torch.empty(0), am)
+            ctx.q_offsets = _host_offsets(q_offsets)
+            ctx.has_w = W is not None
+            return S
+
+        @staticmethod
+        def backward(ctx, gS):
+            q, p, W, am = ctx.saved_tensors
+            W = W if ctx.has_w else None
+            need = (ctx.has_w and ctx.needs_input_grad[3], ctx.needs_input_grad[0], ctx.needs_input_grad[2])
+            dW, dQ, dP = match_backward(q, ctx.q_offsets, p, W, gS.contiguous(), am, need)
+            return dQ, None, dP, dW
+
+    return GiftMatch
+
+
+class _Lazy:
+    def __getattr__(self, item):
+        return getattr(_autograd_function(), item)
+
+
+GiftMatch = _Lazy()

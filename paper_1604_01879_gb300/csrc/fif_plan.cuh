@@ -1,0 +1,36 @@
+// Per-call plan of an F-IF batch (device buffers in the call's scratch).
+#pragma once
+#include "gift_internal.cuh"
+
+namespace gift {
+
+struct FifPlan {
+  // inputs
+  int64_t nv = 0;                 // query views in the batch
+  int ma = 1;                     // assignments per view
+  int32_t B = 0;                  // queries
+  const float* q = nullptr;       // [nv, D] FP32 query views
+  const float* q_inv = nullptr;   // [nv]
+  const int32_t* q_code = nullptr;// [nv * ma]
+  const int32_t* qoff = nullptr;  // [B+1] device
+  const int32_t* vquery = nullptr;// [nv] query of each view
+  unsigned long long* stats = nullptr;  // optional [2]: scanned bytes, pairs
+  // derived
+  int64_t nslots = 0;
+  int32_t* skeys = nullptr;       // [nslots] codeword of each slot (ascending)
+  int64_t* boff = nullptr;        // [K+1] slots of codeword k
+  int32_t* slot_view = nullptr;   // [nslots]
+  int32_t* view_slot = nullptr;   // [nv * ma]
+  int64_t* runbase = nullptr;     // [nslots] first table cell of each slot
+  int64_t* woff = nullptr;        // [K+1] scan work items per codeword (exclusive)
+  int64_t upper_items = 0;        // bound on the number of scan work items
+  int64_t table_upper = 0;        // bound on the table cells
+};
+
+void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s);
+void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
+              const int32_t* cand_sorted, int R, cudaStream_t s);
+void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
+                 const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s);
+
+}  // namespace gift

@@ -1,0 +1,179 @@
+// Internal declarations of the GIFT CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/gift.h"
+
+namespace gift {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+  gift_status status;
+  Error(gift_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(gift_status s, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define GIFT_CUDA(x) ::gift::check_cuda((x), #x, __FILE__, __LINE__)
+#define GIFT_LAUNCHED(name) ::gift::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)
+#define GIFT_REQUIRE(cond, msg) \
+  do { if (!(cond)) ::gift::fail(GIFT_EINVAL, msg); } while (0)
+
+// ---------------------------------------------------------------- scratch
+// Stream-ordered scratch: every allocation is released (stream-ordered) when
+// the Scratch object goes out of scope, so concurrent calls never share it.
+struct Scratch {
+  cudaStream_t stream;
+  std::vector<void*> blocks;
+  explicit Scratch(cudaStream_t s) : stream(s) {}
+  ~Scratch();
+  void* raw(size_t bytes);
+  template <class T> T* get(size_t n) { return static_cast<T*>(raw(n * sizeof(T) + 16)); }
+};
+
+// ---------------------------------------------------------------- fixed point
+// Shape scores are sums of per-view maxima in [0, 1]; they are accumulated in
+// uint64 fixed point so that the sum is exact and independent of the order.
+constexpr double kScoreFix = 4294967296.0;  // 2^32
+// S-IF memberships: uint32 round(S * 2^31), S in [0, 1].
+constexpr double kMemberFix = 2147483648.0;  // 2^31
+
+// ---------------------------------------------------------------- index
+struct Index {
+  gift_index_params prm{};
+  int64_t n_rows = 0;  // N * Nv
+  int device = 0;
+
+  // codebook
+  float* codebook = nullptr;   // [K, D]
+  float* cb_half_sq = nullptr; // [K]  0.5 * ||b_k||^2
+  float cb_max_norm = 0.f;
+
+  // database
+  float* master = nullptr;     // [n_rows, D] FP32 views (keep_exact)
+  float* row_inv = nullptr;    // [n_rows] 1/||x|| (0 for a zero row)
+  int32_t* db_codes = nullptr; // [n_rows]
+
+  // F-IF
+  int64_t* list_off = nullptr;   // [K+1]
+  std::vector<int64_t> h_list_off;
+  int32_t* list_row = nullptr;   // [n_rows] row of each entry (list order)
+  int32_t* list_shape = nullptr; // [n_rows]
+  void* list_feat = nullptr;     // [n_rows, D] in storage dtype
+  float* list_scale = nullptr;   // [n_rows] factor turning a stored dot into a cosine
+  int32_t* entry_run = nullptr;  // [n_rows] run index within its list
+  int32_t* nruns = nullptr;      // [K]
+  int64_t* run_off = nullptr;    // [K] first global run of each list
+  int32_t* run_shape = nullptr;  // [n_runs]
+  int64_t n_runs = 0;
+  int32_t max_runs = 0;
+  int32_t max_list = 0;
+  int32_t n_nonempty = 0;
+  int64_t scan_tiles_upper = 0;  // sum_k ceil(L_k / kScanTE)
+
+  // S-IF
+  int32_t k1 = 0;
+  int64_t* sif_off = nullptr;    // [N+1]
+  int32_t* sif_ids = nullptr;    // [N*k1]
+  uint32_t* sif_mem = nullptr;   // [N*k1]
+  uint64_t* sif_card = nullptr;  // [N]
+  int32_t max_sif_entry = 0;
+
+  size_t device_bytes = 0;
+  std::vector<void*> owned;
+
+  // timing
+  bool timing = false;
+  gift_timing_t last_timing{};
+  std::vector<cudaEvent_t> ev;  // stage events of the last timed call
+  std::vector<int> ev_stage;    // stage id of each event interval
+  unsigned long long* stats_pinned = nullptr;  // scan bytes, pairs, rescore bytes
+  bool stats_valid = false;
+
+  template <class T> T* alloc(size_t n);
+  ~Index();
+};
+
+size_t dtype_bytes(int storage);
+
+// ---------------------------------------------------------------- kernels
+// scan constants: entries and query slots per work item of the scan kernel
+constexpr int kScanTE = 64;
+constexpr int kScanTS = 64;
+
+// k_util.cu
+void launch_row_invnorm(const float* X, int64_t n, int D, float* inv, cudaStream_t s);
+void launch_half_sq_norm(const float* X, int64_t n, int D, float* out, cudaStream_t s);
+void scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, Scratch& sc, cudaStream_t s);
+// Stable sort of items 0..n-1 by key (0 <= key < nbins): perm_out lists item
+// indices grouped by key, ascending index within a key; keys_out the keys.
+void stable_sort_by_key(const int32_t* keys, int64_t n, int32_t nbins, int32_t* perm_out,
+                        int32_t* keys_out, Scratch& sc, cudaStream_t s);
+// off[k] = first position of key k in sorted keys, off[nbins] = n.
+void bin_offsets(const int32_t* sorted_keys, int64_t n, int32_t nbins, int64_t* off, cudaStream_t s);
+void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+
+// k_assign.cu
+// codes[v*ma + a] = a-th nearest codeword by (squared distance, index).
+void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes,
+                  Scratch& sc, cudaStream_t s);
+
+
+// k_exact.cu
+void exact_scores(const Index& ix, const float* q, const float* q_inv, int64_t nv,
+                  const int32_t* d_vquery, const std::vector<int32_t>& h_qoff, int32_t B,
+                  float* S_dense, Scratch& sc, cudaStream_t s);
+
+// k_topk.cu
+// Per row b of `scores` [B, n] (or of keys64 when scores == nullptr): the k
+// largest by (value desc, index asc). ids_out/val_out [B, k] (val_out may be
+// null). When n < k the tail gets id -1 and -INF.
+void topk_rows_f32(const float* scores, int32_t B, int64_t n, int32_t k, int32_t* ids_out,
+                   float* val_out, Scratch& sc, cudaStream_t s);
+void topk_rows_u64(const uint64_t* keys, int32_t B, int64_t n, int32_t k, int32_t* ids_out,
+                   uint64_t* key_out, Scratch& sc, cudaStream_t s);
+// Rows of (id, score) pairs of length r: sort by (score desc, id asc) and keep k.
+void sort_candidates(const int32_t* ids, const float* scores, int32_t B, int32_t r, int32_t k,
+                     int32_t* ids_out, float* scores_out, cudaStream_t s);
+// Rows of ids of length r: ascending copy.
+void sort_ids_rows(const int32_t* ids, int32_t B, int32_t r, int32_t* out, cudaStream_t s);
+
+// k_sif.cu
+void sif_build(Index& ix, const int32_t* nbr_ids, const float* nbr_scores, Scratch& sc,
+               cudaStream_t s);
+void sif_rerank(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B,
+                int32_t n_cand, int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime,
+                Scratch& sc, cudaStream_t s);
+
+// k_match.cu
+void match_forward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq,
+                   const float* p, int32_t Np, int32_t nv, const float* W, int32_t din,
+                   int32_t dout, float* S, int16_t* argmax, Scratch& sc, cudaStream_t s);
+void match_backward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq,
+                    const float* p, int32_t Np, int32_t nv, const float* W, int32_t din,
+                    int32_t dout, const float* gS, const int16_t* argmax, float* dW,
+                    float* dQ, float* dP, Scratch& sc, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Order-preserving map of a float to uint32 (larger float -> larger key).
+__device__ __forceinline__ uint32_t f2key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+}  // namespace gift

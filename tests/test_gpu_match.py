@@ -1,0 +1,78 @@
+"""Differentiable matching (Eq. 3 after a linear view projection) vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import gift_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _tie_free(seed, B, Np, nv, din, dout, margin=1e-3, vq=None):
+    g = np.random.default_rng(seed)
+    while True:
+        counts = np.full(B, nv) if vq is None else g.choice(vq, size=B)
+        off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        Q = g.standard_normal((off[-1], din)).astype(np.float32)
+        P = g.standard_normal((Np, nv, din)).astype(np.float32)
+        W = (g.standard_normal((dout, din)) / np.sqrt(din)).astype(np.float32)
+        U = Q.astype(np.float64) @ W.T.astype(np.float64)
+        V = P.reshape(-1, din).astype(np.float64) @ W.T.astype(np.float64)
+        s = O.cosine(U, V).reshape(off[-1], Np, nv)
+        top2 = np.sort(s, axis=2)[:, :, -2:]
+        if np.min(top2[:, :, 1] - top2[:, :, 0]) > margin:
+            G = g.standard_normal((B, Np)).astype(np.float32)
+            return Q, off, P, W, G
+
+
+@pytest.mark.parametrize("with_w", [True, False])
+def test_forward_and_argmax(gpu_lib, with_w):
+    import torch
+    Q, off, P, W, G = _tie_free(1, B=5, Np=37, nv=9, din=48, dout=32 if with_w else 48, margin=1e-4,
+                                vq=(3, 9, 14))
+    Wt = torch.from_numpy(W).cuda() if with_w else None
+    S, am = gpu_lib.match_forward(torch.from_numpy(Q).cuda(), off, torch.from_numpy(P).cuda(), Wt)
+    Sr, jr = O.match_forward(Q, off, P, W if with_w else None)
+    assert np.allclose(S.cpu().numpy(), Sr, rtol=1e-5, atol=1e-6)
+    assert np.array_equal(am.cpu().numpy().astype(np.int64), jr)
+
+
+@pytest.mark.parametrize("with_w", [True, False])
+def test_backward_matches_oracle(gpu_lib, with_w):
+    import torch
+    Q, off, P, W, G = _tie_free(2, B=4, Np=21, nv=8, din=32, dout=16 if with_w else 32)
+    Wd = torch.from_numpy(W).cuda() if with_w else None
+    qd, pd = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda()
+    S, am = gpu_lib.match_forward(qd, off, pd, Wd)
+    dW, dQ, dP = gpu_lib.match_backward(qd, off, pd, Wd, torch.from_numpy(G).cuda(), am)
+    rW, rQ, rP = O.match_backward(Q, off, P, W if with_w else None, G)
+    scale = max(np.abs(rQ).max(), np.abs(rP).max())
+    assert np.allclose(dQ.cpu().numpy(), rQ, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dP.cpu().numpy(), rP, rtol=1e-4, atol=1e-5 * scale)
+    if with_w:
+        assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
+
+
+def test_autograd_function(gpu_lib):
+    import torch
+    Q, off, P, W, G = _tie_free(3, B=3, Np=11, nv=8, din=32, dout=16)
+    q = torch.from_numpy(Q).cuda().requires_grad_(True)
+    p = torch.from_numpy(P).cuda().requires_grad_(True)
+    w = torch.from_numpy(W).cuda().requires_grad_(True)
+    S = gpu_lib.GiftMatch.apply(q, off, p, w)
+    (S * torch.from_numpy(G).cuda()).sum().backward()
+    rW, rQ, rP = O.match_backward(Q, off, P, W, G)
+    assert np.allclose(q.grad.cpu().numpy(), rQ, rtol=1e-4, atol=1e-5)
+    assert np.allclose(p.grad.cpu().numpy(), rP, rtol=1e-4, atol=1e-5)
+    assert np.allclose(w.grad.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
+
+
+def test_scale_invariants_on_gpu(gpu_lib):
+    """<q_i, dS/dq_i> = 0 and <W, dS/dW> = 0 (cosine scale invariance)."""
+    import torch
+    Q, off, P, W, G = _tie_free(4, B=3, Np=16, nv=8, din=32, dout=16)
+    qd, pd, Wd = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(), torch.from_numpy(W).cuda()
+    S, am = gpu_lib.match_forward(qd, off, pd, Wd)
+    dW, dQ, dP = gpu_lib.match_backward(qd, off, pd, Wd, torch.from_numpy(G).cuda(), am)
+    dq = dQ.double().cpu().numpy()
+    assert np.abs((Q * dq).sum(1)).max() < 1e-4 * np.abs(dq).max() * np.abs(Q).max() * Q.shape[1] ** 0.5
+    assert abs((W * dW.double().cpu().numpy()).sum()) < 1e-4 * np.abs(dW.cpu().numpy()).sum() * np.abs(W).max()

@@ -1,0 +1,281 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Sizes span several scan tiles (64 entries x 64 slots), several GEMM tiles
+(128 x 128) and ragged tails; edge cases: K = 1, MA up to 3, view counts that
+differ per query, database smaller than k, host buffers.
+"""
+import numpy as np
+import pytest
+
+from oracle import gift_oracle as O
+from synth import CONFIGS, make_config_inputs, shape_views, query_views, kmeans_codebook
+from tests.parity import assert_codes, assert_topk, code_margins, close, recall
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(N, Nv, D, C, K, nq, views, seed, ma=1):
+    X = shape_views(0, N, Nv, D, C, 1000 + seed, 4000 + seed)
+    cb = kmeans_codebook(X.reshape(-1, D), K, 3000 + seed, 8)
+    Q, qoff, _ = query_views(nq, views, D, C, 2000 + seed, 4000 + seed, max_views=max(views))
+    dbc = O.quantize(X.reshape(-1, D), cb, 1).reshape(N, Nv)
+    qc = O.quantize(Q, cb, ma)
+    return X, cb, Q, qoff, dbc, qc
+
+
+def _index(gift, torch, X, cb, N, Nv, K, **kw):
+    return gift.Index(torch.from_numpy(X).cuda(), torch.from_numpy(cb).cuda(), N, Nv, K, **kw)
+
+
+@pytest.fixture(scope="module")
+def c1(gpu_lib):
+    import torch
+    cfg = CONFIGS["db200x64_d128_k64"]
+    d = make_config_inputs(cfg)
+    X, cb, Q, qoff = d["db"], d["codebook"], d["q"], d["q_off"]
+    N, Nv, D, K = cfg.n_shapes, cfg.n_views, cfg.dim, cfg.n_codewords
+    dbc = O.quantize(X.reshape(-1, D), cb, 1).reshape(N, Nv)
+    qc = O.quantize(Q, cb, 1)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="f32", sif_k1=cfg.sif_k1, keep_exact=True)
+    yield dict(cfg=cfg, X=X, cb=cb, Q=Q, qoff=qoff, dbc=dbc, qc=qc, ix=ix)
+    ix.close()
+
+
+# ------------------------------------------------------------------ quantiser
+@pytest.mark.parametrize("ma", [1, 2, 3])
+def test_assign_matches_oracle(c1, ma):
+    import torch
+    Q, cb = c1["Q"], c1["cb"]
+    got = c1["ix"].assign(torch.from_numpy(Q).cuda(), ma).cpu().numpy()
+    ref = O.quantize(Q, cb, ma)
+    n_bad, n_tied = assert_codes(got, ref, code_margins(Q, cb, ma))
+    assert n_bad <= n_tied
+
+
+def test_assign_database_rows_all_codewords(c1):
+    import torch
+    X, cb = c1["X"], c1["cb"]
+    rows = X.reshape(-1, X.shape[2])
+    got = c1["ix"].assign(torch.from_numpy(rows).cuda(), 1).cpu().numpy()
+    assert_codes(got, O.quantize(rows, cb, 1), code_margins(rows, cb, 1))
+
+
+# ------------------------------------------------------------------ F-IF structure
+def test_posting_lists_identical(c1):
+    codes, off, rows = c1["ix"].export_fif()
+    N, Nv = c1["dbc"].shape
+    assert_codes(codes.reshape(-1, 1), c1["dbc"].reshape(-1, 1),
+                 code_margins(c1["X"].reshape(N * Nv, -1), c1["cb"], 1))
+    lists = O.build_fif(codes.reshape(N, Nv), c1["cb"].shape[0])
+    assert off[0] == 0 and off[-1] == N * Nv
+    for k, l in enumerate(lists):
+        assert off[k + 1] - off[k] == len(l)
+        ref = (l[:, 0] * Nv + l[:, 1]) if len(l) else np.zeros(0, np.int64)
+        assert np.array_equal(rows[off[k]:off[k + 1]], ref)
+
+
+# ------------------------------------------------------------------ scores and top-k
+def test_exact_query_small_config(c1):
+    import torch
+    ids, sc = c1["ix"].query(torch.from_numpy(c1["Q"]).cuda(), c1["qoff"], mode="exact", topk=10)
+    ref = O.exact_scores(c1["Q"], c1["qoff"], c1["X"])
+    for b in range(len(c1["qoff"]) - 1):
+        assert_topk(ids[b].cpu().numpy(), sc[b].cpu().numpy(), ref[b], 10)
+
+
+def test_fif_query_small_config(c1):
+    import torch
+    ids, sc = c1["ix"].query(torch.from_numpy(c1["Q"]).cuda(), c1["qoff"], mode="fif", topk=10)
+    ref = O.fif_scores(c1["Q"], c1["qoff"], c1["qc"], c1["X"], c1["dbc"])
+    for b in range(len(c1["qoff"]) - 1):
+        assert_topk(ids[b].cpu().numpy(), sc[b].cpu().numpy(), ref[b], 10)
+
+
+def test_fif_full_rows_small_config(c1):
+    """topk = N: every shape's F-IF score, compared element by element."""
+    import torch
+    N = c1["cfg"].n_shapes
+    ids, sc = c1["ix"].query(torch.from_numpy(c1["Q"]).cuda(), c1["qoff"], mode="fif", topk=N)
+    ref = O.fif_scores(c1["Q"], c1["qoff"], c1["qc"], c1["X"], c1["dbc"])
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for b in range(ids.shape[0]):
+        assert sorted(ids[b].tolist()) == list(range(N))
+        assert close(sc[b], ref[b, ids[b]]).all()
+
+
+@pytest.mark.parametrize("ma", [1, 2, 3])
+def test_fif_ragged_multiple_assignment(gpu_lib, ma):
+    """N, N_v, V_q not multiples of any tile; lists longer than a scan tile."""
+    import torch
+    N, Nv, D, C, K = 37, 20, 48, 4, 6
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 9, (5, 12, 20, 33), 31, ma)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="f32", query_ma=ma, keep_exact=True)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=N)
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for b in range(len(qoff) - 1):
+        assert close(sc[b], ref[b, ids[b]]).all(), b
+        assert_topk(ids[b], sc[b], ref[b], N)
+    ids_e, sc_e = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="exact", topk=N)
+    ref_e = O.exact_scores(Q, qoff, X)
+    for b in range(len(qoff) - 1):
+        assert_topk(ids_e[b].cpu().numpy(), sc_e[b].cpu().numpy(), ref_e[b], N)
+    ix.close()
+
+
+def test_many_slots_per_list(gpu_lib):
+    """K = 3 codewords: every list is long and is hit by many query views (slot chunks)."""
+    import torch
+    N, Nv, D, C, K = 300, 16, 32, 3, 3
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 40, (16, 7), 41)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="f32", keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=50)
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    for b in range(len(qoff) - 1):
+        assert_topk(ids[b].cpu().numpy(), sc[b].cpu().numpy(), ref[b], 50)
+    ix.close()
+
+
+def test_one_codeword_fif_equals_exact(gpu_lib):
+    """K = 1: Eq. 4 reduces to Eq. 3 on the GPU as in the oracle."""
+    import torch
+    N, Nv, D = 50, 24, 64
+    X = shape_views(0, N, Nv, D, 5, 1051, 4051)
+    cb = np.ones((1, D), np.float32)
+    Q, qoff, _ = query_views(6, (24, 9), D, 5, 2051, 4051, max_views=24)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, 1, storage="f32", keep_exact=True)
+    qd = torch.from_numpy(Q).cuda()
+    ids_f, sc_f = ix.query(qd, qoff, mode="fif", topk=N)
+    ids_e, sc_e = ix.query(qd, qoff, mode="exact", topk=N)
+    ref = O.exact_scores(Q, qoff, X)
+    for b in range(len(qoff) - 1):
+        assert_topk(ids_f[b].cpu().numpy(), sc_f[b].cpu().numpy(), ref[b], N)
+        assert_topk(ids_e[b].cpu().numpy(), sc_e[b].cpu().numpy(), ref[b], N)
+    ix.close()
+
+
+def test_self_match_ranks_first(c1):
+    import torch
+    X = c1["X"]
+    N, Nv, D = X.shape
+    pick = [0, 17, 199]
+    Q = np.concatenate([X[p] for p in pick])
+    qoff = np.arange(0, len(pick) * Nv + 1, Nv, dtype=np.int32)
+    for mode in ("fif", "exact"):
+        ids, sc = c1["ix"].query(torch.from_numpy(Q).cuda(), qoff, mode=mode, topk=3)
+        assert ids[:, 0].cpu().tolist() == pick
+        assert np.allclose(sc[:, 0].cpu().numpy(), 1.0, atol=2e-6)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_reduced_precision_store_with_fp32_rescore(gpu_lib, storage):
+    """BF16 / FP8 store, top-R rescored in FP32: scores FP32-accurate."""
+    import torch
+    N, Nv, D, C, K = 160, 32, 128, 8, 24
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 12, (32,), 61)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage=storage, rescore_r=60, keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=20)
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    for b in range(len(qoff) - 1):
+        assert_topk(ids[b].cpu().numpy(), sc[b].cpu().numpy(), ref[b], 20)
+    ix.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 3e-3), ("fp8", 6e-2)])
+def test_reduced_precision_store_without_rescore(gpu_lib, storage, tol):
+    import torch
+    N, Nv, D, C, K = 120, 32, 128, 6, 16
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 8, (32,), 71)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage=storage, keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=N)
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    for b in range(len(qoff) - 1):
+        i = ids[b].cpu().numpy()
+        assert np.abs(sc[b].cpu().numpy() - ref[b, i]).max() < tol
+    ix.close()
+
+
+def test_database_smaller_than_k(gpu_lib):
+    import torch
+    N, Nv, D, C, K = 5, 8, 16, 2, 3
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 2, (8,), 81)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="f32", keep_exact=True)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=8)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    assert (ids[:, N:] == -1).all() and np.isneginf(sc[:, N:]).all()
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    for b in range(2):
+        assert_topk(ids[b, :N], sc[b, :N], ref[b], N)
+    ix.close()
+
+
+def test_host_buffers_match_device(c1):
+    import torch
+    Q = c1["Q"]
+    ids_d, sc_d = c1["ix"].query(torch.from_numpy(Q).cuda(), c1["qoff"], mode="fif", topk=10)
+    out = (np.empty((len(c1["qoff"]) - 1, 10), np.int32), np.empty((len(c1["qoff"]) - 1, 10), np.float32))
+    qh = torch.from_numpy(Q).pin_memory()
+    c1["ix"].query(qh, c1["qoff"], mode="fif", topk=10, out=out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out[0], ids_d.cpu().numpy())
+    assert np.array_equal(out[1], sc_d.cpu().numpy())
+
+
+def test_invalid_arguments_rejected(c1):
+    import torch
+    import paper_1604_01879_gb300 as gift
+    qd = torch.from_numpy(c1["Q"]).cuda()
+    with pytest.raises(gift.GiftError):
+        c1["ix"].query(qd, c1["qoff"], mode="fif", topk=2000)
+    bad = np.array(c1["qoff"]).copy()
+    bad[2] = bad[1]
+    with pytest.raises(gift.GiftError):
+        c1["ix"].query(qd, bad, mode="fif", topk=10)
+    with pytest.raises(gift.GiftError):
+        gift.Index(torch.zeros((4, 2, 20), device="cuda"), torch.zeros((3, 20), device="cuda"), 4, 2, 3)
+
+
+# ------------------------------------------------------------------ S-IF
+def _oracle_sif(X, dbc, cb, k1):
+    N, Nv, D = X.shape
+    rows = X.reshape(-1, D)
+    S_db = O.fif_scores(rows, np.arange(0, N * Nv + 1, Nv), O.quantize(rows, cb, 1), X, dbc)
+    return S_db, O.db_memberships(S_db, k1)
+
+
+def test_sif_entries_match_oracle(c1):
+    X, dbc, cb = c1["X"], c1["dbc"], c1["cb"]
+    k1 = c1["cfg"].sif_k1
+    N = X.shape[0]
+    S_db, F_db = _oracle_sif(X, dbc, cb, k1)
+    off, ids, mem, card = c1["ix"].export_sif()
+    assert off[-1] == N * k1
+    # shapes whose k1-th / (k1+1)-th neighbours are too close to order are skipped
+    srt = -np.sort(-S_db, axis=1)
+    boundary_ok = (srt[:, k1 - 1] - srt[:, k1]) > 2e-5
+    got = np.zeros((N, N))
+    for i in range(N):
+        for p, m in zip(ids[off[i]:off[i + 1]], mem[off[i]:off[i + 1]]):
+            got[p, i] = m / 2.0 ** 31
+    for p in np.nonzero(boundary_ok)[0]:
+        assert np.array_equal(np.nonzero(got[p])[0], np.nonzero(F_db[p])[0]), p
+        assert np.allclose(got[p], F_db[p], rtol=2e-5, atol=2e-6)
+        assert abs(card[p] / 2.0 ** 31 - F_db[p].sum()) < 1e-4
+    assert boundary_ok.mean() > 0.8
+    for i in range(N):
+        assert np.all(np.diff(ids[off[i]:off[i + 1]]) > 0)  # p ascending
+
+
+def test_rerank_matches_oracle(c1):
+    import torch
+    X, dbc, cb, Q, qoff = c1["X"], c1["dbc"], c1["cb"], c1["Q"], c1["qoff"]
+    k1 = c1["cfg"].sif_k1
+    S_db, F_db = _oracle_sif(X, dbc, cb, k1)
+    S_q = O.fif_scores(Q, qoff, c1["qc"], X, dbc)
+    ids, sc = c1["ix"].query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=30)
+    rid, rsp = c1["ix"].rerank(ids, sc, k1=k1, topk=10)
+    rid, rsp = rid.cpu().numpy(), rsp.cpu().numpy()
+    for b in range(len(qoff) - 1):
+        Fq = O.membership(S_q[b], k1)
+        ref = np.array([O.contextual(Fq, F_db[p]) for p in range(X.shape[0])])
+        assert_topk(rid[b], rsp[b], ref, 10, rtol=1e-4, atol=2e-5)
