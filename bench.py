@@ -1,0 +1,435 @@
+"""Benchmark of the GIFT query path on GB300.
+
+One step = one batch of queries through the whole hot path: quantise the
+query views, bucket them by codeword, scan the touched F-IF lists, combine
+into shape scores (Eq. 4), select the top-R, rescore them with FP32
+features, select the top-k (gift_query), then re-rank through the S-IF
+(gift_rerank, Eqs. 7-14).
+
+Default workload: 12,000 database shapes x 64 views x D=4096 (BF16 store),
+K=1024 codewords, batches of 1,000 queries of 64 views, FP32 rescore of the
+top 200, top-100 output, S-IF k1=50.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gift|reference]
+
+Under torchrun (N > 1) every rank holds a replica of the index and serves
+its own query batches (queries are independent; no data-path collective):
+weak scaling, time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_CONFIG = "db12000x64_d4096_k1024"
+METRIC = "queries/s and p99 ms, F-IF vs exact on one GB300, at recall@100 >= 0.99 vs FP64"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+        self.marks = []
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip() for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            c = [x.strip() for x in r.split(",")]
+            try:
+                s, m = float(c[1]), float(c[2])
+            except (ValueError, IndexError):
+                continue
+            mx = max(mx, m)
+            sm.append(s)
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        busy = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks / traffic
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1604_01879_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    try:
+        for line in open(path):
+            c = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(c) >= 4 and c[0] == kernel and c[1] == src_hash:
+                return float(c[2]), c[3]
+    except OSError:
+        pass
+    return None, None
+
+
+# ---------------------------------------------------------------- reference arm
+def cpu_oracle_run(cfg, data, n_queries, steps, db_codes=None):
+    """Time the FP64 oracle's query path (Eq. 4 + ranking + S-IF re-rank) on host cores."""
+    from oracle import gift_oracle as O
+    N, Nv, D = cfg.n_shapes, cfg.n_views, cfg.dim
+    X = data["db"]
+    if db_codes is None:
+        t = time.time()
+        db_codes = O.quantize(X.reshape(-1, D), data["codebook"], 1).reshape(N, Nv)
+        log(f"[reference] oracle database codes in {time.time() - t:.1f}s")
+    # S-IF activations of the database: a seeded sparse stand-in with k1 entries per row
+    # (building the true ones needs N oracle queries, an off-line cost outside the step)
+    g = np.random.default_rng(cfg.seed + 77)
+    F_db = np.zeros((N, N))
+    for p in range(N):
+        nb = g.choice(N, cfg.sif_k1, replace=False)
+        F_db[p, nb] = g.random(cfg.sif_k1)
+        F_db[p, p] = 1.0
+    q, qoff = data["q"], data["q_off"]
+    times = []
+    b = 0
+    for _ in range(steps):
+        t = time.time()
+        for _ in range(n_queries):
+            lo, hi = qoff[b], qoff[b + 1]
+            Qb = q[lo:hi]
+            off = np.array([0, hi - lo])
+            qc = O.quantize(Qb, data["codebook"], cfg.query_ma)
+            S = O.fif_scores(Qb, off, qc, X, db_codes)[0]
+            O.rank(S, cfg.topk)
+            O.rerank(S[None, :], F_db, cfg.sif_k1, cfg.topk)
+            b = (b + 1) % (len(qoff) - 1)
+        times.append(time.time() - t)
+    return times, db_codes
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [os.cpu_count() or 1])
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gift", choices=["gift", "reference"])
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="steps only (for ncu launch lists)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if not args.profile else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from synth import CONFIGS, make_config_inputs
+    cfg = CONFIGS[args.config]
+    B = cfg.batch or cfg.n_queries
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        data = make_config_inputs(cfg, n_queries=max(8, args.steps + args.warmup))
+        times, _ = cpu_oracle_run(cfg, data, 1, args.warmup + args.steps)
+        t = times[args.warmup:]
+        qps = len(t) / sum(t)
+        cores = blas_threads()
+        line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(t),
+                "p99_ms": 1e3 * float(np.percentile(t, 99)), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": cfg.name, "queries_per_step": 1, "db_shapes": cfg.n_shapes,
+                           "views": cfg.n_views, "dim": cfg.dim, "codewords": cfg.n_codewords, "topk": cfg.topk,
+                           "sif_k1": cfg.sif_k1},
+                "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                 "sample": "1 query per step through the FP64 oracle: Eq. 4 over all shapes, "
+                                           "top-k, dense Eq. 8 re-rank (off-line database codes untimed)"},
+                "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_1604_01879_gb300 as gift
+    from paper_1604_01879_gb300 import build as gbuild
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    gift.load()
+
+    t0 = time.time()
+    data = make_config_inputs(cfg)
+    if rank > 0:  # every rank serves its own query stream
+        from synth.workload import query_views
+        q, qo, _ = query_views(cfg.n_queries, cfg.query_views, cfg.dim, cfg.n_classes,
+                               cfg.query_seed + 100 * rank, cfg.centre_seed, cfg.noise, max_views=cfg.n_views)
+        data["q"], data["q_off"] = q, qo
+    log(f"[bench] inputs generated in {time.time() - t0:.1f}s")
+    t0 = time.time()
+    db_dev = torch.from_numpy(data["db"]).to(dev)
+    ix = gift.Index(db_dev, torch.from_numpy(data["codebook"]).to(dev), cfg.n_shapes, cfg.n_views,
+                    cfg.n_codewords, storage=cfg.storage, query_ma=cfg.query_ma, sif_k1=cfg.sif_k1,
+                    rescore_r=cfg.rescore_r, keep_exact=True)
+    torch.cuda.synchronize()
+    del db_dev
+    log(f"[bench] index built in {time.time() - t0:.1f}s: {ix.info()}")
+
+    q_all = torch.from_numpy(data["q"]).to(dev)
+    qoff = np.asarray(data["q_off"], np.int64)
+    nb = (len(qoff) - 1) // B
+    batches = []
+    for i in range(nb):
+        lo, hi = qoff[i * B], qoff[(i + 1) * B]
+        batches.append((q_all[lo:hi], (qoff[i * B:(i + 1) * B + 1] - lo).astype(np.int32)))
+    topk, k1 = cfg.topk, cfg.sif_k1
+    stream = torch.cuda.current_stream()
+    out_q = (torch.empty((B, topk), dtype=torch.int32, device=dev), torch.empty((B, topk), device=dev))
+    out_r = (torch.empty((B, topk), dtype=torch.int32, device=dev), torch.empty((B, topk), device=dev))
+
+    def step(i, timing=False):
+        qb, ob = batches[i % nb]
+        ix.query(qb, ob, mode="fif", topk=topk, out=out_q)
+        st_q = ix.timing() if timing else None
+        ix.rerank(out_q[0], out_q[1], k1=k1, topk=topk, out=out_r)
+        st_r = ix.timing() if timing else None
+        return st_q, st_r
+
+    # ---- device-timed steps (inputs resident in HBM; lists 6.3 GB >> L2)
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index) if not args.profile else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.nvtx.range_push("timed_steps")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    n_launch0 = gift.launch_count()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    n_launches = gift.launch_count() - n_launch0
+    if args.profile:
+        torch.cuda.nvtx.range_pop()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t_tensor = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_tensor, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    total_ms = float(t_tensor.item())
+    if args.profile:
+        log(f"[bench] profile run: {total_ms / args.steps:.3f} ms/step")
+        return
+
+    # ---- per-stage device times (CUDA events recorded by the library on this stream)
+    ix.set_timing(True)
+    stages = []
+    for i in range(max(3, min(args.steps, 10))):
+        stages.append(step(i, timing=True))
+    ix.set_timing(False)
+    clocks = sampler.stop()
+
+    def avg(key, which=0):
+        return statistics.mean(s[which][key] for s in stages)
+
+    st = {k: avg(k) for k in ("assign_ms", "bucket_ms", "scan_ms", "combine_ms", "topk_ms", "rescore_ms",
+                               "total_ms")}
+    st["rerank_ms"] = avg("rerank_ms", 1)
+    scan_bytes = stages[-1][0]["scan_bytes"]
+    scan_pairs = stages[-1][0]["scan_pairs"]
+
+    # ---- end to end through the C ABI with host buffers
+    q_host = [(torch.from_numpy(data["q"][qoff[i * B]:qoff[(i + 1) * B]]).pin_memory(), batches[i][1])
+              for i in range(nb)]
+    hq = (torch.empty((B, topk), dtype=torch.int32).pin_memory(), torch.empty((B, topk)).pin_memory())
+    hr = (torch.empty((B, topk), dtype=torch.int32).pin_memory(), torch.empty((B, topk)).pin_memory())
+
+    def e2e_step(i):
+        qh, ob = q_host[i % nb]
+        ix.query(qh, ob, mode="fif", topk=topk, out=hq)
+        ix.rerank(hq[0], hq[1], k1=k1, topk=topk, out=hr)
+
+    for i in range(args.warmup):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e_ev[0].record(stream)
+    for i in range(args.steps):
+        e2e_step(i)
+    e_ev[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_ev[0].elapsed_time(e_ev[1]) / args.steps
+    h2d = q_host[0][0].numel() * 4 + 2 * B * topk * 4
+    d2h = 4 * B * topk * 4
+
+    # ---- exact match (Eq. 3, FP32) on a sub-batch, the plain path
+    nx = min(B, 64)
+    qx, ox = batches[0][0][:int(batches[0][1][nx])], batches[0][1][:nx + 1]
+    ix.query(qx, ox, mode="exact", topk=topk)
+    torch.cuda.synchronize()
+    x_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    x_ev[0].record(stream)
+    ix.query(qx, ox, mode="exact", topk=topk)
+    x_ev[1].record(stream)
+    torch.cuda.synchronize()
+    exact_ms = x_ev[0].elapsed_time(x_ev[1])
+    exact_qps = nx / (exact_ms / 1e3)
+
+    value = world * args.steps * B / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": cfg.name, "db_shapes": cfg.n_shapes, "views": cfg.n_views, "dim": cfg.dim,
+                   "codewords": cfg.n_codewords, "query_ma": cfg.query_ma, "queries_per_step": B,
+                   "storage": cfg.storage, "rescore_r": cfg.rescore_r, "topk": topk, "sif_k1": k1,
+                   "l2": "inputs larger than L2 (list store 6.3 GB, queries 1 GB per batch)",
+                   "parallelism": f"replica x{world}"},
+        "exact": {"value": exact_qps, "unit": "queries/s", "queries": nx, "ms": exact_ms,
+                  "speedup_fif_over_exact": value / world / exact_qps},
+        "stages_ms": st,
+        "e2e": {"value": B / (e2e_ms / 1e3) * world, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+    }
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    stage_kernel = {"scan_ms": "k_fif_scan", "rescore_ms": "k_fif_scan<rescore>", "assign_ms": "k_sgemm_nt<assign>",
+                    "combine_ms": "k_fif_combine", "topk_ms": "k_topk", "rerank_ms": "k_rerank"}
+    dom = max(stage_kernel, key=lambda k: st.get(k, 0.0))
+    fp32_peak = 152 * 128 * 2 * (clocks["sm_mhz"] if clocks else 1900.0) * 1e6 / 1e12
+    src_hash = kernel_source_hash(["k_fif.cu", "fif_plan.cuh"])
+    if dom in ("scan_ms", "rescore_ms"):
+        ms = st[dom]
+        flops = 2.0 * scan_pairs * cfg.dim
+        kname = "k_fif_scan" if dom == "scan_ms" else "k_fif_scan_rescore"
+        traffic, _ = recorded_traffic(kname, src_hash)
+        line["roofline"] = {"kernel": kname, "bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
+                            "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / fp32_peak,
+                            "traffic": traffic, "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x median SM clock",
+                            "hbm_view": {"algorithmic_bytes": scan_bytes, "achieved_gbs": scan_bytes / (ms / 1e3) / 1e9,
+                                         "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}}
+    else:
+        line["roofline"] = {"kernel": stage_kernel[dom], "bound": "alu", "achieved": None, "peak": fp32_peak,
+                            "unit": "TFLOP/s", "frac": None, "traffic": None}
+    line["gpu_launches"] = n_launches
+
+    # ---- recall@100 vs the FP64 oracle on sampled queries (untimed)
+    db_codes = None
+    if not args.no_recall and rank == 0:
+        from oracle import gift_oracle as O
+        t = time.time()
+        N, Nv, D = cfg.n_shapes, cfg.n_views, cfg.dim
+        db_codes = O.quantize(data["db"].reshape(-1, D), data["codebook"], 1).reshape(N, Nv)
+        log(f"[bench] oracle database codes in {time.time() - t:.1f}s")
+        ids, sc = ix.query(batches[0][0], batches[0][1], mode="fif", topk=topk)
+        ids = ids.cpu().numpy()
+        sc = sc.cpu().numpy()
+        rec, errs = [], []
+        for b in (0, B // 3, (2 * B) // 3, B - 1):
+            lo, hi = qoff[b], qoff[b + 1]
+            Qb = data["q"][lo:hi]
+            off = np.array([0, hi - lo])
+            Sref = O.fif_scores(Qb, off, O.quantize(Qb, data["codebook"], cfg.query_ma), data["db"], db_codes)[0]
+            ref_ids, _ = O.rank(Sref, topk)
+            rec.append(len(set(ids[b].tolist()) & set(ref_ids.tolist())) / topk)
+            errs.append(float(np.max(np.abs(sc[b] - Sref[ids[b]]) / np.maximum(np.abs(Sref[ids[b]]), 1e-30))))
+        line["recall_at_100"] = {"value": float(np.mean(rec)), "min": float(np.min(rec)), "queries": len(rec),
+                                 "max_rel_score_err": float(np.max(errs)), "vs": "FP64 oracle, Eq. 4"}
+        log(f"[bench] recall {rec} max rel err {max(errs):.2e} in {time.time() - t:.1f}s")
+
+    # ---- CPU baseline: the oracle on host cores, bounded sample (rank 0, N = 1)
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        times, _ = cpu_oracle_run(cfg, data, 1, 4, db_codes=db_codes)
+        line["cpu_baseline"] = {"value": 1.0 / statistics.mean(times[1:]), "unit": "queries/s",
+                                "cores": blas_threads(), "kind": "oracle",
+                                "sample": "3 queries (after 1 warm-up) through the FP64 oracle: Eq. 4 over all "
+                                          "12,000 shapes, top-100, dense Eq. 8 re-rank over 12,000 shapes"}
+
+    ix.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -247,6 +247,10 @@ GIFT_API gift_status gift_match_backward(const float* q, const int32_t* q_view_o
                                 const int16_t* argmax, float* dW, float* dQ, float* dP,
                                 cudaStream_t stream);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads); the difference across a region counts its launches. */
+GIFT_API int64_t gift_launch_count(void);
+
 /* Message of the last failing call on the calling thread ("" if none). */
 GIFT_API const char* gift_last_error(void);
 

@@ -79,6 +79,7 @@ _SIGS = {
     "gift_match_backward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P, _P,
                                    _P]),
     "gift_last_error": (ctypes.c_char_p, []),
+    "gift_launch_count": (_I64, []),
     "gift_version": (_I32, []),
 }
 SYMBOLS = tuple(_SIGS)
@@ -132,6 +133,11 @@ def _host_offsets(q_off):
     a = np.ascontiguousarray(np.asarray(
         q_off.cpu().numpy() if hasattr(q_off, "cpu") else q_off, dtype=np.int32))
     return a
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().gift_launch_count())
 
 
 class Index:

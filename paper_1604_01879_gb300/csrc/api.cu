@@ -1,6 +1,7 @@
 // C ABI of the GIFT library: index build, queries, re-ranking, exports.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <functional>
 #include <memory>
 
@@ -231,10 +232,10 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   P.vquery = vquery;
   P.stats = stats;
   fif_plan(ix, P, sc, s);
-
-  tm.mark(ST_SCAN);
   uint32_t* table = sc.get<uint32_t>(P.table_upper);
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
+
+  tm.mark(ST_SCAN);
   fif_scan(ix, P, table, false, nullptr, 0, s);
 
   tm.mark(ST_COMBINE);
@@ -264,6 +265,9 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
 }  // namespace
 
 // ------------------------------------------------------------------ plumbing
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 [[noreturn]] void fail(gift_status s, const std::string& msg) { throw Error(s, msg); }
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
@@ -709,5 +713,7 @@ gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, i
 const char* gift_last_error(void) { return gift::g_last_error.c_str(); }
 
 int32_t gift_version(void) { return 100; }
+
+int64_t gift_launch_count(void) { return gift::g_launches.load(); }
 
 }  // extern "C"

@@ -24,7 +24,9 @@ struct Error : std::runtime_error {
 [[noreturn]] void fail(gift_status s, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define GIFT_CUDA(x) ::gift::check_cuda((x), #x, __FILE__, __LINE__)
-#define GIFT_LAUNCHED(name) ::gift::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)
+void count_launch();
+#define GIFT_LAUNCHED(name) \
+  do { ::gift::count_launch(); ::gift::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__); } while (0)
 #define GIFT_REQUIRE(cond, msg) \
   do { if (!(cond)) ::gift::fail(GIFT_EINVAL, msg); } while (0)
 

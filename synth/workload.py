@@ -191,14 +191,18 @@ def kmeans_codebook(sample: np.ndarray, k: int, seed: int, iters: int) -> np.nda
         raise ValueError("k-means needs at least k sample points")
     g = _gen(seed, 0)
     C = X[np.sort(g.choice(n, size=k, replace=False))].copy()
+    X32 = X.astype(np.float32)
     xx = (X * X).sum(1)
     for _ in range(iters):
         cc = (C * C).sum(1)
-        dist = xx[:, None] - 2.0 * (X.astype(np.float32) @ C.T.astype(np.float32)) + cc[None, :]
+        dist = xx[:, None] - 2.0 * (X32 @ C.T.astype(np.float32)) + cc[None, :]
         lab = dist.argmin(1)
+        order = np.argsort(lab, kind="stable")
         cnt = np.bincount(lab, minlength=k)
+        starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+        nonempty = cnt > 0
         sums = np.zeros_like(C)
-        np.add.at(sums, lab, X)
+        sums[nonempty] = np.add.reduceat(X[order], starts[nonempty], axis=0)
         far = np.argsort(-dist[np.arange(n), lab], kind="stable")
         fi = 0
         for c in range(k):
