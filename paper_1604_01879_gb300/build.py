@@ -27,6 +27,9 @@ SOURCES = [
     "k_topk.cu",
     "k_sif.cu",
     "k_match.cu",
+    "k_scan_tc.cu",
+    "tc_host.cu",
+    "k_exact_tc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

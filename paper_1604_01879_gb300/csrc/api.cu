@@ -125,6 +125,20 @@ __global__ void k_pack_lists(const float* __restrict__ master, const int32_t* __
   if (lane == 0) scale_out[e] = sc * row_inv[row];
 }
 
+// residual of the BF16 store: lo = bf16(x - bf16(x)), list order
+__global__ void k_pack_lo(const float* __restrict__ master, const int32_t* __restrict__ list_row, int64_t n, int D,
+                          __nv_bfloat16* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= n) return;
+  const float* x = master + (int64_t)list_row[e] * D;
+  __nv_bfloat16* o = out + e * D;
+  for (int d = lane; d < D; d += 32) {
+    const float v = x[d];
+    o[d] = __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+  }
+}
+
 __global__ void k_list_meta(const int32_t* __restrict__ list_row, const int32_t* __restrict__ skeys, int64_t n,
                             int nv, int32_t* __restrict__ list_shape, int64_t* __restrict__ run_flag) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,7 +232,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   float* q_inv = sc.get<float>(nv);
   launch_row_invnorm(q, nv, ix.prm.dim, q_inv, s);
   int32_t* q_code = sc.get<int32_t>(nv * ma);
-  assign_codes(ix, q, nv, ma, q_code, sc, s);
+  assign_codes(ix, q, nv, ma, q_code, sc, s, q_inv);
 
   tm.mark(ST_BUCKET);
   FifPlan P;
@@ -236,7 +250,10 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
 
   tm.mark(ST_SCAN);
-  fif_scan(ix, P, table, false, nullptr, 0, s);
+  if (ix.prm.storage == GIFT_BF16)
+    fif_scan_tc(ix, P, table, false, nullptr, 0, sc, s);
+  else
+    fif_scan(ix, P, table, false, nullptr, 0, s);
 
   tm.mark(ST_COMBINE);
   float* S = sc.get<float>((size_t)B * N);
@@ -255,7 +272,10 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
 
   tm.mark(ST_RESCORE);
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
-  fif_scan(ix, P, table, true, cand_sorted, Rr, s);
+  if (ix.list_lo)
+    fif_scan_tc(ix, P, table, true, cand_sorted, Rr, sc, s);
+  else
+    fif_scan(ix, P, table, true, cand_sorted, Rr, s);
   float* cand_score = sc.get<float>((size_t)B * Rr);
   fif_combine(ix, P, table, nullptr, cand_sorted, Rr, cand_score, s);
   tm.mark(ST_TOPK);
@@ -381,14 +401,23 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   GIFT_CUDA(cudaMemcpyAsync(ix->codebook, codebook, (size_t)K * D * 4, cudaMemcpyDefault, s));
   ix->cb_half_sq = ix->alloc<float>(K);
   launch_half_sq_norm(ix->codebook, K, D, ix->cb_half_sq, s);
+  ix->cb_rows_alloc = (int64_t)K + 256;  // one TMA box of padding rows
+  ix->cb_hi = ix->alloc<__nv_bfloat16>((size_t)ix->cb_rows_alloc * D);
+  ix->cb_lo = ix->alloc<__nv_bfloat16>((size_t)ix->cb_rows_alloc * D);
+  GIFT_CUDA(cudaMemsetAsync(ix->cb_hi, 0, (size_t)ix->cb_rows_alloc * D * 2, s));
+  GIFT_CUDA(cudaMemsetAsync(ix->cb_lo, 0, (size_t)ix->cb_rows_alloc * D * 2, s));
+  split_rows_bf16(ix->codebook, K, D, ix->cb_hi, ix->cb_lo, s);
   float* d_cbmax = sc.get<float>(1);
   k_cb_maxnorm<<<1, 1024, 0, s>>>(ix->cb_half_sq, K, d_cbmax);
   GIFT_LAUNCHED("k_cb_maxnorm");
 
   // FP32 master (kept for the exact match and the rescore; otherwise scratch)
-  float* master = (p.keep_exact || p.rescore_r > 0) ? ix->alloc<float>((size_t)n_rows * D)
-                                                     : sc.get<float>((size_t)n_rows * D);
-  if (p.keep_exact || p.rescore_r > 0) ix->master = master;
+  const bool split_rescore = p.rescore_r > 0 && p.storage == GIFT_BF16;
+  const bool need_master = p.keep_exact || (p.rescore_r > 0 && !split_rescore);
+  float* master = need_master ? ix->alloc<float>((size_t)n_rows * D) : sc.get<float>((size_t)n_rows * D);
+  if (need_master) ix->master = master;
+  ix->d_err = ix->alloc<int>(1);
+  GIFT_CUDA(cudaMemsetAsync(ix->d_err, 0, sizeof(int), s));
   GIFT_CUDA(cudaMemcpyAsync(master, db_feats, (size_t)n_rows * D * 4, cudaMemcpyDefault, s));
   ix->row_inv = ix->alloc<float>(n_rows);
   launch_row_invnorm(master, n_rows, D, ix->row_inv, s);
@@ -398,7 +427,7 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
 
   // database codes (one assignment per view)
   ix->db_codes = ix->alloc<int32_t>(n_rows);
-  assign_codes(*ix, master, n_rows, 1, ix->db_codes, sc, s);
+  assign_codes(*ix, master, n_rows, 1, ix->db_codes, sc, s, ix->row_inv);
 
   // F-IF: stable sort of rows by code -> lists in (shape, view) order
   ix->list_row = ix->alloc<int32_t>(n_rows);
@@ -441,7 +470,9 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
 
   // list-ordered feature store
   const size_t eb = dtype_bytes(p.storage);
-  ix->list_feat = ix->alloc<uint8_t>((size_t)n_rows * D * eb);
+  ix->list_rows_alloc = n_rows + 256;  // one TMA box of padding rows
+  ix->list_feat = ix->alloc<uint8_t>((size_t)ix->list_rows_alloc * D * eb);
+  GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix->list_feat + (size_t)n_rows * D * eb, 0, (size_t)256 * D * eb, s));
   ix->list_scale = ix->alloc<float>(n_rows);
   const unsigned pg = (unsigned)cdiv(n_rows, 8);
   switch (p.storage) {
@@ -459,6 +490,21 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
       break;
   }
   GIFT_LAUNCHED("k_pack_lists");
+  if (split_rescore) {
+    ix->list_lo = ix->alloc<__nv_bfloat16>((size_t)ix->list_rows_alloc * D);
+    GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_lo + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
+    k_pack_lo<<<pg, 256, 0, s>>>(master, ix->list_row, n_rows, D, (__nv_bfloat16*)ix->list_lo);
+    GIFT_LAUNCHED("k_pack_lo");
+  }
+  if (p.keep_exact) {
+    // shape-ordered two-part BF16 copy for the exact match on the tensor cores
+    ix->ex_rows = n_rows + 128;
+    ix->ex_hi = ix->alloc<__nv_bfloat16>((size_t)ix->ex_rows * D);
+    ix->ex_lo = ix->alloc<__nv_bfloat16>((size_t)ix->ex_rows * D);
+    GIFT_CUDA(cudaMemsetAsync(ix->ex_hi + (size_t)n_rows * D, 0, (size_t)128 * D * 2, s));
+    GIFT_CUDA(cudaMemsetAsync(ix->ex_lo + (size_t)n_rows * D, 0, (size_t)128 * D * 2, s));
+    split_rows_bf16(master, n_rows, D, ix->ex_hi, ix->ex_lo, s);
+  }
   GIFT_CUDA(cudaStreamSynchronize(s));
   ix->max_runs = h_stats[0];
   ix->max_list = h_stats[1];
@@ -539,15 +585,14 @@ gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q
     int32_t* oid = gift::stage_out(out_ids, (size_t)B * topk, sc, outs);
     float* osc = gift::stage_out(out_scores, (size_t)B * topk, sc, outs);
     if (mode == GIFT_MATCH_EXACT) {
-      if (!ix.master) gift::fail(GIFT_EUNSUPPORTED, "exact match needs keep_exact");
+      if (!ix.ex_hi) gift::fail(GIFT_EUNSUPPORTED, "exact match needs keep_exact");
       int32_t* d_qoff = sc.get<int32_t>(B + 1);
       GIFT_CUDA(cudaMemcpyAsync(d_qoff, h.data(), (B + 1) * 4, cudaMemcpyHostToDevice, stream));
       float* q_inv = sc.get<float>(nv);
       gift::launch_row_invnorm(q, nv, D, q_inv, stream);
       tm.mark(gift::ST_SCAN);
       float* S = sc.get<float>((size_t)B * ix.prm.n_shapes);
-      gift::segmax_scores(q, q_inv, nv, ix.master, ix.row_inv, ix.prm.n_shapes, ix.prm.views_per_shape, D, d_qoff,
-                          h, B, S, nullptr, sc, stream);
+      gift::exact_scores_tc(ix, q, q_inv, nv, d_qoff, h, B, S, sc, stream);
       tm.mark(gift::ST_TOPK);
       gift::topk_rows_f32(S, B, ix.prm.n_shapes, topk, oid, osc, sc, stream);
     } else if (mode == GIFT_MATCH_FIF) {

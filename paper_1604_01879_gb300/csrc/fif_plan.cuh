@@ -30,6 +30,9 @@ struct FifPlan {
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s);
 void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
               const int32_t* cand_sorted, int R, cudaStream_t s);
+// tcgen05 scan of a BF16 store (rescore: two-part BF16, candidates only)
+void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
+                 int R, Scratch& sc, cudaStream_t s);
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
                  const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s);
 

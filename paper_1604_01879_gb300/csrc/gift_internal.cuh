@@ -59,6 +59,9 @@ struct Index {
   float* codebook = nullptr;   // [K, D]
   float* cb_half_sq = nullptr; // [K]  0.5 * ||b_k||^2
   float cb_max_norm = 0.f;
+  __nv_bfloat16* cb_hi = nullptr;  // [cb_rows_alloc, D] two-part BF16 codebook (+ padding rows)
+  __nv_bfloat16* cb_lo = nullptr;
+  int64_t cb_rows_alloc = 0;
 
   // database
   float* master = nullptr;     // [n_rows, D] FP32 views (keep_exact)
@@ -71,6 +74,13 @@ struct Index {
   int32_t* list_row = nullptr;   // [n_rows] row of each entry (list order)
   int32_t* list_shape = nullptr; // [n_rows]
   void* list_feat = nullptr;     // [n_rows, D] in storage dtype
+  void* list_lo = nullptr;       // [n_rows, D] BF16 residual x - bf16(x) (BF16 store with rescore)
+  int64_t list_rows_alloc = 0;   // rows of list_feat / list_lo including padding
+
+  // exact match: shape-ordered two-part BF16 copy of the views (+ padding rows)
+  __nv_bfloat16* ex_hi = nullptr;
+  __nv_bfloat16* ex_lo = nullptr;
+  int64_t ex_rows = 0;
   float* list_scale = nullptr;   // [n_rows] factor turning a stored dot into a cosine
   int32_t* entry_run = nullptr;  // [n_rows] run index within its list
   int32_t* nruns = nullptr;      // [K]
@@ -89,6 +99,8 @@ struct Index {
   uint32_t* sif_mem = nullptr;   // [N*k1]
   uint64_t* sif_card = nullptr;  // [N]
   int32_t max_sif_entry = 0;
+
+  int* d_err = nullptr;          // device error flag set by bounded waits (0 = none)
 
   size_t device_bytes = 0;
   std::vector<void*> owned;
@@ -125,9 +137,16 @@ void bin_offsets(const int32_t* sorted_keys, int64_t n, int32_t nbins, int64_t* 
 void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 
 // k_assign.cu
-// codes[v*ma + a] = a-th nearest codeword by (squared distance, index).
+// codes[v*ma + a] = a-th nearest codeword by (squared distance, index);
+// x_inv (optional) holds 1/||x|| of the rows.
 void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes,
-                  Scratch& sc, cudaStream_t s);
+                  Scratch& sc, cudaStream_t s, const float* x_inv = nullptr);
+// hi = bf16(x), lo = bf16(x - hi) of a row-major [n, D] FP32 matrix
+void split_rows_bf16(const float* X, int64_t n, int D, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+
+// k_exact_tc.cu: Eq. 3 over all N shapes on the tensor cores
+void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
+                     const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);
 
 
 // k_exact.cu

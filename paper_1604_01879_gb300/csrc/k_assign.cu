@@ -1,39 +1,126 @@
 // Quantiser c(x) = argmin_k ||x - b_k||^2 with multiple assignment (Sec. 2.3).
 //
-// Stage 1 (coarse): score_k = x.b_k - ||b_k||^2 / 2 for all codewords by a
-// tile GEMM; argmax of the score is argmin of the distance.
-// Stage 2 (refine, one warp per row): every codeword whose coarse score lies
-// within twice the coarse error bound of the ma-th best coarse score is a
-// candidate; candidates get their exact squared distance in two-float (~2^-44
-// relative) arithmetic and the ma smallest by (distance, index) are kept. The
-// bound makes the candidate set contain the true ma nearest codewords, so the
-// result agrees with an exact evaluation except where distances tie to ~1e-13.
+// Coarse stage (tensor cores): score_k = x.b_k - ||b_k||^2 / 2 (argmax of the
+// score is argmin of the distance) for 128 rows x all codewords per work item,
+// from two-part BF16 operands (x = hi + lo, three products, FP32 accumulate),
+// codewords in chunks of 256 columns. The epilogue keeps each row's 16 best
+// coarse scores; every codeword whose coarse score lies within 2E of the
+// ma-th best is a candidate, where E bounds the coarse error:
+//   E = 2^-12 (||x|| max_k ||b_k|| + max_k ||b_k||^2 / 2),
+// about five times the representation bound of the split (3 * 2^-16 relative
+// per product) plus the measured accumulation error. When all 16 kept scores
+// are candidates the row is marked for a full exact pass.
+// Refine stage (CUDA cores, one warp per row): exact squared distances of the
+// candidates in two-float (~2^-44 relative) arithmetic, ma smallest by
+// (distance, index). Results equal an exact evaluation except where
+// distances tie to ~1e-13.
 #include "gift_internal.cuh"
-#include "sgemm_nt.cuh"
+#include "tc_engine.cuh"
 
 namespace gift {
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxCand = 32;
+constexpr int kT = 16;  // coarse candidates kept per row
 
-struct EpiScores {
-  float* C;  // [M, N]
-  int64_t M, N;
+struct AssignPolicy {
+  static constexpr int TN = 256, NBUF = 2, STAGES = 2, SPLIT = 3;
+  static constexpr int kWarpSmem = TN * 4;
+  int64_t n;          // rows
+  int K;
+  int nkb;
+  int ma;
+  const float* x_inv; // [n] 1/||x||
   const float* half_sq;
-  __device__ __forceinline__ void operator()(int64_t m0, int64_t n0, const SgemmFrag& f,
-                                             float (&acc)[8][8]) const {
+  float bmax;
+  int32_t* cand;      // [n, kT]
+  int32_t* cand_cnt;  // [n]; -1 = refine every codeword
+  struct Item {
+    int64_t r0;
+    int nr;
+  };
+  struct Ctx {
+    float val[kT];
+    int idx[kT];
+  };
+  __device__ __forceinline__ int64_t total() const { return cdiv(n, tc::kTM); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    Item it;
+    it.r0 = item * tc::kTM;
+    it.nr = (int)min((int64_t)tc::kTM, n - it.r0);
+    return it;
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return (K + TN - 1) / TN; }
+  __device__ __forceinline__ void chunk(const Item&, int c, int& br, int& kb0, int& kb1) const {
+    br = c * TN;
+    kb0 = 0;
+    kb1 = nkb;
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
+  __device__ __forceinline__ void epi_begin(const Item&, Ctx& x, int, int, uint8_t*) const {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int64_t m = m0 + f.row(i);
-      if (m >= M) continue;
+    for (int t = 0; t < kT; ++t) {
+      x.val[t] = -INFINITY;
+      x.idx[t] = 0x7fffffff;
+    }
+  }
+  __device__ __forceinline__ void epi_chunk(const Item&, int c, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
+    float* hs = reinterpret_cast<float*>(ws);
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < TN; j += 32) {
+      const int k = c * TN + j;
+      hs[j] = k < K ? half_sq[k] : INFINITY;
+    }
+    __syncwarp();
+    const int npieces = min(TN, K - c * TN + 31) >> 5;
+    for (int pc = 0; pc < npieces; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
+      tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t n = n0 + f.col(j);
-        if (n < N) C[m * N + n] = acc[i][j] - half_sq[n];
+      for (int j = 0; j < 32; ++j) {
+        const float s = __uint_as_float(r[j]) - hs[pc * 32 + j];
+        if (s > x.val[kT - 1]) {  // strict: an equal later index never displaces an earlier one
+          x.val[kT - 1] = s;
+          x.idx[kT - 1] = c * TN + pc * 32 + j;
+#pragma unroll
+          for (int t = kT - 1; t > 0; --t) {
+            if (x.val[t] > x.val[t - 1]) {
+              const float tv = x.val[t];
+              x.val[t] = x.val[t - 1];
+              x.val[t - 1] = tv;
+              const int ti = x.idx[t];
+              x.idx[t] = x.idx[t - 1];
+              x.idx[t - 1] = ti;
+            }
+          }
+        }
       }
     }
+    __syncwarp();
+  }
+  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int m, uint8_t*) const {
+    if (m >= it.nr) return;
+    const int64_t row = it.r0 + m;
+    const float xi = x_inv[row];
+    float thr = x.val[0];
+#pragma unroll
+    for (int t = 0; t < kT; ++t)
+      if (t == ma - 1) thr = x.val[t];
+    const float xn = xi > 0.f ? 1.0001f / xi : 0.f;
+    const float E = 2.44140625e-4f * (xn * bmax + 0.5f * bmax * bmax) + 1e-30f;
+    const float lim = thr - 2.f * E;
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      if (x.val[t] >= lim && x.idx[t] != 0x7fffffff) {
+        cand[row * kT + cnt] = x.idx[t];
+        ++cnt;
+      }
+    }
+    const bool overflow = (cnt == kT && K > kT) || xi == 0.f;
+    cand_cnt[row] = overflow ? -1 : cnt;
   }
 };
 
@@ -44,8 +131,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // exact-ish ||x - b||^2 as a normalised two-float (hi, lo), warp cooperative
-__device__ void dist_df(const float* __restrict__ x, const float* __restrict__ b, int D, int lane,
-                        float& ohi, float& olo) {
+__device__ void dist_df(const float* __restrict__ x, const float* __restrict__ b, int D, int lane, float& ohi,
+                        float& olo) {
   float hi = 0.f, lo = 0.f;
   for (int d = lane * 4; d < D; d += 128) {
     const float4 xv = *reinterpret_cast<const float4*>(x + d);
@@ -55,10 +142,10 @@ __device__ void dist_df(const float* __restrict__ x, const float* __restrict__ b
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float s, e;
-      two_sum(xs[c], -bs[c], s, e);         // x - b = s + e exactly
+      two_sum(xs[c], -bs[c], s, e);  // x - b = s + e exactly
       const float p = s * s;
-      float pe = fmaf(s, s, -p);            // s^2 = p + pe exactly
-      pe = fmaf(2.f * s, e, pe);            // + 2 s e (e^2 is below 2^-48 s^2)
+      float pe = fmaf(s, s, -p);     // s^2 = p + pe exactly
+      pe = fmaf(2.f * s, e, pe);     // + 2 s e (e^2 is below 2^-48 s^2)
       float t, te;
       two_sum(hi, p, t, te);
       hi = t;
@@ -86,135 +173,121 @@ __device__ __forceinline__ bool df_less(float ah, float al, int ak, float bh, fl
   return ak < bk;
 }
 
-// insert (h, l, k) into an ascending list of length ma (registers)
-__device__ __forceinline__ void keep_best(float (&H)[GIFT_MAX_MA], float (&L)[GIFT_MAX_MA],
-                                          int (&Kx)[GIFT_MAX_MA], int ma, float h, float l, int k) {
-  if (!df_less(h, l, k, H[ma - 1], L[ma - 1], Kx[ma - 1])) return;
-  int pos = ma - 1;
-#pragma unroll
-  for (int a = GIFT_MAX_MA - 1; a > 0; --a) {
-    if (a <= pos && a - 1 < ma && df_less(h, l, k, H[a - 1], L[a - 1], Kx[a - 1])) {
-      H[a] = H[a - 1];
-      L[a] = L[a - 1];
-      Kx[a] = Kx[a - 1];
-      pos = a - 1;
-    }
-  }
-  H[pos] = h;
-  L[pos] = l;
-  Kx[pos] = k;
-}
-
 __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__ X, int64_t n, int D,
-                                                       const float* __restrict__ scores, int K,
-                                                       const float* __restrict__ cb, int ma,
-                                                       float cb_max_norm, int32_t* __restrict__ codes,
-                                                       int64_t row0) {
-  __shared__ int cand_s[8][kMaxCand];
+                                                       const float* __restrict__ cb, int K, int ma,
+                                                       const int32_t* __restrict__ cand,
+                                                       const int32_t* __restrict__ cand_cnt,
+                                                       int32_t* __restrict__ codes) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + w;
   if (r >= n) return;
-  const float* sr = scores + r * (int64_t)K;
   const float* x = X + r * (int64_t)D;
-
-  // ma-th best coarse score: per-lane top-ma, then ma rounds of warp max
-  float top[GIFT_MAX_MA];
-#pragma unroll
-  for (int a = 0; a < GIFT_MAX_MA; ++a) top[a] = -INFINITY;
-  for (int k = lane; k < K; k += 32) {
-    float v = sr[k];
-#pragma unroll
-    for (int a = 0; a < GIFT_MAX_MA; ++a) {
-      if (a < ma && v > top[a]) {
-        const float t = top[a];
-        top[a] = v;
-        v = t;
-      }
-    }
-  }
-  float thr = -INFINITY;
-  int head = 0;
-  for (int a = 0; a < ma; ++a) {
-    float mine = head < ma ? top[0] : -INFINITY;
-    float m = mine;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    thr = m;
-    const unsigned who = __ballot_sync(kFull, mine == m && head < ma);
-    if (lane == __ffs(who) - 1) {
-#pragma unroll
-      for (int b = 0; b + 1 < GIFT_MAX_MA; ++b) top[b] = top[b + 1];
-      top[GIFT_MAX_MA - 1] = -INFINITY;
-      ++head;
-    }
-  }
-
-  // coarse error bound E: recursive FMA summation of D products plus the
-  // norm term; candidates lie within 2E of the ma-th best coarse score.
-  float xx = 0.f;
-  for (int d = lane; d < D; d += 32) xx = fmaf(x[d], x[d], xx);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(kFull, xx, o);
-  const float xn = sqrtf(xx) * 1.0001f;
-  const float u = 5.9604645e-08f;  // 2^-24
-  const float gam = (float)(D + 2) * u * 1.01f;
-  const float E = gam * (xn * cb_max_norm + 0.5f * cb_max_norm * cb_max_norm) + 1e-30f;
-  const float lim = thr - 2.f * E;
-
-  // collect candidates in index order
-  int cnt = 0;
-  bool overflow = false;
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    const int k = k0 + lane;
-    const bool c = k < K && sr[k] >= lim;
-    const unsigned m = __ballot_sync(kFull, c);
-    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-    if (c && pos < kMaxCand) cand_s[w][pos] = k;
-    cnt += __popc(m);
-  }
-  __syncwarp();
-  if (cnt > kMaxCand) overflow = true;
-
-  float H[GIFT_MAX_MA], L[GIFT_MAX_MA];
+  const int cnt = cand_cnt[r];
+  const int ncheck = cnt < 0 ? K : cnt;
+  float H[GIFT_MAX_MA], Lo[GIFT_MAX_MA];
   int Kx[GIFT_MAX_MA];
 #pragma unroll
   for (int a = 0; a < GIFT_MAX_MA; ++a) {
     H[a] = INFINITY;
-    L[a] = 0.f;
+    Lo[a] = 0.f;
     Kx[a] = 0x7fffffff;
   }
-  const int ncheck = overflow ? K : cnt;
   for (int c = 0; c < ncheck; ++c) {
-    const int k = overflow ? c : cand_s[w][c];
+    const int k = cnt < 0 ? c : cand[r * kT + c];
     float h, l;
     dist_df(x, cb + (int64_t)k * D, D, lane, h, l);
-    keep_best(H, L, Kx, ma, h, l, k);
+    // insert into the ascending list of the ma best (registers, unrolled)
+    if (df_less(h, l, k, H[GIFT_MAX_MA - 1], Lo[GIFT_MAX_MA - 1], Kx[GIFT_MAX_MA - 1])) {
+      H[GIFT_MAX_MA - 1] = h;
+      Lo[GIFT_MAX_MA - 1] = l;
+      Kx[GIFT_MAX_MA - 1] = k;
+#pragma unroll
+      for (int t = GIFT_MAX_MA - 1; t > 0; --t) {
+        if (df_less(H[t], Lo[t], Kx[t], H[t - 1], Lo[t - 1], Kx[t - 1])) {
+          const float th = H[t], tl = Lo[t];
+          const int tk = Kx[t];
+          H[t] = H[t - 1];
+          Lo[t] = Lo[t - 1];
+          Kx[t] = Kx[t - 1];
+          H[t - 1] = th;
+          Lo[t - 1] = tl;
+          Kx[t - 1] = tk;
+        }
+      }
+    }
   }
   if (lane < ma) {
     int out = Kx[0];
 #pragma unroll
     for (int a = 1; a < GIFT_MAX_MA; ++a)
       if (a == lane) out = Kx[a];
-    codes[(row0 + r) * ma + lane] = out;
+    codes[r * ma + lane] = out;
   }
+}
+
+// hi = bf16(x), lo = bf16(x - hi), row-major [n, D]
+__global__ void k_split_rows(const float* __restrict__ X, int64_t n, int D, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // index of a float4
+  if (i >= n * (D / 4)) return;
+  const float4 v = reinterpret_cast<const float4*>(X)[i];
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+  const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+  reinterpret_cast<__nv_bfloat162*>(hi)[2 * i] = a;
+  reinterpret_cast<__nv_bfloat162*>(hi)[2 * i + 1] = b;
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  reinterpret_cast<__nv_bfloat162*>(lo)[2 * i] = __floats2bfloat162_rn(v.x - fa.x, v.y - fa.y);
+  reinterpret_cast<__nv_bfloat162*>(lo)[2 * i + 1] = __floats2bfloat162_rn(v.z - fb.x, v.w - fb.y);
 }
 
 }  // namespace
 
-void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes, Scratch& sc,
-                  cudaStream_t s) {
+void split_rows_bf16(const float* X, int64_t n, int D, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t n4 = n * (D / 4);
+  k_split_rows<<<(unsigned)cdiv(n4, 256), 256, 0, s>>>(X, n, D, hi, lo);
+  GIFT_LAUNCHED("k_split_rows");
+}
+
+void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes, Scratch& sc, cudaStream_t s,
+                  const float* x_inv) {
   if (n <= 0) return;
   const int K = ix.prm.n_codewords, D = ix.prm.dim;
   GIFT_REQUIRE(ma >= 1 && ma <= GIFT_MAX_MA && ma <= K, "multiple assignment must be in [1, min(8, K)]");
-  // rows per chunk: the coarse score block stays under 1 GiB
-  const int64_t chunk = std::max<int64_t>(128, std::min<int64_t>(n, ((int64_t)1 << 28) / K / 128 * 128));
-  float* scores = sc.get<float>((size_t)std::min(chunk, n) * K);
+  const int64_t chunk = std::min<int64_t>(n, 131072);
+  const int64_t rows_alloc = chunk + tc::kTM;  // one box of padding rows
+  __nv_bfloat16* hi = sc.get<__nv_bfloat16>((size_t)rows_alloc * D);
+  __nv_bfloat16* lo = sc.get<__nv_bfloat16>((size_t)rows_alloc * D);
+  int32_t* cand = sc.get<int32_t>((size_t)chunk * kT);
+  int32_t* cnt = sc.get<int32_t>(chunk);
+  float* inv = nullptr;
+  if (!x_inv) {
+    inv = sc.get<float>(n);
+    launch_row_invnorm(X, n, D, inv, s);
+    x_inv = inv;
+  }
+  const CUtensorMap tB = make_tmap_bf16(ix.cb_hi, ix.cb_rows_alloc, D, AssignPolicy::TN);
+  const CUtensorMap tB2 = make_tmap_bf16(ix.cb_lo, ix.cb_rows_alloc, D, AssignPolicy::TN);
+  const int sms = device_sm_count();
   for (int64_t r0 = 0; r0 < n; r0 += chunk) {
     const int64_t m = std::min(chunk, n - r0);
-    EpiScores epi{scores, m, K, ix.cb_half_sq};
-    launch_sgemm_nt(X + r0 * D, m, ix.codebook, K, D, epi, 0, s);
-    k_assign_refine<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(X + r0 * D, m, D, scores, K, ix.codebook, ma,
-                                                          ix.cb_max_norm, codes, r0);
+    split_rows_bf16(X + r0 * D, m, D, hi, lo, s);
+    AssignPolicy p;
+    p.n = m;
+    p.K = K;
+    p.nkb = (int)cdiv(D, tc::kTK);
+    p.ma = ma;
+    p.x_inv = x_inv + r0;
+    p.half_sq = ix.cb_half_sq;
+    p.bmax = ix.cb_max_norm;
+    p.cand = cand;
+    p.cand_cnt = cnt;
+    const CUtensorMap tA = make_tmap_bf16(hi, rows_alloc, D, tc::kTM);
+    const CUtensorMap tA2 = make_tmap_bf16(lo, rows_alloc, D, tc::kTM);
+    const int grid = (int)std::min<int64_t>(sms, cdiv(m, tc::kTM));
+    tc::launch_engine(tA, tB, tA2, tB2, p, ix.d_err, grid, s);
+    k_assign_refine<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(X + r0 * D, m, D, ix.codebook, K, ma, cand, cnt,
+                                                          codes + r0 * ma);
     GIFT_LAUNCHED("k_assign_refine");
   }
 }

@@ -1,0 +1,155 @@
+// Exact set-to-set match (Eq. 3) on the tensor cores:
+// S(x_q, x_p) = (1/|V(x_q)|) sum_i max_j s(q_i, p_j), s the cosine.
+//
+// Work item: (128 database views = columns, 128 query views = rows); items run
+// column-tile-major so CTAs working at the same time share the database tile.
+// Operands are two-part BF16 (x = hi + lo, three products) with the reduction
+// in four chunks summed in FP32 by the epilogue, which scales by the inverse
+// norms and reduces each row over every run of N_v columns of one shape,
+// folding (max, first argmax) into a per-(query view, shape) cell with a
+// 64-bit atomicMax; a second kernel sums the cells of each query's views.
+#include "gift_internal.cuh"
+#include "segmax.cuh"
+#include "tc_engine.cuh"
+
+namespace gift {
+
+namespace {
+
+constexpr int kChunks = 4;
+
+struct ExactPolicy {
+  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3;
+  static constexpr int kWarpSmem = TN * 4;
+  int64_t rows;        // query views in this pass
+  int64_t ncols;       // database views N * N_v
+  int64_t n_rt;        // row tiles
+  int nv;              // views per shape
+  int64_t n_shapes;
+  int nkb;
+  const float* q_inv;  // [rows]
+  const float* r_inv;  // [ncols]
+  unsigned long long* cell;  // [rows, n_shapes]
+  struct Item {
+    int64_t r0, c0;
+    int nr, nc;
+  };
+  struct Ctx {
+    float sum[TN];
+  };
+  __device__ __forceinline__ int64_t total() const { return n_rt * cdiv(ncols, TN); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    Item it;
+    const int64_t ct = item / n_rt, rt = item % n_rt;
+    it.r0 = rt * tc::kTM;
+    it.c0 = ct * TN;
+    it.nr = (int)min((int64_t)tc::kTM, rows - it.r0);
+    it.nc = (int)min((int64_t)TN, ncols - it.c0);
+    return it;
+  }
+  // never an empty chunk: each chunk must write its own accumulator
+  __device__ __forceinline__ int nchunks(const Item&) const { return nkb < kChunks ? nkb : kChunks; }
+  __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
+    br = (int)it.c0;
+    const int nch = nkb < kChunks ? nkb : kChunks;
+    kb0 = (int)((int64_t)nkb * c / nch);
+    kb1 = (int)((int64_t)nkb * (c + 1) / nch);
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int, int, uint8_t* ws) const {
+    float* ri = reinterpret_cast<float*>(ws);
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < TN; c += 32) ri[c] = c < it.nc ? r_inv[it.c0 + c] : 0.f;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) x.sum[j] = 0.f;
+  }
+  __device__ __forceinline__ void epi_chunk(const Item&, int, uint32_t taddr, Ctx& x, int, uint8_t*) const {
+#pragma unroll
+    for (int pc = 0; pc < TN / 32; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
+    }
+  }
+  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int m, uint8_t* ws) const {
+    if (m >= it.nr) return;
+    const float* ri = reinterpret_cast<const float*>(ws);
+    const int64_t row = it.r0 + m;
+    const float qi = q_inv[row];
+    unsigned long long* crow = cell + row * n_shapes;
+    int64_t cur = -1;
+    float best = 0.f;
+    int bj = 0;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      if (c < it.nc) {
+        const int64_t n = it.c0 + c;
+        const int64_t shape = n / nv;
+        const int j = (int)(n - shape * nv);
+        const float v = x.sum[c] * qi * ri[c];
+        if (shape != cur) {
+          if (cur >= 0)
+            atomicMax(crow + cur, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
+          cur = shape;
+          best = v;
+          bj = j;
+        } else if (v > best) {
+          best = v;
+          bj = j;
+        }
+      }
+    }
+    if (cur >= 0) atomicMax(crow + cur, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
+  }
+};
+
+}  // namespace
+
+void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
+                     const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s) {
+  const int D = ix.prm.dim, Nv = ix.prm.views_per_shape;
+  const int64_t N = ix.prm.n_shapes;
+  const int64_t ncols = ix.n_rows;
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 27) / N);  // cell block <= 1 GiB
+  // every TMA source keeps one box of padding rows past its data
+  const int64_t qrows = nv + tc::kTM;
+  __nv_bfloat16* hi = sc.get<__nv_bfloat16>((size_t)qrows * D);
+  __nv_bfloat16* lo = sc.get<__nv_bfloat16>((size_t)qrows * D);
+  split_rows_bf16(q, nv, D, hi, lo, s);
+  unsigned long long* cell = nullptr;
+  int64_t cell_rows = 0;
+  const CUtensorMap tB = make_tmap_bf16(ix.ex_hi, ix.ex_rows, D, ExactPolicy::TN);
+  const CUtensorMap tB2 = make_tmap_bf16(ix.ex_lo, ix.ex_rows, D, ExactPolicy::TN);
+  const int sms = device_sm_count();
+  int32_t b0 = 0;
+  while (b0 < B) {
+    int32_t b1 = b0 + 1;
+    while (b1 < B && (int64_t)(h_qoff[b1 + 1] - h_qoff[b0]) <= cap) ++b1;
+    const int64_t v0 = h_qoff[b0], rows = h_qoff[b1] - v0;
+    if (rows > cell_rows) {
+      cell = sc.get<unsigned long long>((size_t)rows * N);
+      cell_rows = rows;
+    }
+    GIFT_CUDA(cudaMemsetAsync(cell, 0, (size_t)rows * N * 8, s));
+    ExactPolicy p;
+    p.rows = rows;
+    p.ncols = ncols;
+    p.n_rt = cdiv(rows, tc::kTM);
+    p.nv = Nv;
+    p.n_shapes = N;
+    p.nkb = (int)cdiv(D, tc::kTK);
+    p.q_inv = q_inv + v0;
+    p.r_inv = ix.row_inv;
+    p.cell = cell;
+    const CUtensorMap tA = make_tmap_bf16(hi + v0 * D, qrows - v0, D, tc::kTM);
+    const CUtensorMap tA2 = make_tmap_bf16(lo + v0 * D, qrows - v0, D, tc::kTM);
+    const int grid = (int)std::min<int64_t>(sms, p.n_rt * cdiv(ncols, ExactPolicy::TN));
+    tc::launch_engine(tA, tB, tA2, tB2, p, ix.d_err, grid, s);
+    segmax_reduce(cell, N, d_qoff, b0, b1 - b0, (int32_t)v0, S, nullptr, s);
+    b0 = b1;
+  }
+}
+
+}  // namespace gift

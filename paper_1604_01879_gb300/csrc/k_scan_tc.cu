@@ -1,0 +1,340 @@
+// Posting-list scan and candidate rescore on the 5th-generation tensor cores
+// (Eq. 4, Fig. 2), as policies of the tcgen05 engine.
+//
+// Work item: (list k, a tile of consecutive entries of list k, 128
+// consecutive query slots of bucket k). Rows of the MMA (TMEM lanes) are
+// query slots, columns are list entries; list entries of one shape are
+// consecutive, so each epilogue thread walks its row of columns in order,
+// keeps the max cosine of the current shape run (floored at 0) and folds
+// every run maximum into the per-(slot, run) table with atomicMax on the
+// float bits.
+//
+// Scan: BF16 store, one product per k-block, 256 entries per tile.
+// Rescore: two-part BF16 operands (x = hi + lo) and three products, the
+// reduction split in four chunks accumulated in separate TMEM buffers and
+// summed in FP32 by the epilogue; only runs of the query's top-R candidate
+// shapes are kept.
+#include "fif_plan.cuh"
+#include "gift_internal.cuh"
+#include "tc_engine.cuh"
+
+namespace gift {
+
+namespace {
+
+constexpr int kScanTN = 256;
+constexpr int kRescTN = 128;
+constexpr int kRescChunks = 4;
+
+struct ListItem {
+  int64_t e0, s0;
+  int ne, ns;
+};
+
+struct ListSched {
+  const int64_t* woff;      // [K+1] work items per list (exclusive), woff[K] = total
+  int K;
+  const int64_t* boff;      // [K+1] slots per codeword
+  const int64_t* list_off;  // [K+1]
+  int nkb;
+  __device__ __forceinline__ int64_t total_items() const { return woff[K]; }
+  template <int TN>
+  __device__ __forceinline__ ListItem decode_list(int64_t item) const {
+    int lo = 0, hi = K;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (woff[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int k = lo;
+    const int64_t L = list_off[k + 1] - list_off[k];
+    const int64_t M = boff[k + 1] - boff[k];
+    const int64_t nts = cdiv(M, tc::kTM);
+    const int64_t local = item - woff[k];
+    const int64_t te = local / nts, ts = local % nts;
+    ListItem it;
+    it.e0 = list_off[k] + te * TN;
+    it.ne = (int)min((int64_t)TN, L - te * TN);
+    it.s0 = boff[k] + ts * tc::kTM;
+    it.ns = (int)min((int64_t)tc::kTM, M - ts * tc::kTM);
+    return it;
+  }
+};
+
+struct SlotInfo {
+  const int64_t* runbase;    // [nslots]
+  const int32_t* slot_view;  // [nslots]
+  const int32_t* vquery;     // [nv]
+  const float* q_inv;        // [nv]
+  const float* scale;        // [n_rows] list-ordered cosine factor
+  const int32_t* entry_run;  // [n_rows]
+  const int32_t* list_shape; // [n_rows]
+  uint32_t* table;
+};
+
+__device__ __forceinline__ bool is_candidate(const int32_t* c, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (c[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && c[lo] == key;
+}
+
+struct RowCtx {
+  int64_t rb;
+  float qi;
+  int32_t qq;
+  bool valid;
+};
+
+// per-warp shared copy of the tile's entry metadata
+template <int TN>
+__device__ __forceinline__ void load_entry_meta(const SlotInfo& si, const ListItem& it, uint8_t* ws) {
+  int* e_run = reinterpret_cast<int*>(ws);
+  float* e_scale = reinterpret_cast<float*>(e_run + TN);
+  int* e_shape = e_run + 2 * TN;
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < TN; c += 32) {
+    if (c < it.ne) {
+      const int64_t e = it.e0 + c;
+      e_run[c] = si.entry_run[e];
+      e_scale[c] = si.scale[e];
+      e_shape[c] = si.list_shape[e];
+    } else {
+      e_run[c] = -1;
+      e_scale[c] = 0.f;
+      e_shape[c] = 0;
+    }
+  }
+}
+
+__device__ __forceinline__ void load_row(const SlotInfo& si, const ListItem& it, int m, RowCtx& r) {
+  r.valid = m < it.ns;
+  r.rb = 0;
+  r.qi = 0.f;
+  r.qq = 0;
+  if (r.valid) {
+    const int64_t s = it.s0 + m;
+    r.rb = si.runbase[s];
+    const int32_t v = si.slot_view[s];
+    r.qi = si.q_inv[v];
+    r.qq = si.vquery[v];
+  }
+}
+
+// ---------------------------------------------------------------- scan policy
+struct ScanPolicy : ListSched {
+  static constexpr int TN = kScanTN, NBUF = 2, STAGES = 4, SPLIT = 1;
+  static constexpr int kWarpSmem = TN * 12;
+  SlotInfo si;
+  using Item = ListItem;
+  struct Ctx {
+    RowCtx row;
+    int cur_run;
+    float cur_max;
+  };
+  __device__ __forceinline__ int64_t total() const { return total_items(); }
+  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
+  __device__ __forceinline__ int nchunks(const Item&) const { return 1; }
+  __device__ __forceinline__ void chunk(const Item& it, int, int& br, int& kb0, int& kb1) const {
+    br = (int)it.e0;
+    kb0 = 0;
+    kb1 = nkb;
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.s0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int, uint8_t* ws) const {
+    load_entry_meta<TN>(si, it, ws);
+    load_row(si, it, m, x.row);
+    x.cur_run = -1;
+    x.cur_max = 0.f;
+  }
+  __device__ __forceinline__ void flush(const Ctx& x) const {
+    if (x.row.valid && x.cur_run >= 0 && x.cur_max > 0.f)
+      atomicMax(si.table + x.row.rb + x.cur_run, __float_as_uint(x.cur_max));
+  }
+  __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
+    const int* e_run = reinterpret_cast<const int*>(ws);
+    const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
+    const int npieces = (it.ne + 31) >> 5;
+    for (int pc = 0; pc < npieces; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = pc * 32 + j;
+        const int run = e_run[c];
+        const float v = fmaxf(__uint_as_float(r[j]) * x.row.qi * e_scale[c], 0.f);
+        if (run != x.cur_run) {
+          flush(x);
+          x.cur_run = run;
+          x.cur_max = v;
+        } else {
+          x.cur_max = fmaxf(x.cur_max, v);
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ void epi_end(const Item&, Ctx& x, int, uint8_t*) const { flush(x); }
+};
+
+// ---------------------------------------------------------------- rescore policy
+struct RescorePolicy : ListSched {
+  static constexpr int TN = kRescTN, NBUF = 4, STAGES = 3, SPLIT = 3;
+  static constexpr int kWarpSmem = TN * 12;
+  SlotInfo si;
+  const int32_t* cand;  // [B, R] candidate ids sorted ascending
+  int R;
+  using Item = ListItem;
+  struct Ctx {
+    RowCtx row;
+    float sum[TN];
+  };
+  __device__ __forceinline__ int64_t total() const { return total_items(); }
+  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
+  // never an empty chunk: each chunk must write its own accumulator
+  __device__ __forceinline__ int nchunks(const Item&) const { return nkb < kRescChunks ? nkb : kRescChunks; }
+  __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
+    br = (int)it.e0;
+    const int nch = nkb < kRescChunks ? nkb : kRescChunks;
+    kb0 = (int)((int64_t)nkb * c / nch);
+    kb1 = (int)((int64_t)nkb * (c + 1) / nch);
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.s0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int, uint8_t* ws) const {
+    load_entry_meta<TN>(si, it, ws);
+    load_row(si, it, m, x.row);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) x.sum[j] = 0.f;
+  }
+  __device__ __forceinline__ void epi_chunk(const Item&, int c, uint32_t taddr, Ctx& x, int, uint8_t*) const {
+#pragma unroll
+    for (int pc = 0; pc < TN / 32; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
+    }
+    (void)c;
+  }
+  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int, uint8_t* ws) const {
+    const int* e_run = reinterpret_cast<const int*>(ws);
+    const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
+    const int* e_shape = e_run + 2 * TN;
+    if (!x.row.valid) return;
+    const int32_t* cq = cand + (int64_t)x.row.qq * R;
+    int cur_run = -1, cur_shape = 0;
+    float cur_max = 0.f;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const int run = e_run[c];
+      const float v = fmaxf(x.sum[c] * x.row.qi * e_scale[c], 0.f);
+      if (run != cur_run) {
+        if (cur_run >= 0 && cur_max > 0.f && is_candidate(cq, R, cur_shape))
+          atomicMax(si.table + x.row.rb + cur_run, __float_as_uint(cur_max));
+        cur_run = run;
+        cur_max = v;
+        cur_shape = e_shape[c];
+      } else {
+        cur_max = fmaxf(cur_max, v);
+      }
+    }
+    if (cur_run >= 0 && cur_max > 0.f && is_candidate(cq, R, cur_shape))
+      atomicMax(si.table + x.row.rb + cur_run, __float_as_uint(cur_max));
+    (void)it;
+  }
+};
+
+// slot-ordered BF16 copies of the query views: hi = bf16(q), lo = bf16(q - hi)
+__global__ void k_slot_split(const float* __restrict__ q, const int32_t* __restrict__ slot_view, int64_t nslots,
+                             int D, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t s = blockIdx.x;
+  if (s >= nslots) return;
+  const float4* src = reinterpret_cast<const float4*>(q + (int64_t)slot_view[s] * D);
+  __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(hi + s * D);
+  __nv_bfloat162* l2 = lo ? reinterpret_cast<__nv_bfloat162*>(lo + s * D) : nullptr;
+  for (int i = threadIdx.x; i < D / 4; i += blockDim.x) {
+    const float4 v = src[i];
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    h2[2 * i] = a;
+    h2[2 * i + 1] = b;
+    if (l2) {
+      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      l2[2 * i] = __floats2bfloat162_rn(v.x - fa.x, v.y - fa.y);
+      l2[2 * i + 1] = __floats2bfloat162_rn(v.z - fb.x, v.w - fb.y);
+    }
+  }
+}
+
+__global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t* __restrict__ list_off, int K,
+                                int tn, int64_t* __restrict__ wcnt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > K) return;
+  if (k == K) {
+    wcnt[K] = 0;
+    return;
+  }
+  const int64_t M = boff[k + 1] - boff[k];
+  const int64_t L = list_off[k + 1] - list_off[k];
+  wcnt[k] = (M > 0 && L > 0) ? cdiv(L, tn) * cdiv(M, tc::kTM) : 0;
+}
+
+}  // namespace
+
+void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
+                 int R, Scratch& sc, cudaStream_t s) {
+  const int K = ix.prm.n_codewords, D = ix.prm.dim;
+  const int64_t ns = P.nslots;
+  if (ns <= 0) return;
+  const int64_t qrows = ns + tc::kTM;  // one box of padding rows
+  __nv_bfloat16* qhi = sc.get<__nv_bfloat16>((size_t)qrows * D);
+  __nv_bfloat16* qlo = rescore ? sc.get<__nv_bfloat16>((size_t)qrows * D) : nullptr;
+  k_slot_split<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, qhi, qlo);
+  GIFT_LAUNCHED("k_slot_split");
+  const int tn = rescore ? kRescTN : kScanTN;
+  int64_t* wcnt = sc.get<int64_t>(K + 1);
+  int64_t* woff = sc.get<int64_t>(K + 1);
+  k_work_count_tc<<<(unsigned)cdiv(K + 1, 256), 256, 0, s>>>(P.boff, ix.list_off, K, tn, wcnt);
+  GIFT_LAUNCHED("k_work_count_tc");
+  scan_exclusive_i64(wcnt, woff, K + 1, sc, s);
+
+  ListSched ls;
+  ls.woff = woff;
+  ls.K = K;
+  ls.boff = P.boff;
+  ls.list_off = ix.list_off;
+  ls.nkb = (int)cdiv(D, tc::kTK);
+  SlotInfo si;
+  si.runbase = P.runbase;
+  si.slot_view = P.slot_view;
+  si.vquery = P.vquery;
+  si.q_inv = P.q_inv;
+  si.scale = ix.list_scale;
+  si.entry_run = ix.entry_run;
+  si.list_shape = ix.list_shape;
+  si.table = table;
+  const int grid = device_sm_count();
+  const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
+  if (!rescore) {
+    ScanPolicy pol;
+    static_cast<ListSched&>(pol) = ls;
+    pol.si = si;
+    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy::TN);
+    tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
+  } else {
+    GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the BF16 residual store");
+    RescorePolicy pol;
+    static_cast<ListSched&>(pol) = ls;
+    pol.si = si;
+    pol.cand = cand_sorted;
+    pol.R = R;
+    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, RescorePolicy::TN);
+    const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
+    const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, RescorePolicy::TN);
+    tc::launch_engine(tA, tB, tA2, tB2, pol, ix.d_err, grid, s);
+  }
+}
+
+}  // namespace gift

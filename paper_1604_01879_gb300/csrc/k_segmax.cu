@@ -84,6 +84,14 @@ __global__ void k_segmax_reduce(const unsigned long long* __restrict__ cell, int
 
 }  // namespace
 
+void segmax_reduce(const unsigned long long* cell, int64_t n_shapes, const int32_t* d_qoff, int32_t b0, int32_t nq,
+                   int32_t view0, float* S, int16_t* argmax, cudaStream_t s) {
+  const int64_t work = (int64_t)nq * n_shapes;
+  if (work <= 0) return;
+  k_segmax_reduce<<<(unsigned)cdiv(work, 256), 256, 0, s>>>(cell, n_shapes, d_qoff, b0, nq, view0, S, argmax);
+  GIFT_LAUNCHED("k_segmax_reduce");
+}
+
 void segmax_scores(const float* A, const float* inv_a, int64_t n_views, const float* Bm,
                    const float* inv_b, int64_t n_shapes, int nv, int D, const int32_t* d_qoff,
                    const std::vector<int32_t>& h_qoff, int32_t Bq, float* S, int16_t* argmax,

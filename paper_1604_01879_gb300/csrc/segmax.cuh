@@ -12,4 +12,8 @@ void segmax_scores(const float* A, const float* inv_a, int64_t n_views, const fl
                    const std::vector<int32_t>& h_qoff, int32_t Bq, float* S, int16_t* argmax,
                    Scratch& sc, cudaStream_t s);
 
+// S[b, p] (and argmax) from the per-(view, shape) cells of queries [b0, b0 + nq)
+void segmax_reduce(const unsigned long long* cell, int64_t n_shapes, const int32_t* d_qoff, int32_t b0, int32_t nq,
+                   int32_t view0, float* S, int16_t* argmax, cudaStream_t s);
+
 }  // namespace gift

@@ -1,0 +1,254 @@
+// Persistent warp-specialised tcgen05 contraction engine.
+//
+// A work item multiplies a 128-row tile of A with a tile of B (both K-major
+// BF16 in global memory, read by TMA with 128-byte swizzle) in one or more
+// "chunks"; a chunk is a run of 64-element k-blocks over one 128- or 256-row
+// slice of B, accumulated in its own TMEM buffer (FP32, 128 lanes x TN
+// columns). Buffers rotate through NBUF slots, so the epilogue of one chunk
+// overlaps the MMAs of the next.
+//
+//   warp 0        TMA producer (one thread): ring of STAGES shared-memory stages
+//   warp 1        MMA issuer (one thread)
+//   warps 2..5    epilogue; thread = TMEM lane = row of the A tile
+//
+// SPLIT = 3 multiplies two-part operands (x = hi + lo, both BF16):
+// hi*hi + hi*lo + lo*hi. Chunking the reduction dimension bounds how many
+// MMA steps feed one accumulator: the tensor-core FP32 accumulation is not
+// round-to-nearest, and the chunk partials are summed in FP32 on the CUDA
+// cores by the epilogue.
+//
+// A policy class P supplies the schedule and the epilogue:
+//   static constexpr int TN, NBUF, STAGES, SPLIT;
+//   struct Item; struct Ctx;                                  (per-thread epilogue state)
+//   int64_t total() const;  Item decode(int64_t) const;
+//   int nchunks(const Item&) const;
+//   void chunk(const Item&, int c, int& b_row, int& kb0, int& kb1) const;
+//   int a_row(const Item&) const;
+//   void epi_begin(const Item&, Ctx&, int m, int ew, uint8_t* warp_smem) const;
+//   void epi_chunk(const Item&, int c, uint32_t taddr, Ctx&, int m, uint8_t* warp_smem) const;
+//   void epi_end(const Item&, Ctx&, int m, uint8_t* warp_smem) const;
+//   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
+#pragma once
+#include "tc_common.cuh"
+
+namespace gift {
+namespace tc {
+
+constexpr int kTM = 128;
+constexpr int kTK = 64;
+constexpr int kEngineThreads = 192;
+
+template <class P>
+struct EngineLayout {
+  static constexpr int kABytes = kTM * kTK * 2;
+  static constexpr int kBBytes = P::TN * kTK * 2;
+  static constexpr int kParts = P::SPLIT == 1 ? 1 : 2;
+  static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem;
+  static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
+  static_assert(kSmem <= 232448, "shared memory per CTA");
+};
+
+template <class P>
+__global__ void __launch_bounds__(kEngineThreads, 1)
+    tc_engine(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const P p,
+              int* err) {
+  using L = EngineLayout<P>;
+  constexpr int S = P::STAGES;
+  constexpr int NB = P::NBUF;
+  constexpr int TN = P::TN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* tiles = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * L::kStageBytes);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB);
+  uint8_t* wsm = smem + S * L::kStageBytes + L::kBarBytes;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = full0 + 8 * S;
+  const uint32_t tfull0 = empty0 + 8 * S;
+  const uint32_t tempty0 = tfull0 + 8 * NB;
+  constexpr uint32_t kCols = (NB * TN <= 32) ? 32 : (NB * TN <= 64) ? 64 : (NB * TN <= 128) ? 128
+                             : (NB * TN <= 256) ? 256 : 512;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_holder), kCols);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  const int64_t total = p.total();
+  constexpr uint32_t kIdesc = idesc_bf16(kTM, TN);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int last_phase[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) last_phase[s] = -1;
+      for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
+        const typename P::Item it = p.decode(item);
+        const int ar = p.a_row(it);
+        const int nch = p.nchunks(it);
+        for (int c = 0; ok && c < nch; ++c) {
+          int br, kb0, kb1;
+          p.chunk(it, c, br, kb0, kb1);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer)) {
+              ok = false;
+              break;
+            }
+            const uint32_t st = smem_u32(tiles + stage * L::kStageBytes);
+            mbar_expect_tx(full0 + 8 * stage, L::kStageBytes);
+            tma_load_2d(st, &tmA, kb * kTK, ar, full0 + 8 * stage);
+            tma_load_2d(st + L::kABytes, &tmB, kb * kTK, br, full0 + 8 * stage);
+            if (P::SPLIT == 3) {
+              tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * kTK, ar, full0 + 8 * stage);
+              tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * kTK, br, full0 + 8 * stage);
+            }
+            last_phase[stage] = (int)phase;
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        for (int s = 0; s < S; ++s) {  // let issued copies land before exiting (bounded)
+          if (last_phase[s] < 0) continue;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(full0 + 8 * s, (uint32_t)last_phase[s]) && clock64() - t0 < kWaitCycles / 4) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int buf = 0;
+      uint32_t bphase = 0;
+      for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
+        const typename P::Item it = p.decode(item);
+        const int nch = p.nchunks(it);
+        for (int c = 0; ok && c < nch; ++c) {
+          int br, kb0, kb1;
+          p.chunk(it, c, br, kb0, kb1);
+          if (!mbar_wait(tempty0 + 8 * buf, bphase ^ 1, err, kErrMma)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t d = tmem + buf * TN;
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full0 + 8 * stage, phase, err, kErrMma)) {
+              ok = false;
+              break;
+            }
+            fence_after_sync();
+            const uint32_t sa = smem_u32(tiles + stage * L::kStageBytes);
+            const uint32_t sb = sa + L::kABytes;
+            const uint32_t sa2 = sb + L::kBBytes;
+            const uint32_t sb2 = sa2 + L::kABytes;
+#pragma unroll
+            for (int kk = 0; kk < kTK / 16; ++kk) {
+              const uint32_t acc_in = (kb != kb0 || kk != 0) ? 1u : 0u;
+              mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
+              if (P::SPLIT == 3) {
+                mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
+                mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
+              }
+            }
+            mma_commit(empty0 + 8 * stage);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * buf);
+          if (++buf == NB) {
+            buf = 0;
+            bphase ^= 1;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quad = warp & 3;
+    const int m = quad * 32 + lane;
+    const int ew = warp - 2;
+    uint8_t* my = wsm + ew * P::kWarpSmem;
+    int buf = 0;
+    uint32_t bphase = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
+      const typename P::Item it = p.decode(item);
+      typename P::Ctx ctx;
+      __syncwarp();
+      p.epi_begin(it, ctx, m, ew, my);
+      __syncwarp();
+      const int nch = p.nchunks(it);
+      for (int c = 0; c < nch; ++c) {
+        if (!mbar_wait(tfull0 + 8 * buf, bphase, err, kErrTmemFull)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        p.epi_chunk(it, c, tmem + (static_cast<uint32_t>(quad * 32) << 16) + buf * TN, ctx, m, my);
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+        if (++buf == NB) {
+          buf = 0;
+          bphase ^= 1;
+        }
+      }
+      if (!ok) break;
+      p.epi_end(it, ctx, m, my);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, kCols);
+  }
+}
+
+// Launch on every SM of the current device (persistent CTAs).
+template <class P>
+void launch_engine(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2, const CUtensorMap& b2,
+                   const P& p, int* err, int grid, cudaStream_t s) {
+  using L = EngineLayout<P>;
+  GIFT_CUDA(cudaFuncSetAttribute(tc_engine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem));
+  tc_engine<P><<<grid, kEngineThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
+  GIFT_LAUNCHED("tc_engine");
+}
+
+}  // namespace tc
+}  // namespace gift

@@ -83,6 +83,12 @@ CONFIGS = {
         n_classes=40, n_codewords=1024, n_queries=1000, storage="bf16",
         rescore_r=200, topk=100, sif_k1=50, kmeans_shapes=256, kmeans_iters=10,
         seed=2),
+    # reduced ModelNet40-shaped case for kernel profiles (lists > L2, few GB on device)
+    "db2000x64_d4096_k1024": Config(
+        name="db2000x64_d4096_k1024", n_shapes=2000, n_views=64, dim=4096,
+        n_classes=40, n_codewords=1024, n_queries=256, storage="bf16",
+        rescore_r=200, topk=100, sif_k1=50, kmeans_shapes=256, kmeans_iters=10,
+        seed=5),
     # 16x scale-up of ModelNet40 with FP8 store and query-side MA = 2
     "db200000x64_d4096_k4096_fp8": Config(
         name="db200000x64_d4096_k4096_fp8", n_shapes=200000, n_views=64,

@@ -279,3 +279,28 @@ def test_rerank_matches_oracle(c1):
         Fq = O.membership(S_q[b], k1)
         ref = np.array([O.contextual(Fq, F_db[p]) for p in range(X.shape[0])])
         assert_topk(rid[b], rsp[b], ref, 10, rtol=1e-4, atol=2e-5)
+
+
+@pytest.mark.parametrize("D", [256, 80])
+def test_tensor_core_scan_tiling(gpu_lib, D):
+    """BF16 store on the tcgen05 scan: buckets of >128 slots (several slot tiles),
+    lists of >256 entries (several entry tiles), D with a partial 64-wide k-block;
+    scan scores within BF16 error, rescored scores FP32-accurate."""
+    import torch
+    N, Nv, C, K = 100, 32, 2, 2
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 40, (64, 17), 91)
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="bf16", keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=N)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for b in range(len(qoff) - 1):
+        assert sorted(ids[b].tolist()) == list(range(N))
+        assert np.abs(sc[b] - ref[b, ids[b]]).max() < 3e-3
+    ix.close()
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="bf16", rescore_r=N, keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=N)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for b in range(len(qoff) - 1):
+        assert close(sc[b], ref[b, ids[b]]).all()
+        assert_topk(ids[b], sc[b], ref[b], N)
+    ix.close()
