@@ -242,7 +242,7 @@ def main():
     db_dev = torch.from_numpy(data["db"]).to(dev)
     ix = gift.Index(db_dev, torch.from_numpy(data["codebook"]).to(dev), cfg.n_shapes, cfg.n_views,
                     cfg.n_codewords, storage=cfg.storage, query_ma=cfg.query_ma, sif_k1=cfg.sif_k1,
-                    rescore_r=cfg.rescore_r, keep_exact=True)
+                    rescore_r=cfg.rescore_r, keep_exact=not args.profile)
     torch.cuda.synchronize()
     del db_dev
     log(f"[bench] index built in {time.time() - t0:.1f}s: {ix.info()}")

@@ -51,12 +51,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int site) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  for (;;) {
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      atomicCAS(err, 0, site);
-      return false;
+    // the error flag and the clock are polled rarely: a global load in every
+    // iteration would delay the reaction to the phase flip by an L2 round trip
+    if ((i & 255u) == 0) {
+      if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicCAS(err, 0, site);
+        return false;
+      }
     }
   }
 }
