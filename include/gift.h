@@ -173,6 +173,35 @@ GIFT_API gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, con
                         float* out_sprime, cudaStream_t stream);
 
 /*
+ * S-IF re-ranking that allocates no memory. The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory while they
+ * re-rank -- a process whose free device memory is held by another allocator
+ * (a serving framework's caching pool), where an allocation would fail, or a
+ * latency-critical loop that must not enter the CUDA allocator (freeing device
+ * memory can synchronise the device).
+ *  - Same arguments and results as gift_rerank, but every buffer must be in
+ *    device memory (host buffers would need staging memory); returns GIFT_EINVAL
+ *    otherwise.
+ *  - Scratch: one fixed buffer of GIFT_RERANK_NOALLOC_SCRATCH_BYTES inside the
+ *    library, created on every device that uses this call and held until the
+ *    process exits. A batch needs about 20 * B * N + 8 * B * (topk + 1) bytes
+ *    (N = database shapes; 256-byte alignment per part); a larger batch returns
+ *    GIFT_EINVAL with the size it needs -- split it.
+ *  - The first call on a device looks up the buffer's device address with that
+ *    device current (the runtime loads the library's module there); make that
+ *    first call before any stream capture.
+ *  - Every call uses the same buffer and clears what must start at zero; calls
+ *    whose work overlaps on the GPU (several streams or host threads at once)
+ *    race on it, so the caller must serialise them.
+ *  - No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+#define GIFT_RERANK_NOALLOC_SCRATCH_BYTES (16u << 20)
+GIFT_API gift_status gift_rerank_noalloc(gift_index* index, const int32_t* cand_ids,
+                                         const float* cand_scores, int32_t B, int32_t n_cand,
+                                         int32_t k1, int32_t topk, int32_t* out_ids,
+                                         float* out_sprime, cudaStream_t stream);
+
+/*
  * The quantiser alone (Sec. 2.3): out_codes[v * ma + a] is the a-th nearest
  * codeword of row v by (squared distance, index), c(x) = argmin_k ||x - b_k||^2.
  *  - feats: device float [n * D]; out_codes: device int32 [n * ma]; 1 <= ma <= 8.

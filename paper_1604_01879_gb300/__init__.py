@@ -69,6 +69,7 @@ _SIGS = {
     "gift_destroy_index": (None, [_P]),
     "gift_query": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
     "gift_export_fif": (_I32, [_P, _P, _P, _P, _P]),
     "gift_export_sif": (_I32, [_P, _P, _P, _P, _P, _P]),

@@ -30,6 +30,7 @@ SOURCES = [
     "k_scan_tc.cu",
     "tc_host.cu",
     "k_exact_tc.cu",
+    "k_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -357,6 +357,12 @@ gift_status guard(const char* fn, const std::function<void()>& body) {
   }
 }
 
+}  // namespace
+
+gift_status guarded(const char* fn, const std::function<void()>& body) { return guard(fn, body); }
+
+namespace {
+
 std::vector<int32_t> host_offsets(const int32_t* q_view_offsets, int32_t B) {
   GIFT_REQUIRE(q_view_offsets != nullptr, "q_view_offsets is NULL");
   GIFT_REQUIRE(!is_device_ptr(q_view_offsets), "q_view_offsets must be a host pointer");

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -22,6 +23,8 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(gift_status s, const std::string& msg);
+// runs body, turning errors into a status and the thread's last-error message
+gift_status guarded(const char* fn, const std::function<void()>& body);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define GIFT_CUDA(x) ::gift::check_cuda((x), #x, __FILE__, __LINE__)
 void count_launch();
@@ -174,6 +177,11 @@ void sif_build(Index& ix, const int32_t* nbr_ids, const float* nbr_scores, Scrat
 void sif_rerank(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B,
                 int32_t n_cand, int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime,
                 Scratch& sc, cudaStream_t s);
+// bytes of caller-provided scratch sif_rerank_into needs
+size_t sif_rerank_scratch_bytes(int32_t B, int32_t N, int32_t topk);
+void sif_rerank_into(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B, int32_t n_cand,
+                     int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, void* scratch,
+                     size_t scratch_bytes, cudaStream_t s);
 
 // k_match.cu
 void match_forward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq,

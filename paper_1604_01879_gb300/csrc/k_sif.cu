@@ -188,4 +188,52 @@ void sif_rerank(const Index& ix, const int32_t* cand_ids, const float* cand_scor
   GIFT_LAUNCHED("k_keys_to_sprime");
 }
 
+namespace {
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+
+size_t sif_rerank_scratch_bytes(int32_t B, int32_t N, int32_t topk) {
+  const size_t BN = (size_t)B * (size_t)N;
+  return align256(BN * 8) + align256(BN * 4) + align256((size_t)B * 8) + align256(BN * 8) +
+         align256((size_t)B * (size_t)topk * 8);
+}
+
+// The re-rank of sif_rerank on scratch the caller provides (no allocation):
+// the same kernels, with the numerator cleared and the candidate row filled
+// before use, so nothing depends on what the scratch held before.
+void sif_rerank_into(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B, int32_t n_cand,
+                     int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, void* scratch,
+                     size_t scratch_bytes, cudaStream_t s) {
+  const int32_t N = ix.prm.n_shapes;
+  const int64_t BN = (int64_t)B * N;
+  GIFT_REQUIRE(sif_rerank_scratch_bytes(B, N, topk) <= scratch_bytes, "re-rank scratch too small");
+  uint8_t* p = static_cast<uint8_t*>(scratch);
+  unsigned long long* num = reinterpret_cast<unsigned long long*>(p);
+  p += align256((size_t)BN * 8);
+  float* Srow = reinterpret_cast<float*>(p);
+  p += align256((size_t)BN * 4);
+  unsigned long long* fqn = reinterpret_cast<unsigned long long*>(p);
+  p += align256((size_t)B * 8);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
+  p += align256((size_t)BN * 8);
+  unsigned long long* kout = reinterpret_cast<unsigned long long*>(p);
+  GIFT_CUDA(cudaMemsetAsync(num, 0, BN * 8, s));
+  k_fill_f32<<<(unsigned)cdiv(BN, 256), 256, 0, s>>>(Srow, BN, -INFINITY);
+  GIFT_LAUNCHED("k_fill_f32");
+  k_rerank_prep<<<(unsigned)B, 256, 0, s>>>(cand_ids, cand_scores, n_cand, k1, N, Srow, fqn);
+  GIFT_LAUNCHED("k_rerank_prep");
+  k_rerank_walk<<<dim3((unsigned)B, (unsigned)k1), 128, 0, s>>>(cand_ids, cand_scores, n_cand, k1, N, ix.sif_off,
+                                                             ix.sif_ids, ix.sif_mem, num);
+  GIFT_LAUNCHED("k_rerank_walk");
+  k_rerank_keys<<<(unsigned)cdiv(BN, 256), 256, 0, s>>>(num, fqn,
+                                                          reinterpret_cast<const unsigned long long*>(ix.sif_card),
+                                                          Srow, B, N, keys);
+  GIFT_LAUNCHED("k_rerank_keys");
+  Scratch none(s);  // the selection kernel takes a scratch handle but allocates nothing
+  topk_rows_u64(reinterpret_cast<const uint64_t*>(keys), B, N, topk, out_ids, reinterpret_cast<uint64_t*>(kout),
+                none, s);
+  k_keys_to_sprime<<<(unsigned)cdiv((int64_t)B * topk, 256), 256, 0, s>>>(kout, (int64_t)B * topk, out_sprime);
+  GIFT_LAUNCHED("k_keys_to_sprime");
+}
+
 }  // namespace gift
