@@ -104,6 +104,10 @@ typedef struct {
                            + their scales and ids + query rows              */
   int64_t rescore_bytes;/* algorithmic bytes of the rescore                  */
   int64_t scan_pairs;   /* (query view, list entry) pairs scanned           */
+  float assign_kernel_ms;  /* tensor-core quantiser kernel alone              */
+  float scan_kernel_ms;    /* tensor-core scan kernel alone (BF16 store)      */
+  float rescore_kernel_ms; /* tensor-core rescore kernel alone                */
+  int64_t assign_rows;     /* rows quantised                                  */
 } gift_timing_t;
 
 /*

@@ -59,7 +59,9 @@ class _Timing(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in (
         "assign_ms", "bucket_ms", "scan_ms", "combine_ms", "topk_ms", "rescore_ms", "rerank_ms",
         "total_ms")] + [("scan_bytes", ctypes.c_int64), ("rescore_bytes", ctypes.c_int64),
-                        ("scan_pairs", ctypes.c_int64)]
+                        ("scan_pairs", ctypes.c_int64), ("assign_kernel_ms", ctypes.c_float),
+                        ("scan_kernel_ms", ctypes.c_float), ("rescore_kernel_ms", ctypes.c_float),
+                        ("assign_rows", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

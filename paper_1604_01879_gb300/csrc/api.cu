@@ -22,7 +22,11 @@ struct StageTimer {
   cudaStream_t s;
   bool on;
   std::vector<std::pair<int, cudaEvent_t>> marks;
-  StageTimer(Index* i, cudaStream_t st) : ix(i), s(st), on(i && i->timing) {}
+  KernelClock kc;
+  StageTimer(Index* i, cudaStream_t st) : ix(i), s(st), on(i && i->timing) {
+    kc.on = on;
+    kc.s = st;
+  }
   void mark(int stage) {
     if (!on) return;
     cudaEvent_t e;
@@ -42,9 +46,20 @@ struct StageTimer {
       ix->ev_stage.push_back(m.first);
     }
     marks.clear();
+    for (auto& k : ix->kspans) {
+      cudaEventDestroy(k.second.first);
+      cudaEventDestroy(k.second.second);
+    }
+    ix->kspans = kc.spans;
+    ix->k_assign_rows = kc.assign_rows;
+    kc.spans.clear();
   }
   ~StageTimer() {
     for (auto& m : marks) cudaEventDestroy(m.second);
+    for (auto& k : kc.spans) {
+      cudaEventDestroy(k.second.first);
+      cudaEventDestroy(k.second.second);
+    }
   }
 };
 
@@ -232,7 +247,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   float* q_inv = sc.get<float>(nv);
   launch_row_invnorm(q, nv, ix.prm.dim, q_inv, s);
   int32_t* q_code = sc.get<int32_t>(nv * ma);
-  assign_codes(ix, q, nv, ma, q_code, sc, s, q_inv);
+  assign_codes(ix, q, nv, ma, q_code, sc, s, q_inv, &tm.kc);
 
   tm.mark(ST_BUCKET);
   FifPlan P;
@@ -245,6 +260,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   P.qoff = d_qoff;
   P.vquery = vquery;
   P.stats = stats;
+  P.kc = &tm.kc;
   fif_plan(ix, P, sc, s);
   uint32_t* table = sc.get<uint32_t>(P.table_upper);
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
@@ -285,6 +301,23 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
 }  // namespace
 
 // ------------------------------------------------------------------ plumbing
+void KernelClock::begin(int id) {
+  if (!on) return;
+  cudaEvent_t a, b;
+  GIFT_CUDA(cudaEventCreate(&a));
+  GIFT_CUDA(cudaEventCreate(&b));
+  GIFT_CUDA(cudaEventRecord(a, s));
+  spans.push_back({id, {a, b}});
+}
+void KernelClock::end(int id) {
+  if (!on) return;
+  for (auto it = spans.rbegin(); it != spans.rend(); ++it)
+    if (it->first == id) {
+      GIFT_CUDA(cudaEventRecord(it->second.second, s));
+      return;
+    }
+}
+
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -329,6 +362,10 @@ T* Index::alloc(size_t n) {
 
 Index::~Index() {
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  for (auto& k : kspans) {
+    cudaEventDestroy(k.second.first);
+    cudaEventDestroy(k.second.second);
+  }
   if (stats_pinned) cudaFreeHost(stats_pinned);
   for (void* p : owned) cudaFree(p);
 }
@@ -722,6 +759,14 @@ gift_status gift_get_timing(gift_index* index, gift_timing_t* out) {
       if (st >= 0 && st < gift::ST_END) *slot[st] += ms;
     }
     GIFT_CUDA(cudaEventElapsedTime(&t.total_ms, ix.ev.front(), ix.ev.back()));
+    for (auto& k : ix.kspans) {
+      float ms = 0.f;
+      GIFT_CUDA(cudaEventElapsedTime(&ms, k.second.first, k.second.second));
+      if (k.first == 0) t.assign_kernel_ms += ms;
+      if (k.first == 1) t.scan_kernel_ms += ms;
+      if (k.first == 2) t.rescore_kernel_ms += ms;
+    }
+    t.assign_rows = ix.k_assign_rows;
     if (ix.stats_pinned && ix.stats_valid) {
       t.scan_bytes = (int64_t)ix.stats_pinned[0];
       t.scan_pairs = (int64_t)ix.stats_pinned[1];
@@ -763,7 +808,7 @@ gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, i
 
 const char* gift_last_error(void) { return gift::g_last_error.c_str(); }
 
-int32_t gift_version(void) { return 100; }
+int32_t gift_version(void) { return 101; }
 
 int64_t gift_launch_count(void) { return gift::g_launches.load(); }
 

@@ -14,7 +14,8 @@ struct FifPlan {
   const int32_t* q_code = nullptr;// [nv * ma]
   const int32_t* qoff = nullptr;  // [B+1] device
   const int32_t* vquery = nullptr;// [nv] query of each view
-  unsigned long long* stats = nullptr;  // optional [2]: scanned bytes, pairs
+  unsigned long long* stats = nullptr;  // optional [3]: scanned bytes, pairs, rescore bytes
+  KernelClock* kc = nullptr;            // optional kernel timing
   // derived
   int64_t nslots = 0;
   int32_t* skeys = nullptr;       // [nslots] codeword of each slot (ascending)

@@ -45,6 +45,18 @@ struct Scratch {
   template <class T> T* get(size_t n) { return static_cast<T*>(raw(n * sizeof(T) + 16)); }
 };
 
+// ---------------------------------------------------------------- kernel timing
+// CUDA events around single kernel launches (on the launching stream) when a
+// call is timed; ids: 0 quantiser, 1 scan, 2 rescore.
+struct KernelClock {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+  int64_t assign_rows = 0;
+  void begin(int id);
+  void end(int id);
+};
+
 // ---------------------------------------------------------------- fixed point
 // Shape scores are sums of per-view maxima in [0, 1]; they are accumulated in
 // uint64 fixed point so that the sum is exact and independent of the order.
@@ -114,6 +126,8 @@ struct Index {
   std::vector<cudaEvent_t> ev;  // stage events of the last timed call
   std::vector<int> ev_stage;    // stage id of each event interval
   unsigned long long* stats_pinned = nullptr;  // scan bytes, pairs, rescore bytes
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kspans;  // of the last timed call
+  int64_t k_assign_rows = 0;
   bool stats_valid = false;
 
   template <class T> T* alloc(size_t n);
@@ -143,7 +157,7 @@ void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 // codes[v*ma + a] = a-th nearest codeword by (squared distance, index);
 // x_inv (optional) holds 1/||x|| of the rows.
 void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes,
-                  Scratch& sc, cudaStream_t s, const float* x_inv = nullptr);
+                  Scratch& sc, cudaStream_t s, const float* x_inv = nullptr, KernelClock* kc = nullptr);
 // hi = bf16(x), lo = bf16(x - hi) of a row-major [n, D] FP32 matrix
 void split_rows_bf16(const float* X, int64_t n, int D, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 

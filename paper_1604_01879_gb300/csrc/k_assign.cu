@@ -250,7 +250,7 @@ void split_rows_bf16(const float* X, int64_t n, int D, __nv_bfloat16* hi, __nv_b
 }
 
 void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* codes, Scratch& sc, cudaStream_t s,
-                  const float* x_inv) {
+                  const float* x_inv, KernelClock* kc) {
   if (n <= 0) return;
   const int K = ix.prm.n_codewords, D = ix.prm.dim;
   GIFT_REQUIRE(ma >= 1 && ma <= GIFT_MAX_MA && ma <= K, "multiple assignment must be in [1, min(8, K)]");
@@ -285,7 +285,12 @@ void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* c
     const CUtensorMap tA = make_tmap_bf16(hi, rows_alloc, D, tc::kTM);
     const CUtensorMap tA2 = make_tmap_bf16(lo, rows_alloc, D, tc::kTM);
     const int grid = (int)std::min<int64_t>(sms, cdiv(m, tc::kTM));
+    if (kc) kc->begin(0);
     tc::launch_engine(tA, tB, tA2, tB2, p, ix.d_err, grid, s);
+    if (kc) {
+      kc->end(0);
+      kc->assign_rows += m;
+    }
     k_assign_refine<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(X + r0 * D, m, D, ix.codebook, K, ma, cand, cnt,
                                                           codes + r0 * ma);
     GIFT_LAUNCHED("k_assign_refine");

@@ -322,7 +322,9 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     static_cast<ListSched&>(pol) = ls;
     pol.si = si;
     const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy::TN);
+    if (P.kc) P.kc->begin(1);
     tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
+    if (P.kc) P.kc->end(1);
   } else {
     GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the BF16 residual store");
     RescorePolicy pol;
@@ -333,7 +335,9 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, RescorePolicy::TN);
     const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
     const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, RescorePolicy::TN);
+    if (P.kc) P.kc->begin(2);
     tc::launch_engine(tA, tB, tA2, tB2, pol, ix.d_err, grid, s);
+    if (P.kc) P.kc->end(2);
   }
 }
 
