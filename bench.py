@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only (for ncu launch lists)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving session length (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.profile else args.warmup
 
@@ -358,6 +360,47 @@ def main():
     exact_ms = x_ev[0].elapsed_time(x_ev[1])
     exact_qps = nx / (exact_ms / 1e3)
 
+    # ---- serving: Poisson arrivals, view counts uniform in {12, 20, 64}, continuous batching
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        import threading
+        sv = gift.Server(ix, slots=3, max_batch_queries=256, max_batch_views=256 * 64, topk=topk, rerank=True)
+        g = np.random.default_rng(5000 + cfg.seed)
+        n_req = max(1, int(args.serve_rate * args.serve_seconds))
+        vcounts = g.choice(np.array([12, 20, 64]), size=n_req)
+        gaps = g.exponential(1.0 / args.serve_rate, size=n_req)
+        nq_pool = len(qoff) - 1
+        tickets = [None] * n_req
+
+        def producer():
+            t = time.perf_counter()
+            for i in range(n_req):
+                t += gaps[i]
+                while time.perf_counter() < t:
+                    pass
+                b = i % nq_pool
+                tickets[i] = sv.submit(data["q"][qoff[b]:qoff[b] + int(vcounts[i])])
+
+        t_s = time.perf_counter()
+        th = threading.Thread(target=producer)
+        th.start()
+        done = 0
+        while done < n_req:
+            while tickets[done] is None:
+                time.sleep(1e-4)
+            sv.wait(tickets[done], timeout_ms=120000)
+            done += 1
+        th.join()
+        wall = time.perf_counter() - t_s
+        sst = sv.stats()
+        sv.close()
+        serving = {"arrival_rate": args.serve_rate, "seconds": args.serve_seconds, "requests": n_req,
+                   "view_counts": [12, 20, 64], "queries_per_s": n_req / wall, "p50_ms": sst["p50_ms"],
+                   "p99_ms": sst["p99_ms"], "max_ms": sst["max_ms"], "batches": sst["batches"],
+                   "mean_batch": sst["mean_batch"], "slots": 3, "index": cfg.name,
+                   "result": "top-100 after S-IF re-rank"}
+        log(f"[bench] serving: {serving}")
+
     value = world * args.steps * B / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -376,6 +419,7 @@ def main():
         "e2e": {"value": B / (e2e_ms / 1e3) * world, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
+        "serving": serving,
     }
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)

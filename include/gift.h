@@ -280,6 +280,55 @@ GIFT_API gift_status gift_match_backward(const float* q, const int32_t* q_view_o
                                 const int16_t* argmax, float* dW, float* dQ, float* dP,
                                 cudaStream_t stream);
 
+/*
+ * Request loop over a resident index (serving). Requests of mixed view counts
+ * are queued; a dispatcher thread forms batches from the head of the queue
+ * whenever one of `slots` batch slots is free, admits a batch only while the
+ * device memory of all batches in flight fits `memory_budget`, and runs each
+ * batch (F-IF query, optional S-IF re-rank) on its slot's own stream, so
+ * batches overlap on the device. Results and latencies (submission to
+ * completion) are per request. Sec. 2 and Table 4 of the paper measure the
+ * per-query on-line time; this loop is the batched GPU form of that service.
+ */
+typedef struct {
+  int32_t slots;             /* batches in flight, 1..16                                   */
+  int32_t max_batch_queries; /* queries per batch                                          */
+  int32_t max_batch_views;   /* views per batch (and per request)                          */
+  int32_t topk;              /* results per request (<= rescore depth when rescoring)      */
+  int32_t rerank;            /* 1 = results are S-IF re-ranked (needs sif_k1 > 0)          */
+  int32_t start_paused;      /* 1 = queue requests until gift_server_resume                */
+  int64_t memory_budget;     /* device bytes for slot buffers + batches in flight; 0 = 80%
+                                of the free device memory at creation                      */
+} gift_server_params;
+
+typedef struct {
+  int64_t completed, failed, batches, queued;
+  float mean_batch;     /* queries per batch                                             */
+  float p50_ms, p99_ms, max_ms;  /* latency, submission to completion                     */
+  float queries_per_s;  /* completed / (last completion - first submission)              */
+} gift_server_stats_t;
+
+typedef struct gift_server gift_server;
+
+/* Start a request loop on the current device for `index` (which must outlive it).
+ * Errors: EINVAL (limits, budget smaller than one batch), ENOMEM, ECUDA. */
+GIFT_API gift_status gift_server_create(gift_index* index, const gift_server_params* params,
+                                        gift_server** out);
+/* Queue one request: q_feats HOST float [n_views * D] (copied before return).
+ * Writes a ticket. Errors: EINVAL (n_views outside [1, max_batch_views]), ESTATE. */
+GIFT_API gift_status gift_server_submit(gift_server* server, const float* q_feats, int32_t n_views,
+                                        int64_t* ticket);
+/* Wait at most timeout_ms for a request; on success copy its topk ids / scores
+ * (S' when re-ranking) to HOST buffers and forget the ticket. GIFT_ETIMEOUT when
+ * the request is not complete in time (the ticket stays valid). */
+GIFT_API gift_status gift_server_wait(gift_server* server, int64_t ticket, int32_t timeout_ms,
+                                      int32_t* out_ids, float* out_scores);
+/* Start dispatching a server created with start_paused = 1. */
+GIFT_API gift_status gift_server_resume(gift_server* server);
+GIFT_API gift_status gift_server_stats(gift_server* server, gift_server_stats_t* out);
+/* Finish queued and in-flight requests, stop the dispatcher, free the slots. */
+GIFT_API void gift_server_destroy(gift_server* server);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (all threads); the difference across a region counts its launches. */
 GIFT_API int64_t gift_launch_count(void);

@@ -64,6 +64,17 @@ class _Timing(ctypes.Structure):
                         ("assign_rows", ctypes.c_int64)]
 
 
+class _ServerParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "slots", "max_batch_queries", "max_batch_views", "topk", "rerank", "start_paused")] + [
+        ("memory_budget", ctypes.c_int64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("completed", "failed", "batches", "queued")] + [
+        (n, ctypes.c_float) for n in ("mean_batch", "p50_ms", "p99_ms", "max_ms", "queries_per_s")]
+
+
 _P = ctypes.c_void_p
 _I32, _I64 = ctypes.c_int32, ctypes.c_int64
 _SIGS = {
@@ -81,6 +92,12 @@ _SIGS = {
     "gift_match_forward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "gift_match_backward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P, _P,
                                    _P]),
+    "gift_server_create": (_I32, [_P, ctypes.POINTER(_ServerParams), ctypes.POINTER(_P)]),
+    "gift_server_submit": (_I32, [_P, _P, _I32, ctypes.POINTER(_I64)]),
+    "gift_server_wait": (_I32, [_P, _I64, _I32, _P, _P]),
+    "gift_server_resume": (_I32, [_P]),
+    "gift_server_stats": (_I32, [_P, ctypes.POINTER(_ServerStats)]),
+    "gift_server_destroy": (None, [_P]),
     "gift_last_error": (ctypes.c_char_p, []),
     "gift_launch_count": (_I64, []),
     "gift_version": (_I32, []),
@@ -307,3 +324,53 @@ class _Lazy:
 
 
 GiftMatch = _Lazy()
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """Request loop over a resident index (gift_server_*): continuous batching of
+    queries with mixed view counts, memory-based admission, p50/p99 latency."""
+
+    def __init__(self, index: Index, slots: int = 3, max_batch_queries: int = 256, max_batch_views: int = 256 * 64,
+                 topk: int = 10, rerank: bool = True, start_paused: bool = False, memory_budget: int = 0):
+        self.index = index
+        self.topk = int(topk)
+        self.dim = index.dim
+        p = _ServerParams(int(slots), int(max_batch_queries), int(max_batch_views), int(topk), int(bool(rerank)),
+                          int(bool(start_paused)), int(memory_budget))
+        self._h = ctypes.c_void_p()
+        _check(load().gift_server_create(index._h, ctypes.byref(p), ctypes.byref(self._h)))
+
+    def submit(self, q_feats) -> int:
+        """Queue one query (host float32 [n_views, D]); returns its ticket."""
+        q = np.ascontiguousarray(q_feats, dtype=np.float32)
+        t = ctypes.c_int64()
+        _check(load().gift_server_submit(self._h, ctypes.c_void_p(q.ctypes.data), int(q.shape[0]), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        """(ids int32 [topk], scores float32 [topk]) of a request; GiftError ETIMEOUT if not done in time."""
+        ids = np.empty(self.topk, np.int32)
+        sc = np.empty(self.topk, np.float32)
+        _check(load().gift_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.c_void_p(ids.ctypes.data),
+                                       ctypes.c_void_p(sc.ctypes.data)))
+        return ids, sc
+
+    def resume(self):
+        _check(load().gift_server_resume(self._h))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load().gift_server_stats(self._h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().gift_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

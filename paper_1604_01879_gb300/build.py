@@ -31,6 +31,7 @@ SOURCES = [
     "tc_host.cu",
     "k_exact_tc.cu",
     "k_noalloc.cu",
+    "serve.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
