@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="steps only (for ncu launch lists)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving session length (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.profile else args.warmup
 
@@ -401,6 +402,12 @@ def main():
                    "result": "top-100 after S-IF re-rank"}
         log(f"[bench] serving: {serving}")
 
+    # ---- differentiation: projected match forward + backward at its own workload
+    diff = None
+    if not args.no_diff and rank == 0:
+        diff = bench_differentiation(gift, torch, dev, stream)
+        log(f"[bench] differentiation: {diff}")
+
     value = world * args.steps * B / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -420,6 +427,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "serving": serving,
+        "differentiation": diff,
     }
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)
@@ -488,6 +496,46 @@ def main():
     ix.close()
     if rank == 0:
         print(json.dumps(line))
+
+
+def bench_differentiation(gift, torch, dev, stream, reps=3):
+    """Forward + backward of the projected match (Eq. 3 after u = W q) on the
+    differentiation workload; device-timed with CUDA events."""
+    from synth import DIFF_WORKLOAD as W_, shape_views, projection_matrix, upstream_grad
+    nq, N, nv, D, dout = W_["n_queries"], W_["n_shapes"], W_["n_views"], W_["dim"], W_["d_out"]
+    s = W_["seed"]
+    q = torch.from_numpy(shape_views(0, nq, nv, D, W_["n_classes"], 2000 + s, 4000 + s)).to(dev).to(
+        torch.bfloat16).reshape(nq * nv, D)
+    p = torch.from_numpy(shape_views(0, N, nv, D, W_["n_classes"], 1000 + s, 4000 + s)).to(dev).to(torch.bfloat16)
+    W = torch.from_numpy(projection_matrix(dout, D, 3000 + s, W_["w_std"])).to(dev).to(torch.bfloat16)
+    G = torch.from_numpy(upstream_grad(nq, N, 5000 + s)).to(dev)
+    off = np.arange(0, nq * nv + 1, nv, dtype=np.int32)
+    S, am = gift.match_forward(q, off, p, W)
+    gift.match_backward(q, off, p, W, G, am)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw, bw = [], []
+    for _ in range(reps):
+        e[0].record(stream)
+        S, am = gift.match_forward(q, off, p, W)
+        e[1].record(stream)
+        gift.match_backward(q, off, p, W, G, am)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fw.append(e[0].elapsed_time(e[1]))
+        bw.append(e[1].elapsed_time(e[2]))
+    nr = N * nv
+    proj = 2.0 * (nq * nv + nr) * D * dout
+    sim = 2.0 * (nq * nv) * nr * dout
+    f_ms, b_ms = statistics.median(fw), statistics.median(bw)
+    out = {"workload": W_["name"], "forward_ms": f_ms, "backward_ms": b_ms,
+           "useful_tflop_fwd": (proj + sim) / 1e12, "useful_tflop_bwd": (proj + 2 * proj) / 1e12,
+           "fwd_useful_tflops": (proj + sim) / (f_ms / 1e3) / 1e12,
+           "bwd_useful_tflops": 3 * proj / (b_ms / 1e3) / 1e12,
+           "note": "similarity and gradient GEMMs run two-part BF16 (3 products); projections of BF16 inputs 1 product"}
+    del q, p, W, G, S, am
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

@@ -249,18 +249,21 @@ GIFT_API gift_status gift_get_timing(gift_index* index, gift_timing_t* out);
  * Set-to-set matching score of Eq. 3 after a linear view projection
  * u = W q (W may be NULL for the identity), for training the projection:
  *   S[b, p] = (1/|V(x_b)|) sum_i max_j s(W q_i, W p_j).
- *  - q: device float [sum V_q * d_in]; q_view_offsets: HOST int32 [Bq + 1].
- *  - p: device float [Np * nv_p * d_in]; W: device float [d_out * d_in] or NULL
- *    (then d_out must equal d_in).
+ *  - dtype GIFT_F32 or GIFT_BF16: element type of q, p and W.
+ *  - q: device [sum V_q * d_in]; q_view_offsets: HOST int32 [Bq + 1].
+ *  - p: device [Np * nv_p * d_in]; W: device [d_out * d_in] or NULL (then
+ *    d_out must equal d_in). d_in, d_out multiples of 16.
  *  - S: device float [Bq * Np]; argmax: device int16 [sum V_q * Np], the first
  *    j attaining the max for every (query view, database shape), saved for the
  *    backward pass; nv_p <= 32767.
+ * Products run on the tensor cores; the similarity of the projected views is
+ * evaluated in FP32-level precision (two-part BF16 operands).
  * Errors: EINVAL, ENOMEM, ECUDA.
  */
-GIFT_API gift_status gift_match_forward(const float* q, const int32_t* q_view_offsets, int32_t Bq,
-                               const float* p, int32_t Np, int32_t nv_p, const float* W,
-                               int32_t d_in, int32_t d_out, float* S, int16_t* argmax,
-                               cudaStream_t stream);
+GIFT_API gift_status gift_match_forward(const void* q, const int32_t* q_view_offsets, int32_t Bq,
+                                        const void* p, int32_t Np, int32_t nv_p, const void* W,
+                                        int32_t d_in, int32_t d_out, int32_t dtype, float* S,
+                                        int16_t* argmax, cudaStream_t stream);
 
 /*
  * Gradient of L = sum_{b,p} grad_S[b,p] * S[b,p] through gift_match_forward,
@@ -268,17 +271,18 @@ GIFT_API gift_status gift_match_forward(const float* q, const int32_t* q_view_of
  * linear in the selected pair):
  *   dS/du_i = (v_j/|v_j| - s u_i/|u_i|) / |u_i|, dS/dv_j = (u_i/|u_i| - s v_j/|v_j|) / |v_j|,
  * each scaled by grad_S[b,p] / |V(x_b)|; dW = dU^T Q + dV^T P, dQ = dU W, dP = dV W.
- *  - grad_S: device float [Bq * Np]; argmax from the forward call.
+ *  - grad_S: device float [Bq * Np]; argmax from the forward call; inputs as in
+ *    gift_match_forward (same dtype).
  *  - dW: device float [d_out * d_in] or NULL (skipped; must be NULL when W is);
  *    dQ: device float [sum V_q * d_in] or NULL; dP: device float
- *    [Np * nv_p * d_in] or NULL. Outputs are overwritten.
+ *    [Np * nv_p * d_in] or NULL. Outputs are FP32 and overwritten; d_out <= 1024.
  * Errors: EINVAL, ENOMEM, ECUDA.
  */
-GIFT_API gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, int32_t Bq,
-                                const float* p, int32_t Np, int32_t nv_p, const float* W,
-                                int32_t d_in, int32_t d_out, const float* grad_S,
-                                const int16_t* argmax, float* dW, float* dQ, float* dP,
-                                cudaStream_t stream);
+GIFT_API gift_status gift_match_backward(const void* q, const int32_t* q_view_offsets, int32_t Bq,
+                                         const void* p, int32_t Np, int32_t nv_p, const void* W,
+                                         int32_t d_in, int32_t d_out, int32_t dtype,
+                                         const float* grad_S, const int16_t* argmax, float* dW,
+                                         float* dQ, float* dP, cudaStream_t stream);
 
 /*
  * Request loop over a resident index (serving). Requests of mixed view counts

@@ -89,8 +89,8 @@ _SIGS = {
     "gift_index_info": (_I32, [_P, ctypes.POINTER(_Info)]),
     "gift_set_timing": (_I32, [_P, _I32]),
     "gift_get_timing": (_I32, [_P, ctypes.POINTER(_Timing)]),
-    "gift_match_forward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
-    "gift_match_backward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P, _P,
+    "gift_match_forward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_match_backward": (_I32, [_P, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P,
                                    _P]),
     "gift_server_create": (_I32, [_P, ctypes.POINTER(_ServerParams), ctypes.POINTER(_P)]),
     "gift_server_submit": (_I32, [_P, _P, _I32, ctypes.POINTER(_I64)]),
@@ -260,32 +260,46 @@ class Index:
 
 
 # ---------------------------------------------------------------- differentiation
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError("matching inputs must be float32 or bfloat16 tensors")
+
+
 def match_forward(q, q_offsets, p, W=None, stream=None):
     """S [B, Np] of Eq. 3 after the projection u = W q, and the saved argmax [sum V_q, Np] (int16)."""
     import torch
     offs = _host_offsets(q_offsets)
     Bq = len(offs) - 1
     Np, nv, din = p.shape
+    dt = _dtype_code(q)
+    if p.dtype != q.dtype or (W is not None and W.dtype != q.dtype):
+        raise TypeError("q, p and W must share a dtype")
     dout = W.shape[0] if W is not None else din
     S = torch.empty((Bq, Np), dtype=torch.float32, device=q.device)
     am = torch.empty((q.shape[0], Np), dtype=torch.int16, device=q.device)
     _check(load().gift_match_forward(_ptr(q), ctypes.c_void_p(offs.ctypes.data), Bq, _ptr(p), Np, nv, _ptr(W),
-                                     din, dout, _ptr(S), _ptr(am), _stream(stream)))
+                                     din, dout, dt, _ptr(S), _ptr(am), _stream(stream)))
     return S, am
 
 
 def match_backward(q, q_offsets, p, W, grad_S, argmax, need=(True, True, True), stream=None):
-    """(dW or None, dQ, dP) of sum(grad_S * S) through the saved argmax pair."""
+    """(dW or None, dQ, dP) of sum(grad_S * S) through the saved argmax pair (FP32 gradients)."""
     import torch
     offs = _host_offsets(q_offsets)
     Bq = len(offs) - 1
     Np, nv, din = p.shape
+    dt = _dtype_code(q)
     dout = W.shape[0] if W is not None else din
-    dW = torch.empty_like(W) if (W is not None and need[0]) else None
-    dQ = torch.empty_like(q) if need[1] else None
-    dP = torch.empty_like(p) if need[2] else None
+    f32 = dict(dtype=torch.float32, device=q.device)
+    dW = torch.empty(W.shape, **f32) if (W is not None and need[0]) else None
+    dQ = torch.empty(q.shape, **f32) if need[1] else None
+    dP = torch.empty(p.shape, **f32) if need[2] else None
     _check(load().gift_match_backward(_ptr(q), ctypes.c_void_p(offs.ctypes.data), Bq, _ptr(p), Np, nv, _ptr(W), din,
-                                      dout, _ptr(grad_S.contiguous()), _ptr(argmax), _ptr(dW), _ptr(dQ), _ptr(dP),
+                                      dout, dt, _ptr(grad_S.contiguous()), _ptr(argmax), _ptr(dW), _ptr(dQ), _ptr(dP),
                                       _stream(stream)))
     return dW, dQ, dP
 
@@ -312,8 +326,9 @@ def _autograd_function():
             q, p, W, am = ctx.saved_tensors
             W = W if ctx.has_w else None
             need = (ctx.has_w and ctx.needs_input_grad[3], ctx.needs_input_grad[0], ctx.needs_input_grad[2])
-            dW, dQ, dP = match_backward(q, ctx.q_offsets, p, W, gS.contiguous(), am, need)
-            return dQ, None, dP, dW
+            dW, dQ, dP = match_backward(q, ctx.q_offsets, p, W, gS.float().contiguous(), am, need)
+            cast = (lambda g, like: None if g is None else g.to(like.dtype))
+            return cast(dQ, q), None, cast(dP, p), (cast(dW, W) if ctx.has_w else None)
 
     return GiftMatch
 

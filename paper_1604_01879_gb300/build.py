@@ -32,6 +32,7 @@ SOURCES = [
     "k_exact_tc.cu",
     "k_noalloc.cu",
     "serve.cu",
+    "tc_gemm.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

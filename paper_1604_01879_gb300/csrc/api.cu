@@ -7,7 +7,6 @@
 
 #include "fif_plan.cuh"
 #include "gift_internal.cuh"
-#include "segmax.cuh"
 
 namespace gift {
 
@@ -776,22 +775,23 @@ gift_status gift_get_timing(gift_index* index, gift_timing_t* out) {
   });
 }
 
-gift_status gift_match_forward(const float* q, const int32_t* q_view_offsets, int32_t Bq, const float* p,
-                               int32_t Np, int32_t nv_p, const float* W, int32_t d_in, int32_t d_out, float* S,
+gift_status gift_match_forward(const void* q, const int32_t* q_view_offsets, int32_t Bq, const void* p, int32_t Np,
+                               int32_t nv_p, const void* W, int32_t d_in, int32_t d_out, int32_t dtype, float* S,
                                int16_t* argmax, cudaStream_t stream) {
   return gift::guard("gift_match_forward", [&] {
     GIFT_REQUIRE(q && p && S && argmax, "NULL argument");
     GIFT_REQUIRE(Bq > 0 && Np > 0 && nv_p > 0 && nv_p <= 32767, "bad sizes");
     GIFT_REQUIRE(d_in > 0 && d_in % 16 == 0 && d_out > 0 && d_out % 16 == 0, "dims must be multiples of 16");
     GIFT_REQUIRE(W || d_in == d_out, "d_out must equal d_in without a projection");
+    GIFT_REQUIRE(dtype == GIFT_F32 || dtype == GIFT_BF16, "dtype must be GIFT_F32 or GIFT_BF16");
     std::vector<int32_t> h = gift::host_offsets(q_view_offsets, Bq);
     gift::Scratch sc(stream);
-    gift::match_forward(q, h, Bq, p, Np, nv_p, W, d_in, d_out, S, argmax, sc, stream);
+    gift::match_forward(q, h, Bq, p, Np, nv_p, W, d_in, d_out, dtype, S, argmax, sc, stream);
   });
 }
 
-gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, int32_t Bq, const float* p,
-                                int32_t Np, int32_t nv_p, const float* W, int32_t d_in, int32_t d_out,
+gift_status gift_match_backward(const void* q, const int32_t* q_view_offsets, int32_t Bq, const void* p, int32_t Np,
+                                int32_t nv_p, const void* W, int32_t d_in, int32_t d_out, int32_t dtype,
                                 const float* grad_S, const int16_t* argmax, float* dW, float* dQ, float* dP,
                                 cudaStream_t stream) {
   return gift::guard("gift_match_backward", [&] {
@@ -800,9 +800,11 @@ gift_status gift_match_backward(const float* q, const int32_t* q_view_offsets, i
     GIFT_REQUIRE(d_in > 0 && d_in % 16 == 0 && d_out > 0 && d_out % 16 == 0, "dims must be multiples of 16");
     GIFT_REQUIRE(W || d_in == d_out, "d_out must equal d_in without a projection");
     GIFT_REQUIRE(W || !dW, "dW needs a projection");
+    GIFT_REQUIRE(d_out <= 1024, "d_out must be at most 1024 for the backward");
+    GIFT_REQUIRE(dtype == GIFT_F32 || dtype == GIFT_BF16, "dtype must be GIFT_F32 or GIFT_BF16");
     std::vector<int32_t> h = gift::host_offsets(q_view_offsets, Bq);
     gift::Scratch sc(stream);
-    gift::match_backward(q, h, Bq, p, Np, nv_p, W, d_in, d_out, grad_S, argmax, dW, dQ, dP, sc, stream);
+    gift::match_backward(q, h, Bq, p, Np, nv_p, W, d_in, d_out, dtype, grad_S, argmax, dW, dQ, dP, sc, stream);
   });
 }
 

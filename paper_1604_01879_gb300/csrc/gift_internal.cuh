@@ -197,14 +197,13 @@ void sif_rerank_into(const Index& ix, const int32_t* cand_ids, const float* cand
                      int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, void* scratch,
                      size_t scratch_bytes, cudaStream_t s);
 
-// k_match.cu
-void match_forward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq,
-                   const float* p, int32_t Np, int32_t nv, const float* W, int32_t din,
-                   int32_t dout, float* S, int16_t* argmax, Scratch& sc, cudaStream_t s);
-void match_backward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq,
-                    const float* p, int32_t Np, int32_t nv, const float* W, int32_t din,
-                    int32_t dout, const float* gS, const int16_t* argmax, float* dW,
-                    float* dQ, float* dP, Scratch& sc, cudaStream_t s);
+// k_match.cu (dtype: GIFT_F32 or GIFT_BF16 for q, p and W)
+void match_forward(const void* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const void* p, int32_t Np,
+                   int32_t nv, const void* W, int32_t din, int32_t dout, int32_t dtype, float* S, int16_t* argmax,
+                   Scratch& sc, cudaStream_t s);
+void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const void* p, int32_t Np,
+                    int32_t nv, const void* W, int32_t din, int32_t dout, int32_t dtype, const float* gS,
+                    const int16_t* argmax, float* dW, float* dQ, float* dP, Scratch& sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

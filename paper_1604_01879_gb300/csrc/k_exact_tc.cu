@@ -107,21 +107,16 @@ struct ExactPolicy {
 
 }  // namespace
 
-void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
-                     const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s) {
-  const int D = ix.prm.dim, Nv = ix.prm.views_per_shape;
-  const int64_t N = ix.prm.n_shapes;
-  const int64_t ncols = ix.n_rows;
+void segmax_tc(const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo, int64_t a_rows_alloc, const float* a_inv,
+               const __nv_bfloat16* b_hi, const __nv_bfloat16* b_lo, int64_t b_rows_alloc, const float* b_inv,
+               int64_t ncols, int nv, int D, const int32_t* d_qoff, const std::vector<int32_t>& h_qoff, int32_t B,
+               float* S, int16_t* argmax, int* err, Scratch& sc, cudaStream_t s) {
+  const int64_t N = ncols / nv;
   const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 27) / N);  // cell block <= 1 GiB
-  // every TMA source keeps one box of padding rows past its data
-  const int64_t qrows = nv + tc::kTM;
-  __nv_bfloat16* hi = sc.get<__nv_bfloat16>((size_t)qrows * D);
-  __nv_bfloat16* lo = sc.get<__nv_bfloat16>((size_t)qrows * D);
-  split_rows_bf16(q, nv, D, hi, lo, s);
   unsigned long long* cell = nullptr;
   int64_t cell_rows = 0;
-  const CUtensorMap tB = make_tmap_bf16(ix.ex_hi, ix.ex_rows, D, ExactPolicy::TN);
-  const CUtensorMap tB2 = make_tmap_bf16(ix.ex_lo, ix.ex_rows, D, ExactPolicy::TN);
+  const CUtensorMap tB = make_tmap_bf16(b_hi, b_rows_alloc, D, ExactPolicy::TN);
+  const CUtensorMap tB2 = make_tmap_bf16(b_lo, b_rows_alloc, D, ExactPolicy::TN);
   const int sms = device_sm_count();
   int32_t b0 = 0;
   while (b0 < B) {
@@ -137,19 +132,30 @@ void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_
     p.rows = rows;
     p.ncols = ncols;
     p.n_rt = cdiv(rows, tc::kTM);
-    p.nv = Nv;
+    p.nv = nv;
     p.n_shapes = N;
     p.nkb = (int)cdiv(D, tc::kTK);
-    p.q_inv = q_inv + v0;
-    p.r_inv = ix.row_inv;
+    p.q_inv = a_inv + v0;
+    p.r_inv = b_inv;
     p.cell = cell;
-    const CUtensorMap tA = make_tmap_bf16(hi + v0 * D, qrows - v0, D, tc::kTM);
-    const CUtensorMap tA2 = make_tmap_bf16(lo + v0 * D, qrows - v0, D, tc::kTM);
+    const CUtensorMap tA = make_tmap_bf16(a_hi + v0 * D, a_rows_alloc - v0, D, tc::kTM);
+    const CUtensorMap tA2 = make_tmap_bf16(a_lo + v0 * D, a_rows_alloc - v0, D, tc::kTM);
     const int grid = (int)std::min<int64_t>(sms, p.n_rt * cdiv(ncols, ExactPolicy::TN));
-    tc::launch_engine(tA, tB, tA2, tB2, p, ix.d_err, grid, s);
-    segmax_reduce(cell, N, d_qoff, b0, b1 - b0, (int32_t)v0, S, nullptr, s);
+    tc::launch_engine(tA, tB, tA2, tB2, p, err, grid, s);
+    segmax_reduce(cell, N, d_qoff, b0, b1 - b0, (int32_t)v0, S, argmax, s);
     b0 = b1;
   }
+}
+
+void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
+                     const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s) {
+  const int D = ix.prm.dim;
+  const int64_t qrows = nv + tc::kTM;  // one box of padding rows
+  __nv_bfloat16* hi = sc.get<__nv_bfloat16>((size_t)qrows * D);
+  __nv_bfloat16* lo = sc.get<__nv_bfloat16>((size_t)qrows * D);
+  split_rows_bf16(q, nv, D, hi, lo, s);
+  segmax_tc(hi, lo, qrows, q_inv, ix.ex_hi, ix.ex_lo, ix.ex_rows, ix.row_inv, ix.n_rows, ix.prm.views_per_shape, D,
+            d_qoff, h_qoff, B, S, nullptr, ix.d_err, sc, s);
 }
 
 }  // namespace gift

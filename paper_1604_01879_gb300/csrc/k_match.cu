@@ -1,143 +1,173 @@
 // Matching score of Eq. 3 after a learned linear view projection u = W q,
-// and its gradient through the argmax view pair.
+// and its gradient through the argmax view pair, on the tensor cores.
 //
-// Forward: U = Q W^T, V = P W^T (tile GEMMs), S and the first argmax j* of
-// every (query view, shape) by the segmented-max kernel of the exact match.
+// Forward: U = Q W^T and V = P W^T (engine GEMMs; BF16 inputs multiply
+// exactly in one product, FP32 inputs in the two-part split), then the
+// segmented-max contraction of U and V (two-part split, FP32-level) gives
+// S and the first argmax j* of every (query view, shape).
 // Backward, with c = grad_S[b, p] / |V(x_b)| and s = u_i.v_j*/(|u_i||v_j*|):
 //   dU_i  = (1/|u_i|)  ( sum_p c v_j*/|v_j*|  - (sum_p c s) u_i/|u_i| )
 //   dV_r  = (1/|v_r|)  ( sum_{(i,p): j*=r} c u_i/|u_i| - (sum c s) v_r/|v_r| )
-//   dW    = dU^T Q + dV^T P,  dQ = dU W,  dP = dV W.
-// dU is a gather over shapes (one block per query view), dV a per-shape
-// accumulation over query views in shared memory (no atomics).
+// gathered on the CUDA cores (one block per query view for dU; per shape, a
+// shared-memory accumulation over query views for dV, no atomics), then
+//   dW = dU^T Q + dV^T P,  dQ = dU W,  dP = dV W
+// as engine GEMMs on transposed two-part operands.
 #include "gift_internal.cuh"
 #include "segmax.cuh"
-#include "sgemm_nt.cuh"
+#include "tc_gemm.cuh"
 
 namespace gift {
 
 namespace {
 
-struct EpiStore {
-  float* C;
-  int64_t M, N, ldc;
-  int accumulate;
-  __device__ __forceinline__ void operator()(int64_t m0, int64_t n0, const SgemmFrag& f,
-                                             float (&acc)[8][8]) const {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int64_t m = m0 + f.row(i);
-      if (m >= M) continue;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t n = n0 + f.col(j);
-        if (n < N) {
-          float* c = C + m * ldc + n;
-          *c = accumulate ? *c + acc[i][j] : acc[i][j];
-        }
-      }
-    }
-  }
-};
+// element of an input in FP32 or BF16
+template <typename T>
+__device__ __forceinline__ float ld_f(const T* p, int64_t i);
+template <>
+__device__ __forceinline__ float ld_f<float>(const float* p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
 
-// out[c * ldo + r] = in[r * cols + c] for r < rows, c < cols; zero pad up to ldo
-__global__ void k_transpose(const float* __restrict__ in, int64_t rows, int64_t cols, float* __restrict__ out,
-                            int64_t ldo) {
+// two-part BF16 copy of a row-major [rows, cols] matrix (lo may be null)
+template <typename T>
+__global__ void k_split_any(const T* __restrict__ in, int64_t n, __nv_bfloat16* __restrict__ hi,
+                            __nv_bfloat16* __restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = ld_f<T>(in, i);
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+template <typename T>
+__global__ void k_to_float(const T* __restrict__ in, int64_t n, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ld_f<T>(in, i);
+}
+
+// out[c, r] (two-part BF16, row pitch ld) = in[r, c] for r < rows; zero for rows <= r < ld
+template <typename T>
+__global__ void k_transpose_split(const T* __restrict__ in, int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, int64_t ld) {
   __shared__ float t[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   for (int y = threadIdx.y; y < 32; y += 8) {
     const int64_t r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+    t[y][threadIdx.x] = (r < rows && c < cols) ? ld_f<T>(in, r * cols + c) : 0.f;
   }
   __syncthreads();
   for (int y = threadIdx.y; y < 32; y += 8) {
     const int64_t c = c0 + y, r = r0 + threadIdx.x;
-    if (c < cols && r < ldo) out[c * ldo + r] = t[threadIdx.x][y];
+    if (c < cols && r < ld) {
+      const float v = t[threadIdx.x][y];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[c * ld + r] = h;
+      if (lo) lo[c * ld + r] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
 }
 
-// s[i, p] = cos(u_i, v_{p*nv + j*}) , one warp per (i, p)
-__global__ void k_pair_cos(const float* __restrict__ U, const float* __restrict__ uinv,
-                           const float* __restrict__ V, const float* __restrict__ vinv,
-                           const int16_t* __restrict__ argmax, int64_t nq, int Np, int nv, int dout,
-                           float* __restrict__ s) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nq * Np) return;
-  const int64_t i = w / Np, p = w % Np;
-  int j = argmax[w];
-  if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; never index outside the shape
-  const int64_t r = p * nv + j;
-  const float* u = U + i * dout;
-  const float* v = V + r * dout;
-  float acc = 0.f;
-  for (int d = lane; d < dout; d += 32) acc = fmaf(u[d], v[d], acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) s[w] = acc * uinv[i] * vinv[r];
-}
-
-// dU_i, one block per query view
-__global__ void k_grad_u(const float* __restrict__ U, const float* __restrict__ uinv,
-                         const float* __restrict__ V, const float* __restrict__ vinv,
-                         const int16_t* __restrict__ argmax, const float* __restrict__ s,
-                         const float* __restrict__ gS, const int32_t* __restrict__ vquery,
-                         const int32_t* __restrict__ qoff, int Np, int nv, int dout, float* __restrict__ dU) {
-  extern __shared__ float acc[];  // [dout]
-  __shared__ float tot;
+// dU_i and s[i, p] = cos(u_i, v_{p*nv + j*}) for one query view per block:
+// each warp walks a subset of the shapes, keeps u_i and its share of the dU
+// accumulator in registers (lane owns dims lane, lane+32, ...), and the
+// warps' partials are summed through shared memory at the end.
+template <int DPL>  // dims per lane: dout <= 32 * DPL
+__global__ __launch_bounds__(256) void k_grad_u(const float* __restrict__ U, const float* __restrict__ uinv,
+                                                 const float* __restrict__ V, const float* __restrict__ vinv,
+                                                 const int16_t* __restrict__ argmax, const float* __restrict__ gS,
+                                                 const int32_t* __restrict__ vquery, const int32_t* __restrict__ qoff,
+                                                 int Np, int nv, int dout, float* __restrict__ s_out,
+                                                 float* __restrict__ dU) {
+  __shared__ float part[8][DPL * 32];
+  __shared__ float tot_w[8];
   const int64_t i = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = vquery[i];
   const float invV = 1.f / (float)(qoff[b + 1] - qoff[b]);
-  for (int d = threadIdx.x; d < dout; d += blockDim.x) acc[d] = 0.f;
-  if (threadIdx.x == 0) tot = 0.f;
-  __syncthreads();
-  float t_local = 0.f;
-  for (int p = 0; p < Np; ++p) {
-    const float c = gS[(int64_t)b * Np + p] * invV;
-    if (c == 0.f) continue;
-    const int64_t w = i * Np + p;
-    int j = argmax[w];
-    if (j < 0 || j >= nv) j = 0;
-    const int64_t r = (int64_t)p * nv + j;
-    const float cv = c * vinv[r];
-    const float* v = V + r * dout;
-    for (int d = threadIdx.x; d < dout; d += blockDim.x) acc[d] = fmaf(cv, v[d], acc[d]);
-    if (threadIdx.x == 0) t_local = fmaf(c, s[w], t_local);
-  }
-  if (threadIdx.x == 0) tot = t_local;
-  __syncthreads();
   const float ui = uinv[i];
-  for (int d = threadIdx.x; d < dout; d += blockDim.x)
-    dU[i * dout + d] = ui * (acc[d] - tot * U[i * dout + d] * ui);
+  float u[DPL], acc[DPL];
+#pragma unroll
+  for (int k = 0; k < DPL; ++k) {
+    const int d = lane + 32 * k;
+    u[k] = d < dout ? U[i * dout + d] : 0.f;
+    acc[k] = 0.f;
+  }
+  float tot = 0.f;
+#pragma unroll 2
+  for (int p = w; p < Np; p += 8) {
+    const int64_t wi = i * Np + p;
+    int j = argmax[wi];
+    if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; never index outside the shape
+    const int64_t r = (int64_t)p * nv + j;
+    const float* v = V + r * dout;
+    float vv[DPL];
+    float dot = 0.f;
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = lane + 32 * k;
+      vv[k] = d < dout ? v[d] : 0.f;
+      dot = fmaf(u[k], vv[k], dot);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    const float vi = vinv[r];
+    const float sc = dot * ui * vi;
+    if (lane == 0) s_out[wi] = sc;
+    const float c = gS[(int64_t)b * Np + p] * invV;
+    const float cv = c * vi;
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) acc[k] = fmaf(cv, vv[k], acc[k]);
+    tot = fmaf(c, sc, tot);
+  }
+#pragma unroll
+  for (int k = 0; k < DPL; ++k) part[w][lane + 32 * k] = acc[k];  // lanes past dout hold 0
+  if (lane == 0) tot_w[w] = tot;
+  __syncthreads();
+  float T = 0.f;
+#pragma unroll
+  for (int ww = 0; ww < 8; ++ww) T += tot_w[ww];
+  for (int d = threadIdx.x; d < dout; d += 256) {
+    float a = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) a += part[ww][d];
+    dU[i * dout + d] = ui * (a - T * U[i * dout + d] * ui);
+  }
 }
 
-// dV rows of shape p, columns [d0, d1); one block per (shape, column chunk)
-__global__ void k_grad_v(const float* __restrict__ U, const float* __restrict__ uinv,
-                         const float* __restrict__ V, const float* __restrict__ vinv,
-                         const int16_t* __restrict__ argmax, const float* __restrict__ s,
-                         const float* __restrict__ gS, const int32_t* __restrict__ vquery,
-                         const int32_t* __restrict__ qoff, int64_t nq, int Np, int nv, int dout, int dchunk,
-                         float* __restrict__ dV) {
+// dV rows of shape p, columns [d0, d0 + dchunk); one block per (shape, column
+// chunk); warps walk disjoint query views and add into the shared
+// accumulator with shared-memory atomics.
+__global__ __launch_bounds__(512) void k_grad_v(const float* __restrict__ U, const float* __restrict__ uinv,
+                                                 const float* __restrict__ V, const float* __restrict__ vinv,
+                                                 const int16_t* __restrict__ argmax, const float* __restrict__ s,
+                                                 const float* __restrict__ gS, const int32_t* __restrict__ vquery,
+                                                 const int32_t* __restrict__ qoff, int64_t nq, int Np, int nv,
+                                                 int dout, int dchunk, float* __restrict__ dV) {
   extern __shared__ float sm[];  // acc [nv][dchunk] then ctot [nv]
   float* acc = sm;
   float* ctot = sm + (int64_t)nv * dchunk;
   const int p = blockIdx.x;
   const int d0 = blockIdx.y * dchunk;
   const int dw = min(dchunk, dout - d0);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < nv * dchunk; t += blockDim.x) acc[t] = 0.f;
   for (int t = threadIdx.x; t < nv; t += blockDim.x) ctot[t] = 0.f;
   __syncthreads();
-  for (int64_t i = 0; i < nq; ++i) {
+  for (int64_t i = w; i < nq; i += nw) {
     const int b = vquery[i];
     const float c = gS[(int64_t)b * Np + p] / (float)(qoff[b + 1] - qoff[b]);
     if (c == 0.f) continue;
-    const int64_t w = i * Np + p;
-    int j = argmax[w];
+    const int64_t wi = i * Np + p;
+    int j = argmax[wi];
     if (j < 0 || j >= nv) j = 0;
     const float cu = c * uinv[i];
     const float* u = U + i * dout + d0;
     float* a = acc + (int64_t)j * dchunk;
-    for (int d = threadIdx.x; d < dw; d += blockDim.x) a[d] = fmaf(cu, u[d], a[d]);
-    if (threadIdx.x == 0) ctot[j] = fmaf(c, s[w], ctot[j]);
+    for (int d = lane; d < dw; d += 32) atomicAdd(a + d, cu * u[d]);
+    if (lane == 0) atomicAdd(ctot + j, c * s[wi]);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nv * dw; t += blockDim.x) {
@@ -148,31 +178,81 @@ __global__ void k_grad_v(const float* __restrict__ U, const float* __restrict__ 
   }
 }
 
-__global__ void k_view_query(const int32_t* __restrict__ qoff, int B, int32_t* __restrict__ vq) {
+__global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restrict__ vq) {
   const int b = blockIdx.x;
   for (int v = qoff[b] + threadIdx.x; v < qoff[b + 1]; v += blockDim.x) vq[v] = b;
 }
 
+// two-part BF16 operand with one TMA box of padding rows
+struct Operand {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;  // null: one-part (exact BF16 input)
+  int64_t rows_alloc = 0;
+};
+
+Operand make_operand(const void* x, int dtype, int64_t rows, int cols, bool force_split, Scratch& sc, cudaStream_t s) {
+  Operand o;
+  o.rows_alloc = rows + 128;
+  const int64_t n = rows * cols;
+  o.hi = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * cols);
+  const bool split = dtype == GIFT_F32 || force_split;
+  if (split) o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * cols);
+  if (dtype == GIFT_F32)
+    k_split_any<float><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(static_cast<const float*>(x), n, o.hi, o.lo);
+  else
+    k_split_any<__nv_bfloat16><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), n,
+                                                                        o.hi, o.lo);
+  GIFT_LAUNCHED("k_split_any");
+  return o;
+}
+
+// transposed two-part operand: out [cols, ld] with ld = rows rounded up to 64
+Operand make_transposed(const void* x, int dtype, int64_t rows, int64_t cols, int64_t& ld, Scratch& sc,
+                        cudaStream_t s) {
+  Operand o;
+  ld = cdiv(rows, 64) * 64;
+  o.rows_alloc = cols + 128;
+  o.hi = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
+  o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
+  const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(ld, 32)), blk(32, 8);
+  if (dtype == GIFT_F32)
+    k_transpose_split<float><<<grid, blk, 0, s>>>(static_cast<const float*>(x), rows, cols, o.hi, o.lo, ld);
+  else
+    k_transpose_split<__nv_bfloat16><<<grid, blk, 0, s>>>(static_cast<const __nv_bfloat16*>(x), rows, cols, o.hi,
+                                                          o.lo, ld);
+  GIFT_LAUNCHED("k_transpose_split");
+  return o;
+}
+
+float* as_float(const void* x, int dtype, int64_t n, Scratch& sc, cudaStream_t s) {
+  if (dtype == GIFT_F32) return const_cast<float*>(static_cast<const float*>(x));
+  float* f = sc.get<float>((size_t)n);
+  k_to_float<__nv_bfloat16><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), n, f);
+  GIFT_LAUNCHED("k_to_float");
+  return f;
+}
+
 struct Proj {
-  const float* U;
-  const float* V;
+  float* U;
+  float* V;
   float* uinv;
   float* vinv;
 };
 
-Proj project(const float* q, int64_t nq, const float* p, int64_t nr, const float* W, int din, int dout,
-             Scratch& sc, cudaStream_t s) {
+Proj project(const void* q, int64_t nq, const void* p, int64_t nr, const void* W, int din, int dout, int dtype,
+             int* err, Scratch& sc, cudaStream_t s) {
   Proj P;
   if (W) {
-    float* U = sc.get<float>((size_t)nq * dout);
-    float* V = sc.get<float>((size_t)nr * dout);
-    launch_sgemm_nt(q, nq, W, dout, din, EpiStore{U, nq, dout, dout, 0}, 0, s);
-    launch_sgemm_nt(p, nr, W, dout, din, EpiStore{V, nr, dout, dout, 0}, 0, s);
-    P.U = U;
-    P.V = V;
+    const Operand Qo = make_operand(q, dtype, nq, din, false, sc, s);
+    const Operand Po = make_operand(p, dtype, nr, din, false, sc, s);
+    const Operand Wo = make_operand(W, dtype, dout, din, false, sc, s);
+    P.U = sc.get<float>((size_t)nq * dout);
+    P.V = sc.get<float>((size_t)nr * dout);
+    gemm_tc(Qo.hi, Qo.lo, nq, Qo.rows_alloc, 0, Wo.hi, Wo.lo, dout, Wo.rows_alloc, 0, din, P.U, dout, 0, err, s);
+    gemm_tc(Po.hi, Po.lo, nr, Po.rows_alloc, 0, Wo.hi, Wo.lo, dout, Wo.rows_alloc, 0, din, P.V, dout, 0, err, s);
   } else {
-    P.U = q;
-    P.V = p;
+    P.U = as_float(q, dtype, nq * din, sc, s);
+    P.V = as_float(p, dtype, nr * din, sc, s);
   }
   P.uinv = sc.get<float>(nq);
   P.vinv = sc.get<float>(nr);
@@ -187,74 +267,94 @@ int32_t* device_offsets(const std::vector<int32_t>& h_qoff, Scratch& sc, cudaStr
   return d;
 }
 
-// C [M, N] (+)= A^T-free NT product of row-major A [M, K] and B [N, K]
-void gemm_tn_via_transpose(const float* X, int64_t rows, int64_t colsX, const float* Y, int64_t colsY,
-                           float* C, int accumulate, Scratch& sc, cudaStream_t s) {
-  // C[o, k] = sum_r X[r, o] Y[r, k]: transpose both so the reduction is contiguous
-  const int64_t ldr = cdiv(rows, 16) * 16;
-  float* Xt = sc.get<float>((size_t)colsX * ldr);
-  float* Yt = sc.get<float>((size_t)colsY * ldr);
-  dim3 blk(32, 8);
-  k_transpose<<<dim3((unsigned)cdiv(colsX, 32), (unsigned)cdiv(ldr, 32)), blk, 0, s>>>(X, rows, colsX, Xt, ldr);
-  GIFT_LAUNCHED("k_transpose");
-  k_transpose<<<dim3((unsigned)cdiv(colsY, 32), (unsigned)cdiv(ldr, 32)), blk, 0, s>>>(Y, rows, colsY, Yt, ldr);
-  GIFT_LAUNCHED("k_transpose");
-  launch_sgemm_nt(Xt, colsX, Yt, colsY, (int)ldr, EpiStore{C, colsX, colsY, colsY, accumulate}, 0, s);
+int* device_flag(Scratch& sc, cudaStream_t s) {
+  int* f = sc.get<int>(1);
+  GIFT_CUDA(cudaMemsetAsync(f, 0, sizeof(int), s));
+  return f;
 }
 
 }  // namespace
 
-void match_forward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const float* p, int32_t Np,
-                   int32_t nv, const float* W, int32_t din, int32_t dout, float* S, int16_t* argmax, Scratch& sc,
-                   cudaStream_t s) {
+void match_forward(const void* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const void* p, int32_t Np,
+                   int32_t nv, const void* W, int32_t din, int32_t dout, int32_t dtype, float* S, int16_t* argmax,
+                   Scratch& sc, cudaStream_t s) {
   const int64_t nq = h_qoff[Bq];
   const int64_t nr = (int64_t)Np * nv;
-  Proj P = project(q, nq, p, nr, W, din, dout, sc, s);
+  int* err = device_flag(sc, s);
+  const Proj P = project(q, nq, p, nr, W, din, dout, dtype, err, sc, s);
+  const Operand Uo = make_operand(P.U, GIFT_F32, nq, dout, true, sc, s);
+  const Operand Vo = make_operand(P.V, GIFT_F32, nr, dout, true, sc, s);
   int32_t* d_qoff = device_offsets(h_qoff, sc, s);
-  segmax_scores(P.U, P.uinv, nq, P.V, P.vinv, Np, nv, dout, d_qoff, h_qoff, Bq, S, argmax, sc, s);
+  segmax_tc(Uo.hi, Uo.lo, Uo.rows_alloc, P.uinv, Vo.hi, Vo.lo, Vo.rows_alloc, P.vinv, nr, nv, dout, d_qoff, h_qoff,
+            Bq, S, argmax, err, sc, s);
 }
 
-void match_backward(const float* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const float* p, int32_t Np,
-                    int32_t nv, const float* W, int32_t din, int32_t dout, const float* gS, const int16_t* argmax,
-                    float* dW, float* dQ, float* dP, Scratch& sc, cudaStream_t s) {
+void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const void* p, int32_t Np,
+                    int32_t nv, const void* W, int32_t din, int32_t dout, int32_t dtype, const float* gS,
+                    const int16_t* argmax, float* dW, float* dQ, float* dP, Scratch& sc, cudaStream_t s) {
   const int64_t nq = h_qoff[Bq];
   const int64_t nr = (int64_t)Np * nv;
-  Proj P = project(q, nq, p, nr, W, din, dout, sc, s);
+  int* err = device_flag(sc, s);
+  const Proj P = project(q, nq, p, nr, W, din, dout, dtype, err, sc, s);
   int32_t* d_qoff = device_offsets(h_qoff, sc, s);
   int32_t* vquery = sc.get<int32_t>(nq);
-  k_view_query<<<(unsigned)Bq, 128, 0, s>>>(d_qoff, Bq, vquery);
+  k_view_query<<<(unsigned)Bq, 128, 0, s>>>(d_qoff, vquery);
   GIFT_LAUNCHED("k_view_query");
   float* sv = sc.get<float>((size_t)nq * Np);
-  k_pair_cos<<<(unsigned)cdiv(nq * Np * 32, 256), 256, 0, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, nq, Np, nv,
-                                                                dout, sv);
-  GIFT_LAUNCHED("k_pair_cos");
-  // gradients w.r.t. the projected views (W == NULL: these are dQ, dP)
+  // gradients w.r.t. the projected views (without a projection these are dQ, dP)
   float* dU = (W || !dQ) ? sc.get<float>((size_t)nq * dout) : dQ;
   float* dV = (W || !dP) ? sc.get<float>((size_t)nr * dout) : dP;
-  GIFT_CUDA(cudaFuncSetAttribute(k_grad_u, cudaFuncAttributeMaxDynamicSharedMemorySize, dout * 4));
-  k_grad_u<<<(unsigned)nq, 256, (size_t)dout * 4, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, sv, gS, vquery, d_qoff,
-                                                       Np, nv, dout, dU);
+  const int dpl = (int)cdiv(dout, 32);
+  switch (dpl <= 1 ? 1 : dpl <= 2 ? 2 : dpl <= 4 ? 4 : dpl <= 8 ? 8 : dpl <= 16 ? 16 : dpl <= 32 ? 32 : 0) {
+#define GIFT_GRAD_U(n)                                                                                      \
+  case n:                                                                                                   \
+    k_grad_u<n><<<(unsigned)nq, 256, 0, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, gS, vquery, d_qoff, Np, nv, \
+                                             dout, sv, dU);                                                 \
+    break;
+    GIFT_GRAD_U(1)
+    GIFT_GRAD_U(2)
+    GIFT_GRAD_U(4)
+    GIFT_GRAD_U(8)
+    GIFT_GRAD_U(16)
+    GIFT_GRAD_U(32)
+#undef GIFT_GRAD_U
+    default:
+      fail(GIFT_EINVAL, "d_out must be at most 1024 for the backward");
+  }
   GIFT_LAUNCHED("k_grad_u");
   int dchunk = dout;
   while ((int64_t)nv * dchunk * 4 + nv * 4 > 200 * 1024 && dchunk > 32) dchunk = (dchunk + 1) / 2;
   GIFT_REQUIRE((int64_t)nv * dchunk * 4 + nv * 4 <= 200 * 1024, "views per shape too large for the backward");
   const size_t smem = (size_t)nv * dchunk * 4 + (size_t)nv * 4;
   GIFT_CUDA(cudaFuncSetAttribute(k_grad_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_grad_v<<<dim3((unsigned)Np, (unsigned)cdiv(dout, dchunk)), 256, smem, s>>>(
+  k_grad_v<<<dim3((unsigned)Np, (unsigned)cdiv(dout, dchunk)), 512, smem, s>>>(
       P.U, P.uinv, P.V, P.vinv, argmax, sv, gS, vquery, d_qoff, nq, Np, nv, dout, dchunk, dV);
   GIFT_LAUNCHED("k_grad_v");
-  if (W) {
-    if (dW) {
-      gemm_tn_via_transpose(dU, nq, dout, q, din, dW, 0, sc, s);
-      gemm_tn_via_transpose(dV, nr, dout, p, din, dW, 1, sc, s);
+  if (!W) return;
+  if (dW) {
+    int64_t ldq = 0, ldr = 0;
+    const Operand dUt = make_transposed(dU, GIFT_F32, nq, dout, ldq, sc, s);
+    const Operand Qt = make_transposed(q, dtype, nq, din, ldq, sc, s);
+    gemm_tc(dUt.hi, dUt.lo, dout, dUt.rows_alloc, ldq, Qt.hi, Qt.lo, din, Qt.rows_alloc, ldq, (int)ldq, dW, din, 0,
+            err, s);
+    const Operand dVt = make_transposed(dV, GIFT_F32, nr, dout, ldr, sc, s);
+    const Operand Pt = make_transposed(p, dtype, nr, din, ldr, sc, s);
+    gemm_tc(dVt.hi, dVt.lo, dout, dVt.rows_alloc, ldr, Pt.hi, Pt.lo, din, Pt.rows_alloc, ldr, (int)ldr, dW, din, 1,
+            err, s);
+  }
+  if (dQ || dP) {
+    int64_t ldo = 0;
+    const Operand Wt = make_transposed(W, dtype, dout, din, ldo, sc, s);  // [din, ldo], K = dout
+    if (dQ) {
+      const Operand dUo = make_operand(dU, GIFT_F32, nq, dout, true, sc, s);
+      gemm_tc(dUo.hi, dUo.lo, nq, dUo.rows_alloc, dout, Wt.hi, Wt.lo, din, Wt.rows_alloc, ldo, dout, dQ, din, 0, err,
+              s);
     }
-    // dQ = dU W: NT product with W^T [din, dout]
-    float* Wt = sc.get<float>((size_t)din * dout);
-    k_transpose<<<dim3((unsigned)cdiv(din, 32), (unsigned)cdiv(dout, 32)), dim3(32, 8), 0, s>>>(W, dout, din, Wt,
-                                                                                            dout);
-    GIFT_LAUNCHED("k_transpose");
-    if (dQ) launch_sgemm_nt(dU, nq, Wt, din, dout, EpiStore{dQ, nq, din, din, 0}, 0, s);
-    if (dP) launch_sgemm_nt(dV, nr, Wt, din, dout, EpiStore{dP, nr, din, din, 0}, 0, s);
+    if (dP) {
+      const Operand dVo = make_operand(dV, GIFT_F32, nr, dout, true, sc, s);
+      gemm_tc(dVo.hi, dVo.lo, nr, dVo.rows_alloc, dout, Wt.hi, Wt.lo, din, Wt.rows_alloc, ldo, dout, dP, din, 0, err,
+              s);
+    }
   }
 }
 

@@ -148,9 +148,10 @@ __device__ __forceinline__ void named_bar_sync(int id, int threads) {
 
 }  // namespace tc
 
-// host: 2-D BF16 tensor map over a row-major [rows, cols] matrix, box
-// {64 columns (128 bytes), box_rows rows}, 128-byte swizzle, zero fill outside.
-CUtensorMap make_tmap_bf16(const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// host: 2-D BF16 tensor map over a row-major [rows, cols] matrix with a row
+// pitch of `pitch` elements (0 = cols), box {64 columns (128 bytes), box_rows
+// rows}, 128-byte swizzle, zero fill outside.
+CUtensorMap make_tmap_bf16(const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows, uint64_t pitch = 0);
 int device_sm_count();
 
 }  // namespace gift

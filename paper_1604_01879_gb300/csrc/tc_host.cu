@@ -25,15 +25,16 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-CUtensorMap make_tmap_bf16(const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+CUtensorMap make_tmap_bf16(const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows, uint64_t pitch) {
+  if (pitch == 0) pitch = cols;
   GIFT_REQUIRE(reinterpret_cast<uintptr_t>(base) % 16 == 0, "tensor map base must be 16-byte aligned");
-  GIFT_REQUIRE((cols * 2) % 16 == 0, "tensor map row pitch must be a multiple of 16 bytes");
+  GIFT_REQUIRE((pitch * 2) % 16 == 0 && pitch >= cols, "tensor map row pitch must be >= cols and a multiple of 16 bytes");
   GIFT_REQUIRE(box_rows >= 1 && box_rows <= 256, "tensor map box rows must be in [1, 256]");
   // callers pad every source by one box, so a tile never leaves the allocation
   GIFT_REQUIRE(rows >= box_rows, "tensor map extent must cover at least one box");
   CUtensorMap m;
   const cuuint64_t dims[2] = {cols, rows > 0 ? rows : 1};
-  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint64_t strides[1] = {pitch * 2};
   const cuuint32_t box[2] = {64u, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,

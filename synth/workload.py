@@ -220,6 +220,22 @@ def kmeans_codebook(sample: np.ndarray, k: int, seed: int, iters: int) -> np.nda
     return C.astype(np.float32)
 
 
+def projection_matrix(d_out: int, d_in: int, seed: int, std: float) -> np.ndarray:
+    """Seeded Gaussian initialisation of a linear view projection, float32 [d_out, d_in]."""
+    return (_gen(seed, 0).standard_normal((d_out, d_in)) * std).astype(np.float32)
+
+
+def upstream_grad(rows: int, cols: int, seed: int) -> np.ndarray:
+    """Seeded N(0, 1) upstream gradient dL/dS, float32 [rows, cols]."""
+    return _gen(seed, 0).standard_normal((rows, cols)).astype(np.float32)
+
+
+# differentiation workload: 256 query shapes x 64 views against 4,096 database
+# shapes x 64 views, D = 4096, BF16, projection 4096 -> 512 with std 1/64
+DIFF_WORKLOAD = dict(name="match256x4096x64_d4096_p512_bf16", n_queries=256, n_shapes=4096, n_views=64,
+                     dim=4096, d_out=512, w_std=1.0 / 64, n_classes=40, seed=4)
+
+
 def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None = None):
     """Database views, codebook and queries of a config as float32 arrays.
 

@@ -1,0 +1,148 @@
+"""Full-size parity on sampled outputs, in the launch configuration bench.py times.
+
+ModelNet40-sized index (12,000 shapes x 64 views x D=4096, K=1024, BF16 store,
+FP32 rescore of the top 200, S-IF k1=50) queried with one 1,000-query batch:
+sampled codes, the full top-100 of sampled queries against the oracle's Eq. 4
+ranking (the oracle quantises all 768,000 database views in float64), S-IF
+entries and S' of sampled shapes. Differentiation workload (256 x 64 query
+views against 4,096 x 64 database views, D=4096 BF16, projection to 512):
+S, argmax and dQ of sampled query views against the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import gift_oracle as O
+from synth import CONFIGS, make_config_inputs, DIFF_WORKLOAD, shape_views, projection_matrix, upstream_grad
+from tests.parity import assert_codes, assert_topk, code_margins, recall
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2(gpu_lib):
+    import torch
+    cfg = CONFIGS["db12000x64_d4096_k1024"]
+    d = make_config_inputs(cfg)
+    N, Nv, D, K = cfg.n_shapes, cfg.n_views, cfg.dim, cfg.n_codewords
+    ix = gpu_lib.Index(torch.from_numpy(d["db"]).cuda(), torch.from_numpy(d["codebook"]).cuda(), N, Nv, K,
+                       storage=cfg.storage, query_ma=cfg.query_ma, sif_k1=cfg.sif_k1, rescore_r=cfg.rescore_r,
+                       keep_exact=False)
+    q = torch.from_numpy(d["q"]).cuda()
+    ids, sc = ix.query(q, d["q_off"], mode="fif", topk=cfg.topk)
+    torch.cuda.synchronize()
+    db_codes = O.quantize(d["db"].reshape(-1, D), d["codebook"], 1).reshape(N, Nv)
+    yield dict(cfg=cfg, d=d, ix=ix, ids=ids.cpu().numpy(), sc=sc.cpu().numpy(), q=q, db_codes=db_codes)
+    ix.close()
+
+
+def _oracle_row(c, Qb):
+    off = np.array([0, len(Qb)])
+    qc = O.quantize(Qb, c["d"]["codebook"], c["cfg"].query_ma)
+    return O.fif_scores(Qb, off, qc, c["d"]["db"], c["db_codes"])[0]
+
+
+def test_sampled_codes(c2):
+    import torch
+    cfg, d = c2["cfg"], c2["d"]
+    codes, off, rows = c2["ix"].export_fif()
+    g = np.random.default_rng(0)
+    pick = g.choice(cfg.n_shapes * cfg.n_views, 3000, replace=False)
+    X = d["db"].reshape(-1, cfg.dim)
+    assert_codes(codes[pick].reshape(-1, 1), c2["db_codes"].reshape(-1)[pick].reshape(-1, 1),
+                 code_margins(X[pick], d["codebook"], 1))
+    qp = g.choice(len(d["q"]), 2000, replace=False)
+    qcodes = c2["ix"].assign(torch.from_numpy(d["q"][qp]).cuda(), 1).cpu().numpy()
+    assert_codes(qcodes, O.quantize(d["q"][qp], d["codebook"], 1), code_margins(d["q"][qp], d["codebook"], 1))
+    assert off[-1] == cfg.n_shapes * cfg.n_views
+
+
+def test_sampled_queries_top100_and_recall(c2):
+    d, cfg = c2["d"], c2["cfg"]
+    qoff = d["q_off"]
+    rec = []
+    for b in (0, 333, 999):
+        ref = _oracle_row(c2, d["q"][qoff[b]:qoff[b + 1]])
+        assert_topk(c2["ids"][b], c2["sc"][b], ref, cfg.topk)
+        rec.append(recall(c2["ids"][b], ref, cfg.topk))
+    assert min(rec) >= 0.99
+
+
+def test_sampled_sif_entries_and_rerank(c2):
+    import torch
+    d, cfg = c2["d"], c2["cfg"]
+    N, Nv, k1 = cfg.n_shapes, cfg.n_views, cfg.sif_k1
+    off, ids, mem, card = c2["ix"].export_sif()
+    X = d["db"]
+
+    def F(p):  # oracle activation row of database shape p (Eq. 7, p as a query)
+        return O.membership(_oracle_row(c2, X[p]), k1)
+
+    for p in (5, 6789):
+        Fp = F(p)
+        srt = -np.sort(-_oracle_row(c2, X[p]))
+        if srt[k1 - 1] - srt[k1] <= 2e-5:
+            continue  # near tie at the k1 boundary: several sets are correct
+        # entries that list p are exactly p's neighbours
+        nb = np.nonzero(Fp)[0]
+        for i in nb:
+            seg = ids[off[i]:off[i + 1]]
+            j = np.searchsorted(seg, p)
+            assert j < len(seg) and seg[j] == p
+            assert abs(mem[off[i] + j] / 2.0 ** 31 - Fp[i]) < 2e-5
+        assert abs(card[p] / 2.0 ** 31 - Fp.sum()) < 1e-3
+    # S' of the re-ranked top-5 of one query against the oracle's Eq. 8
+    b = 0
+    qoff = d["q_off"]
+    rid, rsp = c2["ix"].rerank(torch.from_numpy(c2["ids"][:1]).cuda(), torch.from_numpy(c2["sc"][:1]).cuda(),
+                               k1=k1, topk=5)
+    rid, rsp = rid.cpu().numpy()[0], rsp.cpu().numpy()[0]
+    Fq = O.membership(_oracle_row(c2, d["q"][qoff[b]:qoff[b + 1]]), k1)
+    for p, v in zip(rid, rsp):
+        assert abs(O.contextual(Fq, F(int(p))) - v) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def diff(gpu_lib):
+    import torch
+    W_ = DIFF_WORKLOAD
+    nq, N, nv, D, dout, s = W_["n_queries"], W_["n_shapes"], W_["n_views"], W_["dim"], W_["d_out"], W_["seed"]
+    Q = shape_views(0, nq, nv, D, W_["n_classes"], 2000 + s, 4000 + s).reshape(nq * nv, D)
+    P = shape_views(0, N, nv, D, W_["n_classes"], 1000 + s, 4000 + s)
+    Wm = projection_matrix(dout, D, 3000 + s, W_["w_std"])
+    G = upstream_grad(nq, N, 5000 + s)
+    qb = torch.from_numpy(Q).cuda().to(torch.bfloat16)
+    pb = torch.from_numpy(P).cuda().to(torch.bfloat16)
+    wb = torch.from_numpy(Wm).cuda().to(torch.bfloat16)
+    off = np.arange(0, nq * nv + 1, nv, dtype=np.int32)
+    S, am = gpu_lib.match_forward(qb, off, pb, wb)
+    dW, dQ, dP = gpu_lib.match_backward(qb, off, pb, wb, torch.from_numpy(G).cuda(), am, need=(False, True, False))
+    Qf, Pf, Wf = (t.float().cpu().numpy() for t in (qb, pb, wb))
+    yield dict(S=S.cpu().numpy(), am=am.cpu().numpy(), dQ=dQ.cpu().numpy(), Q=Qf, P=Pf, W=Wf, G=G, nv=nv, N=N)
+
+
+def test_differentiation_sampled_views(diff):
+    Q, P, W, G, nv, N = diff["Q"], diff["P"], diff["W"], diff["G"], diff["nv"], diff["N"]
+    V = P.reshape(-1, P.shape[2]).astype(np.float64) @ W.T.astype(np.float64)
+    Vn = V / np.linalg.norm(V, axis=1, keepdims=True)
+    for b in (3, 200):
+        rows = np.arange(b * nv, (b + 1) * nv)
+        U = Q[rows].astype(np.float64) @ W.T.astype(np.float64)
+        Un = U / np.linalg.norm(U, axis=1, keepdims=True)
+        s = (Un @ Vn.T).reshape(nv, N, nv)
+        S = s.max(axis=2).mean(axis=0)
+        assert np.allclose(diff["S"][b], S, rtol=1e-5, atol=1e-6)
+        top2 = np.sort(s, axis=2)[:, :, -2:]
+        clear = (top2[:, :, 1] - top2[:, :, 0]) > 1e-4
+        assert np.array_equal(diff["am"][rows][clear], s.argmax(axis=2)[clear])
+        # dQ of the first view: the GPU's argmax must attain the max (within the
+        # near-tie window), and the gradient through that argmax must match
+        i = 0
+        j = diff["am"][rows[i]].astype(np.int64)
+        assert np.all(s[i, np.arange(N), j] >= s[i].max(axis=1) - 1e-4)
+        c = G[b] / nv
+        vsel = Vn[np.arange(N) * nv + j]
+        ssel = s[i, np.arange(N), j]
+        nu = np.linalg.norm(U[i])
+        dU = ((c[:, None] * vsel).sum(0) - (c * ssel).sum() * Un[i]) / nu
+        dq = dU @ W.astype(np.float64)
+        assert np.allclose(diff["dQ"][rows[i]], dq, rtol=1e-4, atol=1e-5 * np.abs(dq).max())

@@ -76,3 +76,29 @@ def test_scale_invariants_on_gpu(gpu_lib):
     dq = dQ.double().cpu().numpy()
     assert np.abs((Q * dq).sum(1)).max() < 1e-4 * np.abs(dq).max() * np.abs(Q).max() * Q.shape[1] ** 0.5
     assert abs((W * dW.double().cpu().numpy()).sum()) < 1e-4 * np.abs(dW.cpu().numpy()).sum() * np.abs(W).max()
+
+
+def test_bf16_inputs_forward_backward(gpu_lib):
+    """BF16 features and projection (the C4 dtype): compared with the oracle on the
+    float64 values of the same BF16 numbers."""
+    import torch
+    Q, off, P, W, G = _tie_free(5, B=3, Np=19, nv=8, din=64, dout=32, margin=2e-3)
+    qb = torch.from_numpy(Q).to(torch.bfloat16).cuda()
+    pb = torch.from_numpy(P).to(torch.bfloat16).cuda()
+    wb = torch.from_numpy(W).to(torch.bfloat16).cuda()
+    Qf, Pf, Wf = (t.float().cpu().numpy() for t in (qb, pb, wb))
+    S, am = gpu_lib.match_forward(qb, off, pb, wb)
+    Sr, jr = O.match_forward(Qf, off, Pf, Wf)
+    assert np.allclose(S.cpu().numpy(), Sr, rtol=1e-5, atol=1e-6)
+    assert np.array_equal(am.cpu().numpy().astype(np.int64), jr)
+    dW, dQ, dP = gpu_lib.match_backward(qb, off, pb, wb, torch.from_numpy(G).cuda(), am)
+    rW, rQ, rP = O.match_backward(Qf, off, Pf, Wf, G)
+    scale = max(np.abs(rQ).max(), np.abs(rP).max())
+    assert np.allclose(dQ.cpu().numpy(), rQ, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dP.cpu().numpy(), rP, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
+    # autograd returns gradients in the input dtype
+    q = qb.clone().requires_grad_(True)
+    S2 = gpu_lib.GiftMatch.apply(q, off, pb, wb)
+    (S2 * torch.from_numpy(G).cuda()).sum().backward()
+    assert q.grad.dtype == torch.bfloat16
