@@ -48,10 +48,16 @@ struct ExactPolicy {
     return it;
   }
   // never an empty chunk: each chunk must write its own accumulator
-  __device__ __forceinline__ int nchunks(const Item&) const { return nkb < kChunks ? nkb : kChunks; }
+  // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
+  // x 4 sub-steps per k-block); short reductions use one chunk
+  __device__ __forceinline__ int nch() const {
+    const int want = (nkb * 12 + 191) / 192;
+    return want < 1 ? 1 : (want > kChunks ? kChunks : want);
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return nch(); }
   __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
     br = (int)it.c0;
-    const int nch = nkb < kChunks ? nkb : kChunks;
+    const int nch = this->nch();
     kb0 = (int)((int64_t)nkb * c / nch);
     kb1 = (int)((int64_t)nkb * (c + 1) / nch);
   }
@@ -79,29 +85,30 @@ struct ExactPolicy {
     const int64_t row = it.r0 + m;
     const float qi = q_inv[row];
     unsigned long long* crow = cell + row * n_shapes;
-    int64_t cur = -1;
+    // walk the columns keeping (shape, j) incrementally: no division per column
+    int64_t shape = it.c0 / nv;
+    int j = (int)(it.c0 - shape * nv);
     float best = 0.f;
     int bj = 0;
+    bool open = false;
 #pragma unroll
     for (int c = 0; c < TN; ++c) {
       if (c < it.nc) {
-        const int64_t n = it.c0 + c;
-        const int64_t shape = n / nv;
-        const int j = (int)(n - shape * nv);
         const float v = x.sum[c] * qi * ri[c];
-        if (shape != cur) {
-          if (cur >= 0)
-            atomicMax(crow + cur, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
-          cur = shape;
+        if (!open || v > best) {
           best = v;
           bj = j;
-        } else if (v > best) {
-          best = v;
-          bj = j;
+          open = true;
+        }
+        if (++j == nv) {
+          atomicMax(crow + shape, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
+          ++shape;
+          j = 0;
+          open = false;
         }
       }
     }
-    if (cur >= 0) atomicMax(crow + cur, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
+    if (open) atomicMax(crow + shape, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
   }
 };
 

@@ -137,44 +137,73 @@ __global__ __launch_bounds__(256) void k_grad_u(const float* __restrict__ U, con
   }
 }
 
-// dV rows of shape p, columns [d0, d0 + dchunk); one block per (shape, column
-// chunk); warps walk disjoint query views and add into the shared
-// accumulator with shared-memory atomics.
+// dV rows of shape p: one block per shape, 16 warps; warp w owns the shape's
+// rows j = w, w + 16, ... (accumulators in registers, lane owns dims lane,
+// lane + 32, ...), scans the argmax column of the shape for the query views
+// that selected one of its rows and adds c * u_i / |u_i| there. No atomics;
+// every row of U is read once per shape, from L2.
+template <int DPL>
 __global__ __launch_bounds__(512) void k_grad_v(const float* __restrict__ U, const float* __restrict__ uinv,
                                                  const float* __restrict__ V, const float* __restrict__ vinv,
                                                  const int16_t* __restrict__ argmax, const float* __restrict__ s,
                                                  const float* __restrict__ gS, const int32_t* __restrict__ vquery,
                                                  const int32_t* __restrict__ qoff, int64_t nq, int Np, int nv,
-                                                 int dout, int dchunk, float* __restrict__ dV) {
-  extern __shared__ float sm[];  // acc [nv][dchunk] then ctot [nv]
-  float* acc = sm;
-  float* ctot = sm + (int64_t)nv * dchunk;
+                                                 int dout, float* __restrict__ dV) {
+  constexpr int RPW = 4;  // rows per warp per pass
   const int p = blockIdx.x;
-  const int d0 = blockIdx.y * dchunk;
-  const int dw = min(dchunk, dout - d0);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < nv * dchunk; t += blockDim.x) acc[t] = 0.f;
-  for (int t = threadIdx.x; t < nv; t += blockDim.x) ctot[t] = 0.f;
-  __syncthreads();
-  for (int64_t i = w; i < nq; i += nw) {
-    const int b = vquery[i];
-    const float c = gS[(int64_t)b * Np + p] / (float)(qoff[b + 1] - qoff[b]);
-    if (c == 0.f) continue;
-    const int64_t wi = i * Np + p;
-    int j = argmax[wi];
-    if (j < 0 || j >= nv) j = 0;
-    const float cu = c * uinv[i];
-    const float* u = U + i * dout + d0;
-    float* a = acc + (int64_t)j * dchunk;
-    for (int d = lane; d < dw; d += 32) atomicAdd(a + d, cu * u[d]);
-    if (lane == 0) atomicAdd(ctot + j, c * s[wi]);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nv * dw; t += blockDim.x) {
-    const int j = t / dw, d = t % dw;
-    const int64_t r = (int64_t)p * nv + j;
-    const float vi = vinv[r];
-    dV[r * dout + d0 + d] = vi * (acc[(int64_t)j * dchunk + d] - ctot[j] * V[r * dout + d0 + d] * vi);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j0 = w * RPW; j0 < nv; j0 += 16 * RPW) {
+    float acc[RPW][DPL];
+    float ct[RPW];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      ct[t] = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) acc[t][k] = 0.f;
+    }
+    for (int64_t i0 = 0; i0 < nq; i0 += 32) {
+      const int64_t i = i0 + lane;
+      int j = -1;
+      if (i < nq) {
+        j = argmax[i * Np + p];
+        if (j < 0 || j >= nv) j = 0;
+      }
+      unsigned hit = __ballot_sync(0xffffffffu, j >= j0 && j < j0 + RPW);
+      while (hit) {
+        const int src = __ffs(hit) - 1;
+        hit &= hit - 1;
+        const int64_t ii = i0 + src;
+        const int jj = __shfl_sync(0xffffffffu, j, src) - j0;
+        const int b = vquery[ii];
+        const float c = gS[(int64_t)b * Np + p] / (float)(qoff[b + 1] - qoff[b]);
+        const float cu = c * uinv[ii];
+        const float sc = s[ii * Np + p];
+        const float* u = U + ii * dout;
+#pragma unroll
+        for (int t = 0; t < RPW; ++t) {
+          if (t == jj) {
+#pragma unroll
+            for (int k = 0; k < DPL; ++k) {
+              const int d = lane + 32 * k;
+              if (d < dout) acc[t][k] = fmaf(cu, u[d], acc[t][k]);
+            }
+            ct[t] = fmaf(c, sc, ct[t]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int j = j0 + t;
+      if (j >= nv) continue;
+      const int64_t r = (int64_t)p * nv + j;
+      const float vi = vinv[r];
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) {
+        const int d = lane + 32 * k;
+        if (d < dout) dV[r * dout + d] = vi * (acc[t][k] - ct[t] * V[r * dout + d] * vi);
+      }
+    }
   }
 }
 
@@ -322,13 +351,22 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
       fail(GIFT_EINVAL, "d_out must be at most 1024 for the backward");
   }
   GIFT_LAUNCHED("k_grad_u");
-  int dchunk = dout;
-  while ((int64_t)nv * dchunk * 4 + nv * 4 > 200 * 1024 && dchunk > 32) dchunk = (dchunk + 1) / 2;
-  GIFT_REQUIRE((int64_t)nv * dchunk * 4 + nv * 4 <= 200 * 1024, "views per shape too large for the backward");
-  const size_t smem = (size_t)nv * dchunk * 4 + (size_t)nv * 4;
-  GIFT_CUDA(cudaFuncSetAttribute(k_grad_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_grad_v<<<dim3((unsigned)Np, (unsigned)cdiv(dout, dchunk)), 512, smem, s>>>(
-      P.U, P.uinv, P.V, P.vinv, argmax, sv, gS, vquery, d_qoff, nq, Np, nv, dout, dchunk, dV);
+  switch (dpl <= 1 ? 1 : dpl <= 2 ? 2 : dpl <= 4 ? 4 : dpl <= 8 ? 8 : dpl <= 16 ? 16 : dpl <= 32 ? 32 : 0) {
+#define GIFT_GRAD_V(n)                                                                                      \
+  case n:                                                                                                   \
+    k_grad_v<n><<<(unsigned)Np, 512, 0, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, sv, gS, vquery, d_qoff, nq, Np, \
+                                             nv, dout, dV);                                                 \
+    break;
+    GIFT_GRAD_V(1)
+    GIFT_GRAD_V(2)
+    GIFT_GRAD_V(4)
+    GIFT_GRAD_V(8)
+    GIFT_GRAD_V(16)
+    GIFT_GRAD_V(32)
+#undef GIFT_GRAD_V
+    default:
+      fail(GIFT_EINVAL, "d_out must be at most 1024 for the backward");
+  }
   GIFT_LAUNCHED("k_grad_v");
   if (!W) return;
   if (dW) {

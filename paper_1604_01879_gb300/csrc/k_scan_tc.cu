@@ -193,10 +193,16 @@ struct RescorePolicy : ListSched {
   __device__ __forceinline__ int64_t total() const { return total_items(); }
   __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
   // never an empty chunk: each chunk must write its own accumulator
-  __device__ __forceinline__ int nchunks(const Item&) const { return nkb < kRescChunks ? nkb : kRescChunks; }
+  // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
+  // x 4 sub-steps per k-block); short reductions use one chunk
+  __device__ __forceinline__ int nch() const {
+    const int want = (nkb * 12 + 191) / 192;
+    return want < 1 ? 1 : (want > kRescChunks ? kRescChunks : want);
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return nch(); }
   __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
     br = (int)it.e0;
-    const int nch = nkb < kRescChunks ? nkb : kRescChunks;
+    const int nch = this->nch();
     kb0 = (int)((int64_t)nkb * c / nch);
     kb1 = (int)((int64_t)nkb * (c + 1) / nch);
   }

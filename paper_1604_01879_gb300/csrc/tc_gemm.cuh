@@ -39,9 +39,15 @@ struct GemmPolicy {
     it.nc = (int)min((int64_t)TN, N - it.c0);
     return it;
   }
-  __device__ __forceinline__ int nchunks(const Item&) const { return nkb < kChunks ? nkb : kChunks; }
+  // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
+  // x 4 sub-steps per k-block); short reductions use one chunk
+  __device__ __forceinline__ int nch() const {
+    const int want = (nkb * 12 + 191) / 192;
+    return want < 1 ? 1 : (want > kChunks ? kChunks : want);
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return nch(); }
   __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
-    const int nch = nkb < kChunks ? nkb : kChunks;
+    const int nch = this->nch();
     br = (int)it.c0;
     kb0 = (int)((int64_t)nkb * c / nch);
     kb1 = (int)((int64_t)nkb * (c + 1) / nch);
