@@ -304,3 +304,26 @@ def test_tensor_core_scan_tiling(gpu_lib, D):
         assert close(sc[b], ref[b, ids[b]]).all()
         assert_topk(ids[b], sc[b], ref[b], N)
     ix.close()
+
+
+def test_sharded_indexes_merge_to_the_unsharded_ranking(gpu_lib):
+    """Two shards of the database, queried separately and merged by (score desc, id asc),
+    give the ranking of one index over all shapes."""
+    import torch
+    from paper_1604_01879_gb300.sharded import merge_topk, shard_range
+    N, Nv, D, C, K = 150, 16, 64, 5, 10
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 7, (16, 9), 111)
+    full = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="f32", keep_exact=False)
+    ids, sc = full.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=40)
+    parts = []
+    for r in range(2):
+        base, n = shard_range(N, r, 2)
+        ix = _index(gpu_lib, torch, np.ascontiguousarray(X[base:base + n]), cb, n, Nv, K, storage="f32",
+                    keep_exact=False)
+        i, s = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=40)
+        parts.append((i.cpu().numpy() + base, s.cpu().numpy()))
+        ix.close()
+    mi, ms = merge_topk([p[0] for p in parts], [p[1] for p in parts], 40)
+    assert np.array_equal(mi, ids.cpu().numpy())
+    assert np.allclose(ms, sc.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    full.close()
