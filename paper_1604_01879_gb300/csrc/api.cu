@@ -265,7 +265,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
 
   tm.mark(ST_SCAN);
-  if (ix.prm.storage == GIFT_BF16)
+  if (ix.prm.storage != GIFT_F32)
     fif_scan_tc(ix, P, table, false, nullptr, 0, sc, s);
   else
     fif_scan(ix, P, table, false, nullptr, 0, s);
@@ -454,7 +454,7 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   GIFT_LAUNCHED("k_cb_maxnorm");
 
   // FP32 master (kept for the exact match and the rescore; otherwise scratch)
-  const bool split_rescore = p.rescore_r > 0 && p.storage == GIFT_BF16;
+  const bool split_rescore = p.rescore_r > 0 && p.storage != GIFT_F32;
   const bool need_master = p.keep_exact || (p.rescore_r > 0 && !split_rescore);
   float* master = need_master ? ix->alloc<float>((size_t)n_rows * D) : sc.get<float>((size_t)n_rows * D);
   if (need_master) ix->master = master;
@@ -537,6 +537,15 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
     GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_lo + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
     k_pack_lo<<<pg, 256, 0, s>>>(master, ix->list_row, n_rows, D, (__nv_bfloat16*)ix->list_lo);
     GIFT_LAUNCHED("k_pack_lo");
+    if (p.storage == GIFT_FP8_E4M3) {
+      // the FP8 store scans; the rescore reads a separate BF16 hi part
+      ix->list_hi = ix->alloc<__nv_bfloat16>((size_t)ix->list_rows_alloc * D);
+      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_hi + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
+      ix->list_scale_hi = ix->alloc<float>(n_rows);
+      k_pack_lists<__nv_bfloat16><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_rows, D,
+                                                     (__nv_bfloat16*)ix->list_hi, ix->list_scale_hi, 0);
+      GIFT_LAUNCHED("k_pack_lists");
+    }
   }
   if (p.keep_exact) {
     // shape-ordered two-part BF16 copy for the exact match on the tensor cores

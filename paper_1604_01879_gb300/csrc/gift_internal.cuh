@@ -89,7 +89,9 @@ struct Index {
   int32_t* list_row = nullptr;   // [n_rows] row of each entry (list order)
   int32_t* list_shape = nullptr; // [n_rows]
   void* list_feat = nullptr;     // [n_rows, D] in storage dtype
-  void* list_lo = nullptr;       // [n_rows, D] BF16 residual x - bf16(x) (BF16 store with rescore)
+  void* list_lo = nullptr;       // [n_rows, D] BF16 residual x - bf16(x) (rescore)
+  void* list_hi = nullptr;       // [n_rows, D] BF16 bf16(x) when the store is FP8 (rescore)
+  float* list_scale_hi = nullptr;// [n_rows] 1/||x|| for the BF16 parts when the store is FP8
   int64_t list_rows_alloc = 0;   // rows of list_feat / list_lo including padding
 
   // exact match: shape-ordered two-part BF16 copy of the views (+ padding rows)

@@ -25,7 +25,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kT = 16;  // coarse candidates kept per row
 
 struct AssignPolicy {
-  static constexpr int TN = 256, NBUF = 2, STAGES = 2, SPLIT = 3;
+  static constexpr int TN = 256, NBUF = 2, STAGES = 2, SPLIT = 3, EB = 2;
   static constexpr int kWarpSmem = TN * 4;
   int64_t n;          // rows
   int K;

@@ -19,7 +19,7 @@ namespace {
 constexpr int kChunks = 4;
 
 struct ExactPolicy {
-  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3;
+  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
   static constexpr int kWarpSmem = TN * 4;
   int64_t rows;        // query views in this pass
   int64_t ncols;       // database views N * N_v

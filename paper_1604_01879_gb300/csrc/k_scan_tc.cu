@@ -68,6 +68,7 @@ struct SlotInfo {
   const float* scale;        // [n_rows] list-ordered cosine factor
   const int32_t* entry_run;  // [n_rows]
   const int32_t* list_shape; // [n_rows]
+  const float* slot_scale;   // [nslots] E4M3 slot scale, or null (BF16 slots)
   uint32_t* table;
 };
 
@@ -117,14 +118,16 @@ __device__ __forceinline__ void load_row(const SlotInfo& si, const ListItem& it,
     const int64_t s = it.s0 + m;
     r.rb = si.runbase[s];
     const int32_t v = si.slot_view[s];
-    r.qi = si.q_inv[v];
+    r.qi = si.q_inv[v] * (si.slot_scale ? si.slot_scale[s] : 1.f);
     r.qq = si.vquery[v];
   }
 }
 
 // ---------------------------------------------------------------- scan policy
+// EB_ = 2: BF16 store and slots; EB_ = 1: E4M3 store and slots (per-row scales)
+template <int EB_>
 struct ScanPolicy : ListSched {
-  static constexpr int TN = kScanTN, NBUF = 2, STAGES = 4, SPLIT = 1;
+  static constexpr int TN = kScanTN, NBUF = 2, STAGES = 4, SPLIT = 1, EB = EB_;
   static constexpr int kWarpSmem = TN * 12;
   SlotInfo si;
   using Item = ListItem;
@@ -180,7 +183,7 @@ struct ScanPolicy : ListSched {
 
 // ---------------------------------------------------------------- rescore policy
 struct RescorePolicy : ListSched {
-  static constexpr int TN = kRescTN, NBUF = 4, STAGES = 3, SPLIT = 3;
+  static constexpr int TN = kRescTN, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
   static constexpr int kWarpSmem = TN * 12;
   SlotInfo si;
   const int32_t* cand;  // [B, R] candidate ids sorted ascending
@@ -274,6 +277,30 @@ __global__ void k_slot_split(const float* __restrict__ q, const int32_t* __restr
   }
 }
 
+// slot-ordered E4M3 copies of the query views with one scale per slot:
+// stored = q / scale, scale = max|q| / 448 (the largest finite E4M3 value)
+__global__ __launch_bounds__(256) void k_slot_fp8(const float* __restrict__ q, const int32_t* __restrict__ slot_view,
+                                                  int64_t nslots, int D, __nv_fp8_e4m3* __restrict__ out,
+                                                  float* __restrict__ scale) {
+  __shared__ float red[8];
+  const int64_t s = blockIdx.x;
+  if (s >= nslots) return;
+  const float* src = q + (int64_t)slot_view[s] * D;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) m = fmaxf(m, fabsf(src[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float mx = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) mx = fmaxf(mx, red[w]);
+  const float sc = mx > 0.f ? mx / 448.f : 1.f;
+  const float inv = 1.f / sc;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) out[s * D + i] = __nv_fp8_e4m3(src[i] * inv);
+  if (threadIdx.x == 0) scale[s] = sc;
+}
+
 __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t* __restrict__ list_off, int K,
                                 int tn, int64_t* __restrict__ wcnt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -294,11 +321,23 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   const int K = ix.prm.n_codewords, D = ix.prm.dim;
   const int64_t ns = P.nslots;
   if (ns <= 0) return;
+  const bool fp8 = !rescore && ix.prm.storage == GIFT_FP8_E4M3;
   const int64_t qrows = ns + tc::kTM;  // one box of padding rows
-  __nv_bfloat16* qhi = sc.get<__nv_bfloat16>((size_t)qrows * D);
-  __nv_bfloat16* qlo = rescore ? sc.get<__nv_bfloat16>((size_t)qrows * D) : nullptr;
-  k_slot_split<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, qhi, qlo);
-  GIFT_LAUNCHED("k_slot_split");
+  __nv_bfloat16* qhi = nullptr;
+  __nv_bfloat16* qlo = nullptr;
+  __nv_fp8_e4m3* q8 = nullptr;
+  float* q8s = nullptr;
+  if (fp8) {
+    q8 = sc.get<__nv_fp8_e4m3>((size_t)qrows * D);
+    q8s = sc.get<float>(ns);
+    k_slot_fp8<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, q8, q8s);
+    GIFT_LAUNCHED("k_slot_fp8");
+  } else {
+    qhi = sc.get<__nv_bfloat16>((size_t)qrows * D);
+    qlo = rescore ? sc.get<__nv_bfloat16>((size_t)qrows * D) : nullptr;
+    k_slot_split<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, qhi, qlo);
+    GIFT_LAUNCHED("k_slot_split");
+  }
   const int tn = rescore ? kRescTN : kScanTN;
   int64_t* wcnt = sc.get<int64_t>(K + 1);
   int64_t* woff = sc.get<int64_t>(K + 1);
@@ -311,7 +350,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   ls.K = K;
   ls.boff = P.boff;
   ls.list_off = ix.list_off;
-  ls.nkb = (int)cdiv(D, tc::kTK);
+  ls.nkb = (int)cdiv(D, fp8 ? 128 : 64);
   SlotInfo si;
   si.runbase = P.runbase;
   si.slot_view = P.slot_view;
@@ -320,25 +359,39 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   si.scale = ix.list_scale;
   si.entry_run = ix.entry_run;
   si.list_shape = ix.list_shape;
+  si.slot_scale = q8s;
   si.table = table;
   const int grid = device_sm_count();
-  const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
-  if (!rescore) {
-    ScanPolicy pol;
+  if (fp8) {
+    ScanPolicy<1> pol;
     static_cast<ListSched&>(pol) = ls;
     pol.si = si;
-    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy::TN);
+    const CUtensorMap tA = make_tmap_u8(q8, qrows, D, tc::kTM);
+    const CUtensorMap tB = make_tmap_u8(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy<1>::TN);
+    if (P.kc) P.kc->begin(1);
+    tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
+    if (P.kc) P.kc->end(1);
+  } else if (!rescore) {
+    ScanPolicy<2> pol;
+    static_cast<ListSched&>(pol) = ls;
+    pol.si = si;
+    const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
+    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy<2>::TN);
     if (P.kc) P.kc->begin(1);
     tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
     if (P.kc) P.kc->end(1);
   } else {
-    GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the BF16 residual store");
+    GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the two-part BF16 list store");
+    // BF16 index: the store itself is the hi part; FP8 index: a separate BF16 hi store
+    const void* bhi = ix.list_hi ? ix.list_hi : ix.list_feat;
     RescorePolicy pol;
     static_cast<ListSched&>(pol) = ls;
     pol.si = si;
+    pol.si.scale = ix.list_hi ? ix.list_scale_hi : ix.list_scale;
     pol.cand = cand_sorted;
     pol.R = R;
-    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, RescorePolicy::TN);
+    const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
+    const CUtensorMap tB = make_tmap_bf16(bhi, ix.list_rows_alloc, D, RescorePolicy::TN);
     const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
     const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, RescorePolicy::TN);
     if (P.kc) P.kc->begin(2);

@@ -18,7 +18,7 @@
 // cores by the epilogue.
 //
 // A policy class P supplies the schedule and the epilogue:
-//   static constexpr int TN, NBUF, STAGES, SPLIT;
+//   static constexpr int TN, NBUF, STAGES, SPLIT, EB;          (EB: operand bytes, 2 BF16 / 1 E4M3)
 //   struct Item; struct Ctx;                                  (per-thread epilogue state)
 //   int64_t total() const;  Item decode(int64_t) const;
 //   int nchunks(const Item&) const;
@@ -40,8 +40,11 @@ constexpr int kEngineThreads = 192;
 
 template <class P>
 struct EngineLayout {
-  static constexpr int kABytes = kTM * kTK * 2;
-  static constexpr int kBBytes = P::TN * kTK * 2;
+  // one k-block = one 128-byte swizzle row of K: 64 BF16 or 128 E4M3 elements
+  static constexpr int kKElems = 128 / P::EB;
+  static constexpr int kABytes = kTM * 128;
+  static constexpr int kBBytes = P::TN * 128;
+  static_assert(P::EB == 2 || P::SPLIT == 1, "two-part operands are BF16");
   static constexpr int kParts = P::SPLIT == 1 ? 1 : 2;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kBarBytes = 256;
@@ -94,7 +97,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   fence_after_sync();
   const uint32_t tmem = *tmem_holder;
   const int64_t total = p.total();
-  constexpr uint32_t kIdesc = idesc_bf16(kTM, TN);
+  constexpr uint32_t kIdesc = P::EB == 2 ? idesc_bf16(kTM, TN) : idesc_e4m3(kTM, TN);
+  constexpr int KE = L::kKElems;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -120,11 +124,11 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
             }
             const uint32_t st = smem_u32(tiles + stage * L::kStageBytes);
             mbar_expect_tx(full0 + 8 * stage, L::kStageBytes);
-            tma_load_2d(st, &tmA, kb * kTK, ar, full0 + 8 * stage);
-            tma_load_2d(st + L::kABytes, &tmB, kb * kTK, br, full0 + 8 * stage);
+            tma_load_2d(st, &tmA, kb * KE, ar, full0 + 8 * stage);
+            tma_load_2d(st + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
             if (P::SPLIT == 3) {
-              tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * kTK, ar, full0 + 8 * stage);
-              tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * kTK, br, full0 + 8 * stage);
+              tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * KE, ar, full0 + 8 * stage);
+              tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
             }
             last_phase[stage] = (int)phase;
             if (++stage == S) {
@@ -173,9 +177,14 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
             const uint32_t sb = sa + L::kABytes;
             const uint32_t sa2 = sb + L::kBBytes;
             const uint32_t sb2 = sa2 + L::kABytes;
+            // four MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 elements)
 #pragma unroll
-            for (int kk = 0; kk < kTK / 16; ++kk) {
+            for (int kk = 0; kk < 4; ++kk) {
               const uint32_t acc_in = (kb != kb0 || kk != 0) ? 1u : 0u;
+              if (P::EB == 1) {
+                mma_f8(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
+                continue;
+              }
               mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
               if (P::SPLIT == 3) {
                 mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);

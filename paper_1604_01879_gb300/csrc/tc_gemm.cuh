@@ -12,7 +12,7 @@ namespace gift {
 
 template <int SPLIT_>
 struct GemmPolicy {
-  static constexpr int TN = 128, NBUF = 4, STAGES = SPLIT_ == 1 ? 6 : 3, SPLIT = SPLIT_;
+  static constexpr int TN = 128, NBUF = 4, STAGES = SPLIT_ == 1 ? 6 : 3, SPLIT = SPLIT_, EB = 2;
   static constexpr int kWarpSmem = 16;
   static constexpr int kChunks = 4;
   int64_t M, N;

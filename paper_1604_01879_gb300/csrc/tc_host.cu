@@ -44,6 +44,24 @@ CUtensorMap make_tmap_bf16(const void* base, uint64_t rows, uint64_t cols, uint3
   return m;
 }
 
+CUtensorMap make_tmap_u8(const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows, uint64_t pitch) {
+  if (pitch == 0) pitch = cols;
+  GIFT_REQUIRE(reinterpret_cast<uintptr_t>(base) % 16 == 0, "tensor map base must be 16-byte aligned");
+  GIFT_REQUIRE(pitch % 16 == 0 && pitch >= cols, "tensor map row pitch must be >= cols and a multiple of 16 bytes");
+  GIFT_REQUIRE(box_rows >= 1 && box_rows <= 256, "tensor map box rows must be in [1, 256]");
+  GIFT_REQUIRE(rows >= box_rows, "tensor map extent must cover at least one box");
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {128u, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box,
+                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(GIFT_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
+  return m;
+}
+
 int device_sm_count() {
   int dev = 0, n = 0;
   GIFT_CUDA(cudaGetDevice(&dev));
