@@ -129,6 +129,27 @@ typedef struct {
 GIFT_API gift_status gift_build_index(const gift_index_params* params, const float* db_feats,
                              const float* codebook, cudaStream_t stream, gift_index** out);
 
+/*
+ * Streamed build, for databases whose FP32 views do not fit in host or device
+ * memory at once. The same index as gift_build_index (keep_exact must be 0: no
+ * FP32 master is kept), built from chunks of whole shapes in three passes; in
+ * every pass each shape is added exactly once, chunks in any order:
+ *   pass 1  quantise the views (codes, norms);            gift_build_end_pass(1) builds the F-IF lists
+ *   pass 2  pack the views into their list positions;    gift_build_end_pass(2)
+ *   pass 3  (sif_k1 > 0) run the shapes as queries;      gift_build_end_pass(3) builds the S-IF
+ * feats: device or host float [n_shapes * N_v * D], the views of shapes
+ * [first_shape, first_shape + n_shapes); gift_build_add returns after the chunk
+ * has been consumed, so its buffer may be reused. Queries before the last
+ * pass is closed return GIFT_ESTATE.
+ * Errors: EINVAL (sizes, order of passes, a pass closed before every shape was
+ * added), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_build_begin(const gift_index_params* params, const float* codebook,
+                                      cudaStream_t stream, gift_index** out);
+GIFT_API gift_status gift_build_add(gift_index* index, int32_t pass, const float* feats,
+                                    int32_t first_shape, int32_t n_shapes, cudaStream_t stream);
+GIFT_API gift_status gift_build_end_pass(gift_index* index, int32_t pass, cudaStream_t stream);
+
 /* Release the index and all its device memory (synchronises the device). */
 GIFT_API void gift_destroy_index(gift_index* index);
 

@@ -80,6 +80,9 @@ _I32, _I64 = ctypes.c_int32, ctypes.c_int64
 _SIGS = {
     "gift_build_index": (_I32, [ctypes.POINTER(_Params), _P, _P, _P, ctypes.POINTER(_P)]),
     "gift_destroy_index": (None, [_P]),
+    "gift_build_begin": (_I32, [ctypes.POINTER(_Params), _P, _P, ctypes.POINTER(_P)]),
+    "gift_build_add": (_I32, [_P, _I32, _P, _I32, _I32, _P]),
+    "gift_build_end_pass": (_I32, [_P, _I32, _P]),
     "gift_query": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
@@ -177,6 +180,44 @@ class Index:
         self.n_shapes, self.views_per_shape, self.dim = int(n_shapes), int(views_per_shape), dim
         self.n_codewords, self.query_ma, self.sif_k1 = int(n_codewords), int(query_ma), int(sif_k1)
         self.rescore_r = int(rescore_r)
+
+    @classmethod
+    def streamed(cls, chunk_fn, codebook, n_shapes: int, views_per_shape: int, n_codewords: int,
+                 chunk_shapes: int = 1024, storage="bf16", query_ma: int = 1, sif_k1: int = 0,
+                 rescore_r: int = 0, stream=None):
+        """Build an index from chunks in three passes (gift_build_begin / add / end_pass).
+
+        chunk_fn(first_shape, n_shapes) returns the float32 views [n_shapes, N_v, D] of
+        those shapes (host numpy or device tensor); it is called once per chunk per pass,
+        so a seeded generator can regenerate chunks instead of holding the database.
+        """
+        lib = load()
+        self = cls.__new__(cls)
+        dim = int(codebook.shape[-1])
+        self.params = _Params(int(n_shapes), int(views_per_shape), dim, int(n_codewords),
+                              _STORAGE[storage] if isinstance(storage, str) else int(storage),
+                              int(query_ma), int(sif_k1), int(rescore_r), 0)
+        self._h = ctypes.c_void_p()
+        st = _stream(stream)
+        _check(lib.gift_build_begin(ctypes.byref(self.params), _ptr(codebook), st, ctypes.byref(self._h)))
+        self.n_shapes, self.views_per_shape, self.dim = int(n_shapes), int(views_per_shape), dim
+        self.n_codewords, self.query_ma, self.sif_k1 = int(n_codewords), int(query_ma), int(sif_k1)
+        self.rescore_r = int(rescore_r)
+        try:
+            for p in (1, 2, 3):
+                if p == 3 and sif_k1 == 0:
+                    break
+                for first in range(0, n_shapes, chunk_shapes):
+                    n = min(chunk_shapes, n_shapes - first)
+                    x = chunk_fn(first, n)
+                    if isinstance(x, np.ndarray):
+                        x = np.ascontiguousarray(x, dtype=np.float32)
+                    _check(lib.gift_build_add(self._h, p, _ptr(x), int(first), int(n), st))
+                _check(lib.gift_build_end_pass(self._h, p, st))
+        except BaseException:
+            self.close()
+            raise
+        return self
 
     # -- queries -----------------------------------------------------------
     def query(self, q_feats, q_offsets, mode="fif", topk: int = 10, out=None, stream=None):

@@ -214,6 +214,100 @@ __global__ void k_cb_maxnorm(const float* __restrict__ half_sq, int K, float* __
   }
 }
 
+// list position of every database row: pos[list_row[e]] = e
+__global__ void k_list_pos(const int32_t* __restrict__ list_row, int64_t n, int32_t* __restrict__ pos) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) pos[list_row[e]] = (int32_t)e;
+}
+
+// pass 2 of a streamed build: pack the rows of one chunk into their list
+// positions (store dtype + cosine factor; BF16 parts for the rescore)
+template <typename TO>
+__global__ void k_scatter_pack(const float* __restrict__ chunk, int64_t row0, int64_t n, int D,
+                               const int32_t* __restrict__ pos, const float* __restrict__ row_inv,
+                               TO* __restrict__ out, float* __restrict__ scale_out, int fp8,
+                               __nv_bfloat16* __restrict__ hi, float* __restrict__ scale_hi,
+                               __nv_bfloat16* __restrict__ lo) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const float* x = chunk + r * D;
+  const int64_t e = pos[row0 + r];
+  float sc = 1.f;
+  if (fp8) {
+    float m = 0.f;
+    for (int d = lane; d < D; d += 32) m = fmaxf(m, fabsf(x[d]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    sc = m > 0.f ? m / 448.f : 1.f;
+  }
+  const float inv_sc = 1.f / sc;
+  for (int d = lane; d < D; d += 32) {
+    const float v = x[d];
+    out[e * D + d] = cvt_store<TO>(fp8 ? v * inv_sc : v);
+    if (lo) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      lo[e * D + d] = __float2bfloat16_rn(v - __bfloat162float(h));
+      if (hi) hi[e * D + d] = h;
+    }
+  }
+  if (lane == 0) {
+    scale_out[e] = sc * row_inv[row0 + r];
+    if (scale_hi) scale_hi[e] = row_inv[row0 + r];
+  }
+}
+
+// F-IF from the database codes: stable sort of rows by code (lists in
+// (shape, view) order), shape ids, runs of equal shape per list, sizes.
+void build_lists(Index& ix_, Scratch& sc, cudaStream_t s) {
+  Index* ix = &ix_;
+  const int K = ix->prm.n_codewords, Nv = ix->prm.views_per_shape;
+  const int64_t n_rows = ix->n_rows;
+  ix->list_row = ix->alloc<int32_t>(n_rows);
+  int32_t* skeys = sc.get<int32_t>(n_rows);
+  stable_sort_by_key(ix->db_codes, n_rows, K, ix->list_row, skeys, sc, s);
+  ix->list_off = ix->alloc<int64_t>(K + 1);
+  bin_offsets(skeys, n_rows, K, ix->list_off, s);
+  ix->list_shape = ix->alloc<int32_t>(n_rows);
+  int64_t* run_flag = sc.get<int64_t>(n_rows + 1);
+  k_list_meta<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(ix->list_row, skeys, n_rows, Nv, ix->list_shape,
+                                                            run_flag);
+  GIFT_LAUNCHED("k_list_meta");
+  int64_t* run_excl = sc.get<int64_t>(n_rows + 1);
+  scan_exclusive_i64(run_flag, run_excl, n_rows, sc, s);
+  int64_t h_last[2];
+  GIFT_CUDA(cudaMemcpyAsync(&h_last[0], run_excl + n_rows - 1, 8, cudaMemcpyDeviceToHost, s));
+  GIFT_CUDA(cudaMemcpyAsync(&h_last[1], run_flag + n_rows - 1, 8, cudaMemcpyDeviceToHost, s));
+  GIFT_CUDA(cudaStreamSynchronize(s));
+  ix->n_runs = h_last[0] + h_last[1];
+  ix->entry_run = ix->alloc<int32_t>(n_rows);
+  ix->run_shape = ix->alloc<int32_t>(ix->n_runs);
+  k_runs<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(run_excl, run_flag, skeys, ix->list_off, ix->list_shape,
+                                                       n_rows, ix->entry_run, ix->run_shape);
+  GIFT_LAUNCHED("k_runs");
+  ix->nruns = ix->alloc<int32_t>(K);
+  ix->run_off = ix->alloc<int64_t>(K);
+  int* d_stats = sc.get<int>(4);
+  unsigned long long* d_tiles = sc.get<unsigned long long>(1);
+  GIFT_CUDA(cudaMemsetAsync(d_stats, 0, 16, s));
+  GIFT_CUDA(cudaMemsetAsync(d_tiles, 0, 8, s));
+  k_list_runs<<<(unsigned)cdiv(K, 256), 256, 0, s>>>(ix->list_off, run_excl, run_flag, K, ix->n_runs, ix->nruns,
+                                                       ix->run_off, d_stats, d_tiles);
+  GIFT_LAUNCHED("k_list_runs");
+  int h_stats[4];
+  unsigned long long h_tiles = 0;
+  ix->h_list_off.resize(K + 1);
+  GIFT_CUDA(cudaMemcpyAsync(h_stats, d_stats, 16, cudaMemcpyDeviceToHost, s));
+  GIFT_CUDA(cudaMemcpyAsync(&h_tiles, d_tiles, 8, cudaMemcpyDeviceToHost, s));
+  GIFT_CUDA(cudaMemcpyAsync(ix->h_list_off.data(), ix->list_off, (K + 1) * 8, cudaMemcpyDeviceToHost, s));
+
+  GIFT_CUDA(cudaStreamSynchronize(s));
+  ix->max_runs = h_stats[0];
+  ix->max_list = h_stats[1];
+  ix->n_nonempty = h_stats[2];
+  ix->scan_tiles_upper = (int64_t)h_tiles;
+}
+
 // ------------------------------------------------------------------ query core
 struct QueryOut {
   int32_t* ids;
@@ -360,6 +454,7 @@ T* Index::alloc(size_t n) {
 }
 
 Index::~Index() {
+  delete sb;
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
   for (auto& k : kspans) {
     cudaEventDestroy(k.second.first);
@@ -471,44 +566,7 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   ix->db_codes = ix->alloc<int32_t>(n_rows);
   assign_codes(*ix, master, n_rows, 1, ix->db_codes, sc, s, ix->row_inv);
 
-  // F-IF: stable sort of rows by code -> lists in (shape, view) order
-  ix->list_row = ix->alloc<int32_t>(n_rows);
-  int32_t* skeys = sc.get<int32_t>(n_rows);
-  stable_sort_by_key(ix->db_codes, n_rows, K, ix->list_row, skeys, sc, s);
-  ix->list_off = ix->alloc<int64_t>(K + 1);
-  bin_offsets(skeys, n_rows, K, ix->list_off, s);
-  ix->list_shape = ix->alloc<int32_t>(n_rows);
-  int64_t* run_flag = sc.get<int64_t>(n_rows + 1);
-  k_list_meta<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(ix->list_row, skeys, n_rows, Nv, ix->list_shape,
-                                                            run_flag);
-  GIFT_LAUNCHED("k_list_meta");
-  int64_t* run_excl = sc.get<int64_t>(n_rows + 1);
-  scan_exclusive_i64(run_flag, run_excl, n_rows, sc, s);
-  int64_t h_last[2];
-  GIFT_CUDA(cudaMemcpyAsync(&h_last[0], run_excl + n_rows - 1, 8, cudaMemcpyDeviceToHost, s));
-  GIFT_CUDA(cudaMemcpyAsync(&h_last[1], run_flag + n_rows - 1, 8, cudaMemcpyDeviceToHost, s));
-  GIFT_CUDA(cudaStreamSynchronize(s));
-  ix->n_runs = h_last[0] + h_last[1];
-  ix->entry_run = ix->alloc<int32_t>(n_rows);
-  ix->run_shape = ix->alloc<int32_t>(ix->n_runs);
-  k_runs<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(run_excl, run_flag, skeys, ix->list_off, ix->list_shape,
-                                                       n_rows, ix->entry_run, ix->run_shape);
-  GIFT_LAUNCHED("k_runs");
-  ix->nruns = ix->alloc<int32_t>(K);
-  ix->run_off = ix->alloc<int64_t>(K);
-  int* d_stats = sc.get<int>(4);
-  unsigned long long* d_tiles = sc.get<unsigned long long>(1);
-  GIFT_CUDA(cudaMemsetAsync(d_stats, 0, 16, s));
-  GIFT_CUDA(cudaMemsetAsync(d_tiles, 0, 8, s));
-  k_list_runs<<<(unsigned)cdiv(K, 256), 256, 0, s>>>(ix->list_off, run_excl, run_flag, K, ix->n_runs, ix->nruns,
-                                                       ix->run_off, d_stats, d_tiles);
-  GIFT_LAUNCHED("k_list_runs");
-  int h_stats[4];
-  unsigned long long h_tiles = 0;
-  ix->h_list_off.resize(K + 1);
-  GIFT_CUDA(cudaMemcpyAsync(h_stats, d_stats, 16, cudaMemcpyDeviceToHost, s));
-  GIFT_CUDA(cudaMemcpyAsync(&h_tiles, d_tiles, 8, cudaMemcpyDeviceToHost, s));
-  GIFT_CUDA(cudaMemcpyAsync(ix->h_list_off.data(), ix->list_off, (K + 1) * 8, cudaMemcpyDeviceToHost, s));
+  build_lists(*ix, sc, s);
 
   // list-ordered feature store
   const size_t eb = dtype_bytes(p.storage);
@@ -557,10 +615,6 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
     split_rows_bf16(master, n_rows, D, ix->ex_hi, ix->ex_lo, s);
   }
   GIFT_CUDA(cudaStreamSynchronize(s));
-  ix->max_runs = h_stats[0];
-  ix->max_list = h_stats[1];
-  ix->n_nonempty = h_stats[2];
-  ix->scan_tiles_upper = (int64_t)h_tiles;
 
   // S-IF: every database shape as a query, first k1 neighbours (self included)
   if (p.sif_k1 > 0) {
@@ -590,6 +644,178 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   *out = reinterpret_cast<gift_index*>(ix.release());
 }
 
+void stream_begin(const gift_index_params* prm, const float* codebook, cudaStream_t s, gift_index** out) {
+  GIFT_REQUIRE(prm && codebook && out, "NULL argument");
+  const gift_index_params p = *prm;
+  GIFT_REQUIRE(p.n_shapes > 0 && p.views_per_shape > 0 && p.n_codewords > 0, "sizes must be positive");
+  GIFT_REQUIRE(p.dim > 0 && p.dim % 16 == 0, "dim must be a positive multiple of 16");
+  GIFT_REQUIRE(p.storage >= GIFT_F32 && p.storage <= GIFT_FP8_E4M3, "unknown storage type");
+  GIFT_REQUIRE(p.storage != GIFT_F32 || p.rescore_r == 0, "a streamed FP32 store does not rescore");
+  GIFT_REQUIRE(p.query_ma >= 1 && p.query_ma <= GIFT_MAX_MA && p.query_ma <= p.n_codewords,
+               "query_ma must be in [1, min(8, K)]");
+  GIFT_REQUIRE(p.sif_k1 >= 0 && p.sif_k1 <= std::min(1024, p.n_shapes), "sif_k1 must be in [0, min(1024, N)]");
+  GIFT_REQUIRE(p.rescore_r >= 0 && p.rescore_r <= 1024, "rescore_r must be in [0, 1024]");
+  GIFT_REQUIRE(p.rescore_r == 0 || p.sif_k1 <= p.rescore_r, "sif_k1 must be <= rescore_r when rescoring");
+  GIFT_REQUIRE(!p.keep_exact, "a streamed build keeps no FP32 master (keep_exact must be 0)");
+  GIFT_REQUIRE(p.views_per_shape <= 32767, "views_per_shape must be <= 32767");
+  const int64_t n_rows = (int64_t)p.n_shapes * p.views_per_shape;
+  GIFT_REQUIRE(n_rows < (int64_t)INT32_MAX, "too many database views");
+  std::unique_ptr<Index> ix(new Index());
+  ix->prm = p;
+  ix->n_rows = n_rows;
+  GIFT_CUDA(cudaGetDevice(&ix->device));
+  {
+    cudaMemPool_t pool;
+    GIFT_CUDA(cudaDeviceGetDefaultMemPool(&pool, ix->device));
+    uint64_t keep = UINT64_MAX;
+    GIFT_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  }
+  const int D = p.dim, K = p.n_codewords;
+  Scratch sc(s);
+  ix->codebook = ix->alloc<float>((size_t)K * D);
+  GIFT_CUDA(cudaMemcpyAsync(ix->codebook, codebook, (size_t)K * D * 4, cudaMemcpyDefault, s));
+  ix->cb_half_sq = ix->alloc<float>(K);
+  launch_half_sq_norm(ix->codebook, K, D, ix->cb_half_sq, s);
+  ix->cb_rows_alloc = (int64_t)K + 256;
+  ix->cb_hi = ix->alloc<__nv_bfloat16>((size_t)ix->cb_rows_alloc * D);
+  ix->cb_lo = ix->alloc<__nv_bfloat16>((size_t)ix->cb_rows_alloc * D);
+  GIFT_CUDA(cudaMemsetAsync(ix->cb_hi, 0, (size_t)ix->cb_rows_alloc * D * 2, s));
+  GIFT_CUDA(cudaMemsetAsync(ix->cb_lo, 0, (size_t)ix->cb_rows_alloc * D * 2, s));
+  split_rows_bf16(ix->codebook, K, D, ix->cb_hi, ix->cb_lo, s);
+  float* d_cbmax = sc.get<float>(1);
+  k_cb_maxnorm<<<1, 1024, 0, s>>>(ix->cb_half_sq, K, d_cbmax);
+  GIFT_LAUNCHED("k_cb_maxnorm");
+  GIFT_CUDA(cudaMemcpyAsync(&ix->cb_max_norm, d_cbmax, 4, cudaMemcpyDeviceToHost, s));
+  ix->row_inv = ix->alloc<float>(n_rows);
+  ix->db_codes = ix->alloc<int32_t>(n_rows);
+  ix->d_err = ix->alloc<int>(1);
+  GIFT_CUDA(cudaMemsetAsync(ix->d_err, 0, sizeof(int), s));
+  GIFT_CUDA(cudaStreamSynchronize(s));
+  ix->cb_max_norm *= 1.0001f;
+  ix->sb = new StreamBuild();
+  *out = reinterpret_cast<gift_index*>(ix.release());
+}
+
+void stream_add(Index& ix, int pass, const float* feats, int32_t first, int32_t n, cudaStream_t s) {
+  if (!ix.sb) fail(GIFT_ESTATE, "the index is not being built in a stream");
+  GIFT_REQUIRE(pass == ix.sb->stage, "chunks of pass " + std::to_string(ix.sb->stage) + " are expected");
+  GIFT_REQUIRE(feats && n > 0 && first >= 0 && (int64_t)first + n <= ix.prm.n_shapes, "chunk out of range");
+  std::vector<uint8_t>& seen = ix.sb->seen;
+  if (seen.empty()) seen.assign(ix.prm.n_shapes, 0);
+  for (int32_t i = first; i < first + n; ++i)
+    GIFT_REQUIRE(!seen[i], "shape " + std::to_string(i) + " was already added in this pass");
+  const int D = ix.prm.dim, Nv = ix.prm.views_per_shape;
+  const int64_t row0 = (int64_t)first * Nv, rows = (int64_t)n * Nv;
+  Scratch sc(s);
+  const float* x = feats;
+  if (!is_device_ptr(feats)) {
+    float* d = sc.get<float>((size_t)rows * D);
+    GIFT_CUDA(cudaMemcpyAsync(d, feats, (size_t)rows * D * 4, cudaMemcpyHostToDevice, s));
+    x = d;
+  }
+  if (pass == 1) {
+    launch_row_invnorm(x, rows, D, ix.row_inv + row0, s);
+    assign_codes(ix, x, rows, 1, ix.db_codes + row0, sc, s, ix.row_inv + row0);
+  } else if (pass == 2) {
+    const unsigned g = (unsigned)cdiv(rows, 8);
+    __nv_bfloat16* hi = (__nv_bfloat16*)ix.list_hi;
+    __nv_bfloat16* lo = (__nv_bfloat16*)ix.list_lo;
+    switch (ix.prm.storage) {
+      case GIFT_F32:
+        k_scatter_pack<float><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv, (float*)ix.list_feat,
+                                                ix.list_scale, 0, nullptr, nullptr, nullptr);
+        break;
+      case GIFT_BF16:
+        k_scatter_pack<__nv_bfloat16><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv,
+                                                        (__nv_bfloat16*)ix.list_feat, ix.list_scale, 0, nullptr,
+                                                        nullptr, lo);
+        break;
+      default:
+        k_scatter_pack<__nv_fp8_e4m3><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv,
+                                                        (__nv_fp8_e4m3*)ix.list_feat, ix.list_scale, 1, hi,
+                                                        ix.list_scale_hi, lo);
+        break;
+    }
+    GIFT_LAUNCHED("k_scatter_pack");
+  } else {
+    const int k1 = ix.prm.sif_k1;
+    const int R = ix.prm.rescore_r;
+    const int topk = R > 0 ? std::min(k1, R) : k1;
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)1 << 26) / ix.prm.n_shapes));
+    for (int64_t b0 = 0; b0 < n; b0 += per) {
+      const int32_t nb = (int32_t)std::min<int64_t>(per, n - b0);
+      std::vector<int32_t> h(nb + 1);
+      for (int32_t i = 0; i <= nb; ++i) h[i] = i * Nv;
+      Scratch bsc(s);
+      StageTimer none(nullptr, s);
+      const int64_t shape0 = first + b0;
+      run_fif(ix, x + b0 * Nv * (int64_t)D, (int64_t)nb * Nv, h, nb, topk, ix.sb->nbr_ids + shape0 * k1,
+              ix.sb->nbr_sc + shape0 * k1, bsc, s, none, nullptr);
+    }
+  }
+  GIFT_CUDA(cudaStreamSynchronize(s));  // the chunk buffer may be reused by the caller
+  std::fill(seen.begin() + first, seen.begin() + first + n, (uint8_t)1);
+  ix.sb->rows_added += rows;
+}
+
+void stream_end(Index& ix, int pass, cudaStream_t s) {
+  if (!ix.sb) fail(GIFT_ESTATE, "the index is not being built in a stream");
+  GIFT_REQUIRE(pass == ix.sb->stage, "pass " + std::to_string(ix.sb->stage) + " is the open pass");
+  GIFT_REQUIRE(ix.sb->rows_added == ix.n_rows, "every database shape must be added once in each pass");
+  const int D = ix.prm.dim;
+  const int64_t n_rows = ix.n_rows;
+  Scratch sc(s);
+  if (pass == 1) {
+    build_lists(ix, sc, s);
+    const size_t eb = dtype_bytes(ix.prm.storage);
+    ix.list_rows_alloc = n_rows + 256;
+    ix.list_feat = ix.alloc<uint8_t>((size_t)ix.list_rows_alloc * D * eb);
+    GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix.list_feat + (size_t)n_rows * D * eb, 0, (size_t)256 * D * eb, s));
+    ix.list_scale = ix.alloc<float>(n_rows);
+    if (ix.prm.rescore_r > 0) {
+      ix.list_lo = ix.alloc<__nv_bfloat16>((size_t)ix.list_rows_alloc * D);
+      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_lo + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
+      if (ix.prm.storage == GIFT_FP8_E4M3) {
+        ix.list_hi = ix.alloc<__nv_bfloat16>((size_t)ix.list_rows_alloc * D);
+        GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_hi + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
+        ix.list_scale_hi = ix.alloc<float>(n_rows);
+      }
+    }
+    GIFT_CUDA(cudaMalloc(&ix.sb->pos, n_rows * sizeof(int32_t)));
+    k_list_pos<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(ix.list_row, n_rows, ix.sb->pos);
+    GIFT_LAUNCHED("k_list_pos");
+    ix.sb->stage = 2;
+  } else if (pass == 2) {
+    if (ix.prm.sif_k1 > 0) {
+      const int64_t n = (int64_t)ix.prm.n_shapes * ix.prm.sif_k1;
+      GIFT_CUDA(cudaFree(ix.sb->pos));
+      ix.sb->pos = nullptr;
+      GIFT_CUDA(cudaMalloc(&ix.sb->nbr_ids, n * sizeof(int32_t)));
+      GIFT_CUDA(cudaMalloc(&ix.sb->nbr_sc, n * sizeof(float)));
+      ix.sb->stage = 3;
+    } else {
+      ix.sb->stage = 4;
+    }
+  } else {
+    // the S-IF arrays appear only now, so no call sees a half-built S-IF
+    const int64_t n = (int64_t)ix.prm.n_shapes * ix.prm.sif_k1;
+    ix.k1 = ix.prm.sif_k1;
+    ix.sif_off = ix.alloc<int64_t>(ix.prm.n_shapes + 1);
+    ix.sif_ids = ix.alloc<int32_t>(n);
+    ix.sif_mem = ix.alloc<uint32_t>(n);
+    ix.sif_card = ix.alloc<uint64_t>(ix.prm.n_shapes);
+    sif_build(ix, ix.sb->nbr_ids, ix.sb->nbr_sc, sc, s);
+    ix.sb->stage = 4;
+  }
+  GIFT_CUDA(cudaStreamSynchronize(s));
+  ix.sb->rows_added = 0;
+  ix.sb->seen.clear();
+  if (ix.sb->stage == 4) {
+    delete ix.sb;
+    ix.sb = nullptr;
+  }
+}
+
 }  // namespace
 }  // namespace gift
 
@@ -600,6 +826,26 @@ extern "C" {
 gift_status gift_build_index(const gift_index_params* params, const float* db_feats, const float* codebook,
                              cudaStream_t stream, gift_index** out) {
   return gift::guard("gift_build_index", [&] { gift::build(params, db_feats, codebook, stream, out); });
+}
+
+gift_status gift_build_begin(const gift_index_params* params, const float* codebook, cudaStream_t stream,
+                             gift_index** out) {
+  return gift::guard("gift_build_begin", [&] { gift::stream_begin(params, codebook, stream, out); });
+}
+
+gift_status gift_build_add(gift_index* index, int32_t pass, const float* feats, int32_t first_shape,
+                           int32_t n_shapes, cudaStream_t stream) {
+  return gift::guard("gift_build_add", [&] {
+    GIFT_REQUIRE(index, "NULL index");
+    gift::stream_add(*reinterpret_cast<Index*>(index), pass, feats, first_shape, n_shapes, stream);
+  });
+}
+
+gift_status gift_build_end_pass(gift_index* index, int32_t pass, cudaStream_t stream) {
+  return gift::guard("gift_build_end_pass", [&] {
+    GIFT_REQUIRE(index, "NULL index");
+    gift::stream_end(*reinterpret_cast<Index*>(index), pass, stream);
+  });
 }
 
 void gift_destroy_index(gift_index* index) {
@@ -620,6 +866,7 @@ gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q
     GIFT_REQUIRE(B > 0, "B must be positive");
     GIFT_REQUIRE(topk > 0 && topk <= 1024, "topk must be in [1, 1024]");
     Index& ix = *reinterpret_cast<Index*>(index);
+    if (!ix.ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
     std::vector<int32_t> h = gift::host_offsets(q_view_offsets, B);
     const int64_t nv = h[B];
     const int D = ix.prm.dim;
@@ -670,6 +917,7 @@ gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, const float*
   return gift::guard("gift_rerank", [&] {
     GIFT_REQUIRE(index && cand_ids && cand_scores && out_ids && out_sprime, "NULL argument");
     Index& ix = *reinterpret_cast<Index*>(index);
+    if (!ix.ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
     if (!ix.sif_off) gift::fail(GIFT_EUNSUPPORTED, "index built without an S-IF (sif_k1 == 0)");
     GIFT_REQUIRE(B > 0 && n_cand > 0 && k1 > 0 && k1 <= n_cand, "need 0 < k1 <= n_cand and B > 0");
     GIFT_REQUIRE(topk > 0 && topk <= 1024, "topk must be in [1, 1024]");
@@ -704,6 +952,7 @@ gift_status gift_export_fif(const gift_index* index, int32_t* db_codes, int64_t*
   return gift::guard("gift_export_fif", [&] {
     GIFT_REQUIRE(index, "NULL index");
     const Index& ix = *reinterpret_cast<const Index*>(index);
+    if (!ix.list_off) gift::fail(GIFT_ESTATE, "the F-IF lists of this index are not built yet");
     if (db_codes)
       GIFT_CUDA(cudaMemcpyAsync(db_codes, ix.db_codes, ix.n_rows * 4, cudaMemcpyDefault, stream));
     if (list_offsets)

@@ -65,6 +65,21 @@ constexpr double kScoreFix = 4294967296.0;  // 2^32
 constexpr double kMemberFix = 2147483648.0;  // 2^31
 
 // ---------------------------------------------------------------- index
+// State of a streamed build (gift_build_begin / add / end_pass).
+struct StreamBuild {
+  int stage = 1;               // pass accepting chunks: 1 codes, 2 stores, 3 S-IF; 4 = complete
+  int64_t rows_added = 0;      // rows added in the current pass
+  std::vector<uint8_t> seen;   // [N] shapes added in the current pass
+  int32_t* pos = nullptr;      // [n_rows] list position of each database row (pass 2)
+  int32_t* nbr_ids = nullptr;  // [N * k1] neighbours of every database shape (pass 3)
+  float* nbr_sc = nullptr;
+  ~StreamBuild() {  // the pass buffers are freed once the build completes
+    cudaFree(pos);
+    cudaFree(nbr_ids);
+    cudaFree(nbr_sc);
+  }
+};
+
 struct Index {
   gift_index_params prm{};
   int64_t n_rows = 0;  // N * Nv
@@ -118,6 +133,7 @@ struct Index {
   int32_t max_sif_entry = 0;
 
   int* d_err = nullptr;          // device error flag set by bounded waits (0 = none)
+  StreamBuild* sb = nullptr;     // non-null while a streamed build is in progress
 
   size_t device_bytes = 0;
   std::vector<void*> owned;
@@ -133,6 +149,7 @@ struct Index {
   bool stats_valid = false;
 
   template <class T> T* alloc(size_t n);
+  bool ready() const { return sb == nullptr; }
   ~Index();
 };
 

@@ -246,6 +246,7 @@ gift_status gift_server_create(gift_index* index, const gift_server_params* para
     GIFT_REQUIRE(p.topk >= 1 && p.topk <= 1024, "topk must be in [1, 1024]");
     std::unique_ptr<Server> sv(new Server());
     sv->ix = reinterpret_cast<gift::Index*>(index);
+    if (!sv->ix->ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
     GIFT_REQUIRE(!p.rerank || sv->ix->sif_off, "re-ranking needs an index with an S-IF");
     if (sv->ix->prm.rescore_r > 0)
       GIFT_REQUIRE(p.topk <= std::min(sv->ix->prm.rescore_r, sv->ix->prm.n_shapes), "topk exceeds the rescore depth");
