@@ -14,6 +14,9 @@ as library steps. What each function computes, with the passage it follows:
 * ``exact_scores``         S(x_q, x_p), Eq. 3
 * ``fif_scores``           the approximate match of Eq. 4, literally (Kronecker delta)
 * ``fif_scores_lists``     Eq. 4 evaluated by walking the inverted file
+* ``fif_upper_bound``/``fif_topk_bounded``  the top-k of Eq. 4 over a database
+                           too large to quantise whole: an upper bound of every
+                           Eq. 4 term prunes the shapes that cannot rank
 * ``rank``                 the ranked list, order (score desc, id asc)
 * ``membership``           the sparse activation F_q of Eq. 7
 * ``contextual``           S'(x_q, x_p) of Eq. 8
@@ -191,6 +194,84 @@ def fif_scores_lists(Q, q_off, q_codes, X, lists):
                     v = max(v, 0.0)
                 S[b, p] += v / V
     return S
+
+
+def fif_upper_bound(Q, q_off, views_of, n_shapes, chunk_shapes=1024):
+    """U(x_q, x_p) = (1/|V(x_q)|) sum_i max(0, max_j s(q_i, p_j)), float64 [B, N].
+
+    Every term of Eq. 4 is at most max(0, max_j s(q_i, p_j)): the delta keeps a
+    subset of the products and contributes 0 for the rest. So U bounds the
+    Eq. 4 score from above (it equals Eq. 3 when all cosines are >= 0).
+    ``views_of(first, n)`` returns the views [n, N_v, D] of database shapes
+    [first, first + n); the next chunk is drawn while the current one is used.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    q_off = np.asarray(q_off)
+    B = len(q_off) - 1
+    U = np.zeros((B, n_shapes))
+    Qa = _f64(Q[:q_off[-1]])
+    starts = list(range(0, n_shapes, chunk_shapes))
+    with ThreadPoolExecutor(1) as ex:
+        nxt = ex.submit(views_of, 0, min(chunk_shapes, n_shapes)) if starts else None
+        for c, lo in enumerate(starts):
+            X = np.asarray(nxt.result())
+            n, Nv, D = X.shape
+            if c + 1 < len(starts):
+                lo2 = starts[c + 1]
+                nxt = ex.submit(views_of, lo2, min(chunk_shapes, n_shapes - lo2))
+            s = cosine(Qa, X.reshape(n * Nv, D)).reshape(-1, n, Nv)
+            m = np.maximum(s.max(axis=2), 0.0)
+            for b in range(B):
+                U[b, lo:lo + n] = m[q_off[b]:q_off[b + 1]].sum(axis=0) / (q_off[b + 1] - q_off[b])
+    return U
+
+
+def fif_topk_bounded(Q, q_off, q_codes, codebook, views_of_shape, U, k, group=128):
+    """Top-k of Eq. 4 for each query, quantising only the shapes it must visit.
+
+    Shapes are visited in order of the upper bound U (``fif_upper_bound``,
+    desc, ties by id); the views of each visited shape are quantised
+    (``quantize``, one assignment) and its Eq. 4 score computed
+    (``fif_scores``). The walk stops once k shapes are scored and the k-th
+    best score exceeds the bound of the next shape: no shape left can enter
+    the top-k. ``views_of_shape(p)`` returns the views [N_v, D] of shape p.
+    Returns ([(ids, scores)] ordered by (score desc, id asc) per query, the
+    number of shapes visited per query).
+    """
+    q_off = np.asarray(q_off)
+    q_codes = np.asarray(q_codes)
+    B, N = U.shape
+    codes_cache = {}
+    out, visited = [], []
+    for b in range(B):
+        order = np.lexsort((np.arange(N), -U[b]))
+        Qb = Q[q_off[b]:q_off[b + 1]]
+        cb = q_codes[q_off[b]:q_off[b + 1]]
+        found_ids, found_sc = [], []
+        pos = 0
+        while pos < N:
+            ids = order[pos:pos + group]
+            Xg = np.stack([views_of_shape(int(p)) for p in ids])
+            need = [i for i, p in enumerate(ids) if int(p) not in codes_cache]
+            if need:
+                cg = quantize(Xg[need].reshape(-1, Xg.shape[2]), codebook, 1).reshape(len(need), -1)
+                for r, i in enumerate(need):
+                    codes_cache[int(ids[i])] = cg[r]
+            dbc = np.stack([codes_cache[int(p)] for p in ids])
+            sc = fif_scores(Qb, np.array([0, len(Qb)]), cb, Xg, dbc)[0]
+            found_ids.extend(int(p) for p in ids)
+            found_sc.extend(sc.tolist())
+            pos += len(ids)
+            if len(found_sc) >= k and pos < N:
+                kth = np.sort(np.asarray(found_sc))[::-1][k - 1]
+                if kth > U[b, order[pos]]:
+                    break
+        fi = np.asarray(found_ids, np.int64)
+        fs = np.asarray(found_sc)
+        o = np.lexsort((fi, -fs))[:k]
+        out.append((fi[o], fs[o]))
+        visited.append(pos)
+    return out, visited
 
 
 def rank(scores, k):

@@ -12,6 +12,7 @@ from .workload import (  # noqa: F401
     query_views,
     kmeans_codebook,
     make_config_inputs,
+    config_views,
     projection_matrix,
     upstream_grad,
     DIFF_WORKLOAD,

@@ -52,6 +52,7 @@ class Config:
     kmeans_iters: int = 25
     noise: float = 0.3
     seed: int = 0          # config number; seeds derive from it
+    generator: str = "sequential"  # "sequential" (numpy PCG64 blocks) | "counter" (synth.counter)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -94,7 +95,7 @@ CONFIGS = {
         name="db200000x64_d4096_k4096_fp8", n_shapes=200000, n_views=64,
         dim=4096, n_classes=400, n_codewords=4096, n_queries=10000, query_ma=2,
         storage="fp8", rescore_r=400, topk=100, sif_k1=50, batch=256,
-        kmeans_shapes=512, kmeans_iters=6, seed=3),
+        kmeans_shapes=512, kmeans_iters=6, seed=3, generator="counter"),
 }
 
 
@@ -161,9 +162,27 @@ def shape_views(first_shape: int, n_shapes: int, n_views: int, dim: int,
     return out
 
 
+def config_views(cfg: Config, first: int, n: int, device=None, query: bool = False):
+    """Views of shapes [first, first + n) of a config's database (or query set).
+
+    float32 [n, N_v, D]: a numpy array, or a torch tensor drawn on ``device``
+    (counter generator only; bit-identical to the host draw).
+    """
+    seed = cfg.query_seed if query else cfg.db_seed
+    if cfg.generator == "counter":
+        from .counter import shape_views_np, shape_views_torch
+        if device is not None:
+            return shape_views_torch(first, n, cfg.n_views, cfg.dim, cfg.n_classes, seed, cfg.centre_seed,
+                                     device=device)
+        return shape_views_np(first, n, cfg.n_views, cfg.dim, cfg.n_classes, seed, cfg.centre_seed)
+    if device is not None:
+        raise ValueError("only the counter generator draws on a device")
+    return shape_views(first, n, cfg.n_views, cfg.dim, cfg.n_classes, seed, cfg.centre_seed, cfg.noise)
+
+
 def query_views(n_queries: int, view_choices, dim: int, n_classes: int,
                 seed: int, centre_seed: int, noise: float = 0.3,
-                max_views: int = 64):
+                max_views: int = 64, generator: str = "sequential"):
     """Query views: (float32 [sum V_q, D], int32 offsets [B+1], int64 classes [B]).
 
     Query b has class b mod n_classes; its view count is drawn uniformly from
@@ -173,8 +192,12 @@ def query_views(n_queries: int, view_choices, dim: int, n_classes: int,
     view_choices = tuple(int(v) for v in view_choices)
     counts = _gen(seed, 0).choice(np.asarray(view_choices), size=n_queries) \
         if len(view_choices) > 1 else np.full(n_queries, view_choices[0])
-    full = shape_views(0, n_queries, max(max_views, max(view_choices)), dim,
-                       n_classes, seed, centre_seed, noise)
+    nv = max(max_views, max(view_choices))
+    if generator == "counter":
+        from .counter import shape_views_np
+        full = shape_views_np(0, n_queries, nv, dim, n_classes, seed, centre_seed)
+    else:
+        full = shape_views(0, n_queries, nv, dim, n_classes, seed, centre_seed, noise)
     offs = np.zeros(n_queries + 1, np.int64)
     offs[1:] = np.cumsum(counts)
     flat = np.empty((int(offs[-1]), dim), np.float32)
@@ -244,7 +267,9 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
     """
     nq = cfg.n_queries if n_queries is None else n_queries
     db = None
-    if with_db:
+    if with_db and cfg.generator == "counter":
+        db = config_views(cfg, 0, cfg.n_shapes)
+    elif with_db:
         db = shape_views(0, cfg.n_shapes, cfg.n_views, cfg.dim, cfg.n_classes,
                          cfg.db_seed, cfg.centre_seed, cfg.noise)
     ks = cfg.kmeans_shapes or cfg.n_shapes
@@ -254,6 +279,12 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
         sample_shapes = np.sort(_gen(cfg.codebook_seed, 1).choice(cfg.n_shapes, ks, replace=False))
     if db is not None:
         sample = db[sample_shapes].reshape(-1, cfg.dim)
+    elif cfg.generator == "counter":
+        from .counter import centres_np, key_of, _views_np
+        mu, key = centres_np(cfg.n_classes, cfg.dim, cfg.centre_seed), key_of(cfg.db_seed)
+        with ThreadPoolExecutor(min(32, os.cpu_count() or 1)) as ex:
+            parts = list(ex.map(lambda s: _views_np(int(s), 1, cfg.n_views, cfg.dim, mu, key), sample_shapes))
+        sample = np.concatenate(parts).reshape(-1, cfg.dim)
     else:
         sample = np.concatenate([
             shape_views(int(s), 1, cfg.n_views, cfg.dim, cfg.n_classes, cfg.db_seed,
@@ -262,5 +293,5 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
     codebook = kmeans_codebook(sample, cfg.n_codewords, cfg.codebook_seed, cfg.kmeans_iters)
     q, q_off, q_cls = query_views(nq, cfg.query_views, cfg.dim, cfg.n_classes,
                                   cfg.query_seed, cfg.centre_seed, cfg.noise,
-                                  max_views=cfg.n_views)
+                                  max_views=cfg.n_views, generator=cfg.generator)
     return dict(db=db, codebook=codebook, q=q, q_off=q_off, q_class=q_cls)

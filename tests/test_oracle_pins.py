@@ -232,6 +232,64 @@ def test_posting_lists_partition_the_views():
         assert keys == sorted(keys)
 
 
+# ----------------------------------------------------------------- bounded top-k of Eq. 4
+@pytest.mark.parametrize("signed,ma,k", [(False, 1, 5), (False, 2, 12), (True, 1, 7), (True, 2, 30)])
+def test_bounded_topk_equals_full_ranking(signed, ma, k):
+    """The pruned walk returns the top-k of the full Eq. 4 row (brute force over all shapes)."""
+    if signed:
+        Q, off, X = rand_case(21, N=40, Nv=6, D=8, B=4, signed=True, vq=(3, 6))
+        Bk = np.random.default_rng(22).standard_normal((6, 8))
+    else:
+        X, Bk = _small_mixture(n_shapes=60, seed=14)
+        Q, off, _ = query_views(4, (5, 9, 16), X.shape[2], 5, 2014, 4014, max_views=16)
+        X, Q = X.astype(np.float64), Q.astype(np.float64)  # py_fif multiplies in the input type
+    N, Nv, D = X.shape
+    qc = O.quantize(Q, Bk, ma)
+    full = py_fif(Q, off, qc, X, O.quantize(X.reshape(-1, D), Bk, 1).reshape(N, Nv))
+    U = O.fif_upper_bound(Q, off, lambda f, n: X[f:f + n], N, chunk_shapes=7)
+    assert np.all(full <= U + 1e-14)
+    if not signed:  # all cosines >= 0: the bound is Eq. 3
+        assert np.allclose(U, py_exact(Q, off, X), atol=1e-13, rtol=0)
+    res, visited = O.fif_topk_bounded(Q, off, qc, Bk, lambda p: X[p], U, k, group=4)
+    for b, (ids, sc) in enumerate(res):
+        ref = O.rank(full[b], k)
+        assert ids.tolist() == ref[0].tolist()
+        assert np.allclose(sc, ref[1], atol=1e-13, rtol=0)
+    if not signed:
+        assert min(visited) < N  # the bound prunes on clustered views
+
+
+def test_bounded_topk_bound_uses_zero_candidate():
+    """A query view whose cosines are all negative still bounds Eq. 4 by 0, not by its max."""
+    X = -np.ones((3, 2, 2))
+    X[2, 0] = [1.0, 0.0]
+    Q = np.array([[1.0, 0.0], [0.0, 1.0]])
+    off = np.array([0, 2])
+    U = O.fif_upper_bound(Q, off, lambda f, n: X[f:f + n], 3)
+    assert U[0].tolist() == pytest.approx([0.0, 0.0, 0.5])
+    res, _ = O.fif_topk_bounded(Q, off, np.array([[0], [0]]), np.ones((1, 2)), lambda p: X[p], U, 3)
+    assert res[0][0].tolist() == [2, 0, 1]
+
+
+# ----------------------------------------------------------------- counter generator
+def test_counter_generator_host_and_torch_bit_identical():
+    torch = pytest.importorskip("torch")
+    from synth.counter import shape_views_np, shape_views_torch
+    a = shape_views_np(13, 5, 7, 48, 3, 77, 78)
+    b = shape_views_torch(13, 5, 7, 48, 3, 77, 78, device="cpu").numpy()
+    assert a.dtype == np.float32 and np.array_equal(a, b)
+    assert np.array_equal(shape_views_np(15, 1, 7, 48, 3, 77, 78)[0], a[2])  # any range alone
+    assert np.all(a >= 0) and np.allclose(np.linalg.norm(a, axis=2), 1.0, atol=1e-6)
+
+
+def test_counter_generator_splitmix64_reference_values():
+    """splitmix64 seeded with 0: its published first outputs."""
+    from synth.counter import _mix_np, _GOLDEN
+    z = (np.arange(1, 4, dtype=np.uint64) * np.uint64(_GOLDEN))
+    got = [int(v) for v in _mix_np(z)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
 # ----------------------------------------------------------------- ranking
 def test_rank_matches_sorted_with_ties():
     s = np.array([0.3, 0.9, 0.3, 0.1, 0.9, 0.0, 0.3])
