@@ -226,7 +226,7 @@ def fif_upper_bound(Q, q_off, views_of, n_shapes, chunk_shapes=1024):
     return U
 
 
-def fif_topk_bounded(Q, q_off, q_codes, codebook, views_of_shape, U, k, group=128):
+def fif_topk_bounded(Q, q_off, q_codes, codebook, views_of_shape, U, k, group=128, views_of_group=None):
     """Top-k of Eq. 4 for each query, quantising only the shapes it must visit.
 
     Shapes are visited in order of the upper bound U (``fif_upper_bound``,
@@ -234,7 +234,8 @@ def fif_topk_bounded(Q, q_off, q_codes, codebook, views_of_shape, U, k, group=12
     (``quantize``, one assignment) and its Eq. 4 score computed
     (``fif_scores``). The walk stops once k shapes are scored and the k-th
     best score exceeds the bound of the next shape: no shape left can enter
-    the top-k. ``views_of_shape(p)`` returns the views [N_v, D] of shape p.
+    the top-k. ``views_of_shape(p)`` returns the views [N_v, D] of shape p
+    (``views_of_group(ids)``, if given, those of several shapes at once).
     Returns ([(ids, scores)] ordered by (score desc, id asc) per query, the
     number of shapes visited per query).
     """
@@ -251,7 +252,7 @@ def fif_topk_bounded(Q, q_off, q_codes, codebook, views_of_shape, U, k, group=12
         pos = 0
         while pos < N:
             ids = order[pos:pos + group]
-            Xg = np.stack([views_of_shape(int(p)) for p in ids])
+            Xg = views_of_group(ids) if views_of_group else np.stack([views_of_shape(int(p)) for p in ids])
             need = [i for i, p in enumerate(ids) if int(p) not in codes_cache]
             if need:
                 cg = quantize(Xg[need].reshape(-1, Xg.shape[2]), codebook, 1).reshape(len(need), -1)

@@ -213,6 +213,9 @@ class Index:
                     if isinstance(x, np.ndarray):
                         x = np.ascontiguousarray(x, dtype=np.float32)
                     _check(lib.gift_build_add(self._h, p, _ptr(x), int(first), int(n), st))
+                    del x
+                import torch
+                torch.cuda.empty_cache()  # the stores allocated at the end of pass 1 are large
                 _check(lib.gift_build_end_pass(self._h, p, st))
         except BaseException:
             self.close()

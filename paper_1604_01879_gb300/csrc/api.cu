@@ -767,6 +767,12 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
   Scratch sc(s);
   if (pass == 1) {
     build_lists(ix, sc, s);
+    {  // the stores need most of the device: hand cached scratch back first
+      cudaMemPool_t pool;
+      GIFT_CUDA(cudaDeviceGetDefaultMemPool(&pool, ix.device));
+      GIFT_CUDA(cudaStreamSynchronize(s));
+      GIFT_CUDA(cudaMemPoolTrimTo(pool, 0));
+    }
     const size_t eb = dtype_bytes(ix.prm.storage);
     ix.list_rows_alloc = n_rows + 256;
     ix.list_feat = ix.alloc<uint8_t>((size_t)ix.list_rows_alloc * D * eb);

@@ -13,6 +13,7 @@ from .workload import (  # noqa: F401
     kmeans_codebook,
     make_config_inputs,
     config_views,
+    config_codebook,
     projection_matrix,
     upstream_grad,
     DIFF_WORKLOAD,

@@ -272,6 +272,15 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
     elif with_db:
         db = shape_views(0, cfg.n_shapes, cfg.n_views, cfg.dim, cfg.n_classes,
                          cfg.db_seed, cfg.centre_seed, cfg.noise)
+    codebook = config_codebook(cfg, db)
+    q, q_off, q_cls = query_views(nq, cfg.query_views, cfg.dim, cfg.n_classes,
+                                  cfg.query_seed, cfg.centre_seed, cfg.noise,
+                                  max_views=cfg.n_views, generator=cfg.generator)
+    return dict(db=db, codebook=codebook, q=q, q_off=q_off, q_class=q_cls)
+
+
+def config_codebook(cfg: Config, db=None) -> np.ndarray:
+    """The codebook fixture of a config: seeded k-means on a seeded sample of its database shapes."""
     ks = cfg.kmeans_shapes or cfg.n_shapes
     if ks >= cfg.n_shapes:
         sample_shapes = np.arange(cfg.n_shapes)
@@ -290,8 +299,4 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
             shape_views(int(s), 1, cfg.n_views, cfg.dim, cfg.n_classes, cfg.db_seed,
                         cfg.centre_seed, cfg.noise, threads=1) for s in sample_shapes
         ]).reshape(-1, cfg.dim)
-    codebook = kmeans_codebook(sample, cfg.n_codewords, cfg.codebook_seed, cfg.kmeans_iters)
-    q, q_off, q_cls = query_views(nq, cfg.query_views, cfg.dim, cfg.n_classes,
-                                  cfg.query_seed, cfg.centre_seed, cfg.noise,
-                                  max_views=cfg.n_views, generator=cfg.generator)
-    return dict(db=db, codebook=codebook, q=q, q_off=q_off, q_class=q_cls)
+    return kmeans_codebook(sample, cfg.n_codewords, cfg.codebook_seed, cfg.kmeans_iters)
