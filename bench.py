@@ -600,11 +600,22 @@ def main():
                 ref = dict(zip(ref_ids, got["scores"][j]))
                 errs += [abs(float(s_) - ref[int(p_)]) / max(abs(ref[int(p_)]), 1e-30)
                          for p_, s_ in zip(ids[j], sc[j]) if int(p_) in ref]
+            # recall against the rescore depth (R = 0: ranked by the FP8 scan alone)
+            sweep = {}
+            for r_ in (0, 100, 200, 400, 600, 800, R):
+                if r_ > R or (0 < r_ < topk):
+                    continue
+                ix.set_rescore_depth(r_)
+                ids_r = ix.query(qs, off_s, mode="fif", topk=topk)[0].cpu().numpy()
+                sweep[r_] = float(np.mean([len(set(ids_r[j].tolist()) & set(got["ids"][j])) / topk
+                                           for j in range(len(q_sample))]))
+            ix.set_rescore_depth(R)
             line["recall_at_100"] = {"value": float(np.mean(rec)), "min": float(np.min(rec)),
                                      "queries": len(rec), "query_ids": q_sample,
                                      "max_rel_score_err": float(np.max(errs)) if errs else None,
                                      "vs": "FP64 oracle, Eq. 4 (top-k pruned by the Eq. 3 bound)",
-                                     "oracle_shapes_visited": got["visited"]}
+                                     "oracle_shapes_visited": got["visited"],
+                                     "vs_rescore_depth": sweep}
             line["cpu_baseline"] = {"value": len(q_sample) / got["seconds"], "unit": "queries/s",
                                     "cores": got["threads"], "kind": "oracle",
                                     "sample": f"{len(q_sample)} queries through the FP64 oracle: bound pass "

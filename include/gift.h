@@ -257,6 +257,12 @@ GIFT_API gift_status gift_export_sif(const gift_index* index, int64_t* entry_off
 /* Sizes of a built index. */
 GIFT_API gift_status gift_index_info(const gift_index* index, gift_index_info_t* out);
 
+/* Change the FP32 rescore depth R of later gift_query calls (0 = rank by the
+ * store's scores alone). R > 0 needs an index built with rescore_r > 0 (the
+ * rescore store). Not to be called while another call or a server uses the
+ * index. Errors: EINVAL (R outside [0, 1024]), EUNSUPPORTED, ESTATE. */
+GIFT_API gift_status gift_set_rescore_depth(gift_index* index, int32_t rescore_r);
+
 /*
  * Per-stage timing of gift_query / gift_rerank calls on this index: when
  * enabled, each call records CUDA events around its stages on its stream;

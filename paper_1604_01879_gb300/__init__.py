@@ -80,6 +80,7 @@ _I32, _I64 = ctypes.c_int32, ctypes.c_int64
 _SIGS = {
     "gift_build_index": (_I32, [ctypes.POINTER(_Params), _P, _P, _P, ctypes.POINTER(_P)]),
     "gift_destroy_index": (None, [_P]),
+    "gift_set_rescore_depth": (_I32, [_P, _I32]),
     "gift_build_begin": (_I32, [ctypes.POINTER(_Params), _P, _P, ctypes.POINTER(_P)]),
     "gift_build_add": (_I32, [_P, _I32, _P, _I32, _I32, _P]),
     "gift_build_end_pass": (_I32, [_P, _I32, _P]),
@@ -282,6 +283,11 @@ class Index:
         i = _Info()
         _check(load().gift_index_info(self._h, ctypes.byref(i)))
         return {n: getattr(i, n) for n, _ in _Info._fields_}
+
+    def set_rescore_depth(self, r: int):
+        """FP32 rescore depth of later queries (0 = scores of the list store alone)."""
+        _check(load().gift_set_rescore_depth(self._h, int(r)))
+        self.rescore_r = int(r)
 
     def set_timing(self, on: bool = True):
         _check(load().gift_set_timing(self._h, int(bool(on))))

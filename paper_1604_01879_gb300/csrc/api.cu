@@ -999,6 +999,18 @@ gift_status gift_index_info(const gift_index* index, gift_index_info_t* out) {
   });
 }
 
+gift_status gift_set_rescore_depth(gift_index* index, int32_t rescore_r) {
+  return gift::guard("gift_set_rescore_depth", [&] {
+    GIFT_REQUIRE(index, "NULL index");
+    Index& ix = *reinterpret_cast<Index*>(index);
+    if (!ix.ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
+    GIFT_REQUIRE(rescore_r >= 0 && rescore_r <= 1024, "rescore_r must be in [0, 1024]");
+    if (rescore_r > 0 && !ix.list_lo && !ix.master)
+      gift::fail(GIFT_EUNSUPPORTED, "the index was built without a rescore store (rescore_r == 0)");
+    ix.prm.rescore_r = rescore_r;
+  });
+}
+
 gift_status gift_set_timing(gift_index* index, int32_t enable) {
   return gift::guard("gift_set_timing", [&] {
     GIFT_REQUIRE(index, "NULL index");

@@ -94,7 +94,7 @@ CONFIGS = {
     "db200000x64_d4096_k4096_fp8": Config(
         name="db200000x64_d4096_k4096_fp8", n_shapes=200000, n_views=64,
         dim=4096, n_classes=400, n_codewords=4096, n_queries=10000, query_ma=2,
-        storage="fp8", rescore_r=400, topk=100, sif_k1=50, batch=256,
+        storage="fp8", rescore_r=1000, topk=100, sif_k1=50, batch=256,
         kmeans_shapes=512, kmeans_iters=6, seed=3, generator="counter"),
 }
 

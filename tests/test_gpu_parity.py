@@ -327,3 +327,28 @@ def test_sharded_indexes_merge_to_the_unsharded_ranking(gpu_lib):
     assert np.array_equal(mi, ids.cpu().numpy())
     assert np.allclose(ms, sc.cpu().numpy(), rtol=1e-6, atol=1e-7)
     full.close()
+
+
+def test_rescore_depth_can_change_after_build(gpu_lib):
+    """R = 0 on a rescoring index ranks by the store alone, like an index built without rescore;
+    restoring R gives the built results again; an index without a rescore store refuses R > 0."""
+    import torch
+    N, Nv, D, C, K = 120, 16, 64, 4, 12
+    X, cb, Q, qoff, dbc, qc = _case(N, Nv, D, C, K, 6, (16, 7), 121)
+    q = torch.from_numpy(Q).cuda()
+    with_r = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="bf16", rescore_r=30, keep_exact=False)
+    no_r = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="bf16", rescore_r=0, keep_exact=False)
+    ref_i, ref_s = with_r.query(q, qoff, topk=10)
+    with_r.set_rescore_depth(0)
+    a = with_r.query(q, qoff, topk=10)
+    b = no_r.query(q, qoff, topk=10)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    with_r.set_rescore_depth(30)
+    c = with_r.query(q, qoff, topk=10)
+    assert torch.equal(c[0], ref_i) and torch.equal(c[1], ref_s)
+    with pytest.raises(gpu_lib.GiftError):
+        no_r.set_rescore_depth(10)
+    with pytest.raises(gpu_lib.GiftError):
+        with_r.set_rescore_depth(2000)
+    with_r.close()
+    no_r.close()
