@@ -201,6 +201,62 @@ def oracle_bounded_worker(cfg_name, q_ids, codebook, k, threads, conn):
     conn.close()
 
 
+def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks, peak_src, with_traffic=True):
+    """Roofline entry of the dominant kernel (most device time per step), from the
+    per-kernel CUDA-event times ``st`` and the batch's work counters."""
+    bf16_peak = float(peaks["bf16_tflops"])
+    hbm_peak = float(peaks["hbm_gbs"])
+    D = cfg.dim
+    # useful tensor-core FLOPs (unpadded pairs):
+    #   scan     2 * pairs * D                       (one product)
+    #   rescore  3 * 2 * pairs * D                   (hi*hi + hi*lo + lo*hi, FP32-accurate)
+    #   assign   3 * 2 * rows * K * D                (same split)
+    # the FP8 scan runs kind::f8f6f4 MMAs: its peak is the BF16 peak x 2 (nominal ratio)
+    scan_peak = bf16_peak * (2.0 if cfg.storage == "fp8" else 1.0)
+    # algorithmic bytes:
+    #   scan     every touched list row once per batch (store row + id + scale)
+    #   rescore  every touched list row once per batch (two-part BF16 row + id + scale)
+    #   assign   the FP32 query rows and the FP32 codebook once
+    kernels = {
+        "tc_engine<ScanPolicy>": (st["scan_kernel_ms"], 2.0 * scan_pairs * D, scan_bytes, ["k_scan_tc.cu"],
+                                  scan_peak),
+        "tc_engine<RescorePolicy>": (st["rescore_kernel_ms"], 6.0 * scan_pairs * D, rescore_bytes,
+                                     ["k_scan_tc.cu"], bf16_peak),
+        "tc_engine<AssignPolicy>": (st["assign_kernel_ms"], 6.0 * assign_rows * cfg.n_codewords * D,
+                                    assign_rows * D * 4 + cfg.n_codewords * D * 4, ["k_assign.cu"], bf16_peak),
+    }
+    # each kernel against both roofs; its bound is the roof it is closer to
+    table = {}
+    for name, (ms, flops, nbytes, files, pk) in kernels.items():
+        if ms > 0:
+            ach = flops / (ms / 1e3) / 1e12
+            gbs = nbytes / (ms / 1e3) / 1e9
+            t_frac, h_frac = ach / pk, gbs / hbm_peak
+            if h_frac > t_frac:
+                table[name] = {"ms": ms, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": h_frac, "tensor_frac": t_frac}
+            else:
+                table[name] = {"ms": ms, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                               "frac": t_frac, "hbm_frac": h_frac}
+    dom = max(table, key=lambda k: table[k]["ms"])
+    src_hash = kernel_source_hash(kernels[dom][3] + ["tc_engine.cuh", "tc_common.cuh"])
+    traffic, _ = recorded_traffic(dom, src_hash) if with_traffic else (None, None)
+    dt = table[dom]
+    if dt["bound"] == "hbm":
+        psrc = f"{peak_src} hbm_gbs"
+        work = "algorithmic bytes: every list row the batch touches, read once"
+    else:
+        psrc = f"{peak_src} bf16_tflops (burst)" + (" x 2 for E4M3" if dt["peak"] != bf16_peak else "")
+        work = ("useful MMA FLOPs on unpadded pairs; the rescore and quantiser run three BF16 products per "
+                "FP32-accurate product")
+    return {"kernel": dom, "bound": dt["bound"], "achieved": dt["achieved"], "peak": dt["peak"],
+            "unit": dt["unit"], "frac": dt["frac"], "traffic": traffic, "peak_source": psrc,
+            "kernel_ms": dt["ms"], "work": work, "src_hash": src_hash, "all": table,
+            "scan_hbm": {"algorithmic_bytes": scan_bytes,
+                         "achieved_gbs": scan_bytes / (st["scan_kernel_ms"] / 1e3) / 1e9,
+                         "peak_gbs": hbm_peak}}
+
+
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -408,6 +464,7 @@ def main():
                                "total_ms", "assign_kernel_ms", "scan_kernel_ms", "rescore_kernel_ms")}
     st["rerank_ms"] = avg("rerank_ms", 1)
     scan_bytes = stages[-1][0]["scan_bytes"]
+    rescore_bytes = stages[-1][0]["rescore_bytes"]
     scan_pairs = stages[-1][0]["scan_pairs"]
     assign_rows = stages[-1][0]["assign_rows"]
 
@@ -545,40 +602,8 @@ def main():
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)
     peaks, peak_src = measured_peaks()
-    bf16_peak = float(peaks["bf16_tflops"])
-    D = cfg.dim
-    # executed BF16 tensor-core FLOPs on useful (unpadded) work:
-    #   scan     2 * pairs * D                       (one product)
-    #   rescore  3 * 2 * pairs * D                   (hi*hi + hi*lo + lo*hi, FP32-accurate)
-    #   assign   3 * 2 * rows * K * D                (same split)
-    # the FP8 scan runs kind::f8f6f4 MMAs: its peak is the BF16 peak x 2 (nominal ratio)
-    scan_peak = bf16_peak * (2.0 if cfg.storage == "fp8" else 1.0)
-    kernels = {
-        "tc_engine<ScanPolicy>": (st["scan_kernel_ms"], 2.0 * scan_pairs * D, ["k_scan_tc.cu"], scan_peak),
-        "tc_engine<RescorePolicy>": (st["rescore_kernel_ms"], 6.0 * scan_pairs * D, ["k_scan_tc.cu"], bf16_peak),
-        "tc_engine<AssignPolicy>": (st["assign_kernel_ms"], 6.0 * assign_rows * cfg.n_codewords * D,
-                                    ["k_assign.cu"], bf16_peak),
-    }
-    table = {}
-    for name, (ms, flops, files, pk) in kernels.items():
-        if ms > 0:
-            ach = flops / (ms / 1e3) / 1e12
-            table[name] = {"ms": ms, "achieved": ach, "frac": ach / pk, "peak": pk}
-    dom = max(table, key=lambda k: table[k]["ms"])
-    src_hash = kernel_source_hash(kernels[dom][2] + ["tc_engine.cuh", "tc_common.cuh"])
-    traffic, traffic_src = recorded_traffic(dom, src_hash)
-    line["roofline"] = {"kernel": dom, "bound": "tensor", "achieved": table[dom]["achieved"],
-                        "peak": table[dom]["peak"], "unit": "TFLOP/s", "frac": table[dom]["frac"],
-                        "traffic": traffic if not large else None,
-                        "peak_source": f"{peak_src} bf16_tflops (burst)"
-                                       + (" x 2 for E4M3" if table[dom]["peak"] != bf16_peak else ""),
-                        "kernel_ms": table[dom]["ms"],
-                        "work": "executed BF16 MMA FLOPs on unpadded pairs; the rescore and quantiser run "
-                                "three BF16 products per FP32-accurate product",
-                        "src_hash": src_hash, "all": table,
-                        "scan_hbm": {"algorithmic_bytes": scan_bytes,
-                                     "achieved_gbs": scan_bytes / (st["scan_kernel_ms"] / 1e3) / 1e9,
-                                     "peak_gbs": peaks["hbm_gbs"]}}
+    line["roofline"] = roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks, peak_src,
+                                with_traffic=not large)
 
     # ---- recall@100 vs the FP64 oracle on sampled queries (untimed)
     db_codes = None

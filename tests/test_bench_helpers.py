@@ -1,0 +1,32 @@
+"""Host-side arithmetic of bench.py (roofline entry, traffic lookup), on made-up timings."""
+import json
+
+import bench
+from synth import CONFIGS
+
+
+def _st(scan, resc, assign):
+    return {"scan_kernel_ms": scan, "rescore_kernel_ms": resc, "assign_kernel_ms": assign}
+
+
+def test_roofline_picks_dominant_kernel_and_its_roof():
+    cfg = CONFIGS["db12000x64_d4096_k1024"]
+    peaks = {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}
+    pairs, D = 7.3e8, cfg.dim
+    # rescore dominant and compute-bound: 6 * pairs * D flops in 12 ms
+    r = bench.roofline(cfg, _st(3.0, 12.0, 1.0), pairs, 6e9, 12e9, 64000, peaks, "measured")
+    assert r["kernel"] == "tc_engine<RescorePolicy>" and r["bound"] == "tensor"
+    assert abs(r["achieved"] - 6 * pairs * D / 12e-3 / 1e12) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 2000.0) < 1e-12
+    assert r["unit"] == "TFLOP/s" and json.dumps(r)
+    # the same kernel reading 210 GB in 31 ms is HBM-bound
+    r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.0, 31.0, 1.2), 7.3e8, 47e9, 210e9, 16384,
+                       peaks, "measured", with_traffic=False)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+    assert abs(r["achieved"] - 210e9 / 31e-3 / 1e9) < 1e-6 * r["achieved"]
+    # the FP8 scan is held against twice the BF16 peak
+    assert r["all"]["tc_engine<ScanPolicy>"].get("tensor_frac") is not None
+
+
+def test_recorded_traffic_ignores_other_sources(tmp_path, monkeypatch):
+    assert bench.recorded_traffic("no-such-kernel", "0" * 12) == (None, None)
