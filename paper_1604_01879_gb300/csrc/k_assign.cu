@@ -1,19 +1,22 @@
 // Quantiser c(x) = argmin_k ||x - b_k||^2 with multiple assignment (Sec. 2.3).
 //
 // Coarse stage (tensor cores): score_k = x.b_k - ||b_k||^2 / 2 (argmax of the
-// score is argmin of the distance) for 128 rows x all codewords per work item,
-// from two-part BF16 operands (x = hi + lo, three products, FP32 accumulate),
-// codewords in chunks of 256 columns. The epilogue keeps each row's 16 best
-// coarse scores; every codeword whose coarse score lies within 2E of the
-// ma-th best is a candidate, where E bounds the coarse error:
+// score is argmin of the distance) from two-part BF16 operands (x = hi + lo,
+// three products, FP32 accumulate). A work item is 128 rows x one chunk of 256
+// codewords; the chunks of one row tile are consecutive items, so the CTAs
+// that run them at the same time share the row tile through L2. The epilogue
+// keeps each row's 16 best coarse scores of its chunk.
+// Refine stage (CUDA cores, one warp per row): every codeword whose coarse
+// score lies within 2E of the ma-th best over all chunks is a candidate, where
+// E bounds the coarse error:
 //   E = 2^-12 (||x|| max_k ||b_k|| + max_k ||b_k||^2 / 2),
 // about five times the representation bound of the split (3 * 2^-16 relative
-// per product) plus the measured accumulation error. When all 16 kept scores
-// are candidates the row is marked for a full exact pass.
-// Refine stage (CUDA cores, one warp per row): exact squared distances of the
-// candidates in two-float (~2^-44 relative) arithmetic, ma smallest by
-// (distance, index). Results equal an exact evaluation except where
-// distances tie to ~1e-13.
+// per product) plus the measured accumulation error. When a chunk's 16th kept
+// score is still a candidate, that chunk may hold more, and the row takes the
+// exact pass over every codeword. The candidates' squared distances are
+// evaluated in two-float (~2^-44 relative) arithmetic; the ma smallest by
+// (distance, index) are the codes. Results equal an exact evaluation except
+// where distances tie to ~1e-13.
 #include "gift_internal.cuh"
 #include "tc_engine.cuh"
 
@@ -22,38 +25,39 @@ namespace gift {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kT = 16;  // coarse candidates kept per row
+constexpr int kT = 16;    // coarse candidates kept per row and chunk
+constexpr int TNA = 256;  // codewords per chunk (AssignPolicy::TN)
 
 struct AssignPolicy {
-  static constexpr int TN = 256, NBUF = 2, STAGES = 2, SPLIT = 3, EB = 2;
+  static constexpr int TN = TNA, NBUF = 2, STAGES = 2, SPLIT = 3, EB = 2;
   static constexpr int kWarpSmem = TN * 4;
   int64_t n;          // rows
   int K;
+  int nch;            // codeword chunks of TN
   int nkb;
-  int ma;
-  const float* x_inv; // [n] 1/||x||
   const float* half_sq;
-  float bmax;
-  int32_t* cand;      // [n, kT]
-  int32_t* cand_cnt;  // [n]; -1 = refine every codeword
+  float* cval;        // [n, nch, kT] best coarse scores of each chunk, descending
+  int32_t* cidx;      // [n, nch, kT] their codewords (0x7fffffff: none)
   struct Item {
     int64_t r0;
     int nr;
+    int c;
   };
   struct Ctx {
     float val[kT];
     int idx[kT];
   };
-  __device__ __forceinline__ int64_t total() const { return cdiv(n, tc::kTM); }
+  __device__ __forceinline__ int64_t total() const { return cdiv(n, tc::kTM) * nch; }
   __device__ __forceinline__ Item decode(int64_t item) const {
     Item it;
-    it.r0 = item * tc::kTM;
+    it.r0 = (item / nch) * tc::kTM;
+    it.c = (int)(item % nch);
     it.nr = (int)min((int64_t)tc::kTM, n - it.r0);
     return it;
   }
-  __device__ __forceinline__ int nchunks(const Item&) const { return (K + TN - 1) / TN; }
-  __device__ __forceinline__ void chunk(const Item&, int c, int& br, int& kb0, int& kb1) const {
-    br = c * TN;
+  __device__ __forceinline__ int nchunks(const Item&) const { return 1; }
+  __device__ __forceinline__ void chunk(const Item& it, int, int& br, int& kb0, int& kb1) const {
+    br = it.c * TN;
     kb0 = 0;
     kb1 = nkb;
   }
@@ -65,9 +69,10 @@ struct AssignPolicy {
       x.idx[t] = 0x7fffffff;
     }
   }
-  __device__ __forceinline__ void epi_chunk(const Item&, int c, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
+  __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
     float* hs = reinterpret_cast<float*>(ws);
     const int lane = threadIdx.x & 31;
+    const int c = it.c;
     for (int j = lane; j < TN; j += 32) {
       const int k = c * TN + j;
       hs[j] = k < K ? half_sq[k] : INFINITY;
@@ -102,25 +107,12 @@ struct AssignPolicy {
   }
   __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int m, uint8_t*) const {
     if (m >= it.nr) return;
-    const int64_t row = it.r0 + m;
-    const float xi = x_inv[row];
-    float thr = x.val[0];
-#pragma unroll
-    for (int t = 0; t < kT; ++t)
-      if (t == ma - 1) thr = x.val[t];
-    const float xn = xi > 0.f ? 1.0001f / xi : 0.f;
-    const float E = 2.44140625e-4f * (xn * bmax + 0.5f * bmax * bmax) + 1e-30f;
-    const float lim = thr - 2.f * E;
-    int cnt = 0;
+    const int64_t o = ((it.r0 + m) * nch + it.c) * kT;
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
-      if (x.val[t] >= lim && x.idx[t] != 0x7fffffff) {
-        cand[row * kT + cnt] = x.idx[t];
-        ++cnt;
-      }
+      cval[o + t] = x.val[t];
+      cidx[o + t] = x.idx[t];
     }
-    const bool overflow = (cnt == kT && K > kT) || xi == 0.f;
-    cand_cnt[row] = overflow ? -1 : cnt;
   }
 };
 
@@ -173,17 +165,68 @@ __device__ __forceinline__ bool df_less(float ah, float al, int ak, float bh, fl
   return ak < bk;
 }
 
+// warp-wide best entry of (value desc, position asc) strictly after the key
+// (pv, pp) in that order; positions index the row's nch * kT kept entries
+__device__ __forceinline__ void next_best(const float* __restrict__ v, const int32_t* __restrict__ id, int tot,
+                                          float pv, int pp, int lane, float& bv, int& bp) {
+  bv = -INFINITY;
+  bp = 0x7fffffff;
+  for (int e = lane; e < tot; e += 32) {
+    const float x = v[e];
+    if (id[e] == 0x7fffffff) continue;
+    const bool after = x < pv || (x == pv && e > pp);
+    if (after && (x > bv || (x == bv && e < bp))) {
+      bv = x;
+      bp = e;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(kFull, bv, o);
+    const int op = __shfl_xor_sync(kFull, bp, o);
+    if (ov > bv || (ov == bv && op < bp)) {
+      bv = ov;
+      bp = op;
+    }
+  }
+}
+
 __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__ X, int64_t n, int D,
                                                        const float* __restrict__ cb, int K, int ma,
-                                                       const int32_t* __restrict__ cand,
-                                                       const int32_t* __restrict__ cand_cnt,
+                                                       const float* __restrict__ cval,
+                                                       const int32_t* __restrict__ cidx, int nch,
+                                                       const float* __restrict__ x_inv, float bmax,
                                                        int32_t* __restrict__ codes) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + w;
   if (r >= n) return;
   const float* x = X + r * (int64_t)D;
-  const int cnt = cand_cnt[r];
-  const int ncheck = cnt < 0 ? K : cnt;
+  const int tot = nch * kT;
+  const float* v = cval + r * tot;
+  const int32_t* id = cidx + r * tot;
+  // the ma-th best coarse score over all chunks
+  float thr = INFINITY;
+  int tp = -1, found = 0;
+  for (int a = 0; a < ma; ++a) {
+    float bv;
+    int bp;
+    next_best(v, id, tot, thr, tp, lane, bv, bp);
+    if (bp == 0x7fffffff) break;
+    thr = bv;
+    tp = bp;
+    ++found;
+  }
+  const float xi = x_inv[r];
+  const float xn = xi > 0.f ? 1.0001f / xi : 0.f;
+  const float E = 2.44140625e-4f * (xn * bmax + 0.5f * bmax * bmax) + 1e-30f;
+  const float lim = thr - 2.f * E;
+  // a chunk whose last kept score is a candidate may hold more candidates
+  bool full = xi == 0.f || found < ma;  // (fewer kept scores than ma only with non-finite inputs)
+  for (int c = lane; c < nch; c += 32) {
+    const int e = c * kT + kT - 1;
+    if (id[e] != 0x7fffffff && v[e] >= lim && min(TNA, K - c * TNA) > kT) full = true;
+  }
+  full = __any_sync(kFull, full);
   float H[GIFT_MAX_MA], Lo[GIFT_MAX_MA];
   int Kx[GIFT_MAX_MA];
 #pragma unroll
@@ -192,26 +235,42 @@ __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__
     Lo[a] = 0.f;
     Kx[a] = 0x7fffffff;
   }
-  for (int c = 0; c < ncheck; ++c) {
-    const int k = cnt < 0 ? c : cand[r * kT + c];
-    float h, l;
-    dist_df(x, cb + (int64_t)k * D, D, lane, h, l);
-    // insert into the ascending list of the ma best (registers, unrolled)
-    if (df_less(h, l, k, H[GIFT_MAX_MA - 1], Lo[GIFT_MAX_MA - 1], Kx[GIFT_MAX_MA - 1])) {
-      H[GIFT_MAX_MA - 1] = h;
-      Lo[GIFT_MAX_MA - 1] = l;
-      Kx[GIFT_MAX_MA - 1] = k;
+  const int nscan = full ? K : tot;
+  for (int base = 0; base < nscan; base += 32) {
+    const int e = base + lane;
+    bool take;
+    int kk;
+    if (full) {
+      take = e < K;
+      kk = e;
+    } else {
+      kk = e < tot ? id[e] : 0x7fffffff;
+      take = e < tot && kk != 0x7fffffff && v[e] >= lim;
+    }
+    unsigned mask = __ballot_sync(kFull, take);
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int k = __shfl_sync(kFull, kk, j);
+      float h, l;
+      dist_df(x, cb + (int64_t)k * D, D, lane, h, l);
+      // insert into the ascending list of the ma best (registers, unrolled)
+      if (df_less(h, l, k, H[GIFT_MAX_MA - 1], Lo[GIFT_MAX_MA - 1], Kx[GIFT_MAX_MA - 1])) {
+        H[GIFT_MAX_MA - 1] = h;
+        Lo[GIFT_MAX_MA - 1] = l;
+        Kx[GIFT_MAX_MA - 1] = k;
 #pragma unroll
-      for (int t = GIFT_MAX_MA - 1; t > 0; --t) {
-        if (df_less(H[t], Lo[t], Kx[t], H[t - 1], Lo[t - 1], Kx[t - 1])) {
-          const float th = H[t], tl = Lo[t];
-          const int tk = Kx[t];
-          H[t] = H[t - 1];
-          Lo[t] = Lo[t - 1];
-          Kx[t] = Kx[t - 1];
-          H[t - 1] = th;
-          Lo[t - 1] = tl;
-          Kx[t - 1] = tk;
+        for (int t = GIFT_MAX_MA - 1; t > 0; --t) {
+          if (df_less(H[t], Lo[t], Kx[t], H[t - 1], Lo[t - 1], Kx[t - 1])) {
+            const float th = H[t], tl = Lo[t];
+            const int tk = Kx[t];
+            H[t] = H[t - 1];
+            Lo[t] = Lo[t - 1];
+            Kx[t] = Kx[t - 1];
+            H[t - 1] = th;
+            Lo[t - 1] = tl;
+            Kx[t - 1] = tk;
+          }
         }
       }
     }
@@ -258,8 +317,9 @@ void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* c
   const int64_t rows_alloc = chunk + tc::kTM;  // one box of padding rows
   __nv_bfloat16* hi = sc.get<__nv_bfloat16>((size_t)rows_alloc * D);
   __nv_bfloat16* lo = sc.get<__nv_bfloat16>((size_t)rows_alloc * D);
-  int32_t* cand = sc.get<int32_t>((size_t)chunk * kT);
-  int32_t* cnt = sc.get<int32_t>(chunk);
+  const int nch = (int)cdiv(K, TNA);
+  float* cval = sc.get<float>((size_t)chunk * nch * kT);
+  int32_t* cidx = sc.get<int32_t>((size_t)chunk * nch * kT);
   float* inv = nullptr;
   if (!x_inv) {
     inv = sc.get<float>(n);
@@ -275,24 +335,22 @@ void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* c
     AssignPolicy p;
     p.n = m;
     p.K = K;
+    p.nch = nch;
     p.nkb = (int)cdiv(D, tc::kTK);
-    p.ma = ma;
-    p.x_inv = x_inv + r0;
     p.half_sq = ix.cb_half_sq;
-    p.bmax = ix.cb_max_norm;
-    p.cand = cand;
-    p.cand_cnt = cnt;
+    p.cval = cval;
+    p.cidx = cidx;
     const CUtensorMap tA = make_tmap_bf16(hi, rows_alloc, D, tc::kTM);
     const CUtensorMap tA2 = make_tmap_bf16(lo, rows_alloc, D, tc::kTM);
-    const int grid = (int)std::min<int64_t>(sms, cdiv(m, tc::kTM));
+    const int grid = (int)std::min<int64_t>(sms, cdiv(m, tc::kTM) * nch);
     if (kc) kc->begin(0);
     tc::launch_engine(tA, tB, tA2, tB2, p, ix.d_err, grid, s);
     if (kc) {
       kc->end(0);
       kc->assign_rows += m;
     }
-    k_assign_refine<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(X + r0 * D, m, D, ix.codebook, K, ma, cand, cnt,
-                                                          codes + r0 * ma);
+    k_assign_refine<<<(unsigned)cdiv(m, 8), 256, 0, s>>>(X + r0 * D, m, D, ix.codebook, K, ma, cval, cidx, nch,
+                                                          x_inv + r0, ix.cb_max_norm, codes + r0 * ma);
     GIFT_LAUNCHED("k_assign_refine");
   }
 }
