@@ -595,6 +595,8 @@ def main():
         "e2e": {"value": B / (e2e_ms / 1e3) * world, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
+        "gpu_launches": n_launches,
+        "gpu_launches_per_step": n_launches / args.steps,
         "build_s": build_s,
         "serving": serving,
         "differentiation": diff,
