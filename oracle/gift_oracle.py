@@ -23,6 +23,10 @@ as library steps. What each function computes, with the passage it follows:
 * ``build_sif``/``sif_scores_inverted``  Eq. 13 / Eq. 14 over the second
                            inverted file (Sec. 2.4.2, Fig. 3)
 * ``rerank``               the re-ranked list by (S' desc, S desc, id asc)
+* ``augment``/``aca_fuse``/``aca_activation``/``rerank_aca``  two similarity
+                           measures: neighbour augmentation (Eq. 10), co-augmentation
+                           (Eq. 11), the generalised-mean aggregation of Eq. 9 and the
+                           re-rank by S' of the fused activations
 * ``match_forward``/``match_backward``  Eq. 3 after a linear view projection
                            u = W q, and its gradient through the argmax view
 
@@ -36,6 +40,9 @@ Readings where the paper is silent (each also listed in the design notes):
 * ranking ties go to the lower shape id; re-ranking orders by
   (S' desc, S desc, id asc); S' = 0 when both F vectors are zero;
 * a database shape's neighbour set N_k1 includes the shape itself;
+* with two measures, the re-ranked order breaks S' ties by the first measure's
+  score S^(1), then by id; the neighbour sets of Eqs. 10/11 are the first k2
+  entries of the same rankings that give N_k1;
 * the squared distance is evaluated as ||x||^2 - 2 x.b + ||b||^2 in float64
   (an algebraic identity; its rounding, about 1e-15 of ||x||^2 + ||b||^2,
   is far below any margin at which codes are compared).
@@ -367,6 +374,74 @@ def rerank(S_q, F_db, k1, k):
         Fq = membership(S_q[b], k1)
         Sprime = np.array([contextual(Fq, F_db[p]) for p in range(N)])
         order = np.lexsort((np.arange(N), -S_q[b], -Sprime))[:k]
+        ids[b] = order
+        sp[b] = Sprime[order]
+    return ids, sp
+
+
+def augment(F_rows, nbrs):
+    """Eq. 10 (and each line of Eq. 11): the mean of the activations F_i of the
+    shapes i in the neighbour set ``nbrs`` (ids); ``F_rows`` float64 [N, N]."""
+    nbrs = np.asarray(nbrs, np.int64)
+    return _f64(F_rows)[nbrs].sum(axis=0) / len(nbrs)
+
+
+def aca_fuse(F1, F2, alpha):
+    """Eq. 9: element-wise generalised mean with exponent alpha of two activations."""
+    F1 = _f64(F1)
+    F2 = _f64(F2)
+    return ((F1 ** alpha + F2 ** alpha) / 2.0) ** (1.0 / alpha)
+
+
+def aca_activation(S1, S2, F1_db, F2_db, k1, k2, alpha, mode):
+    """Aggregated contextual activation (Sec. 2.4) of one shape from its two score rows.
+
+    mode "none": F^(l) = Eq. 7 of measure l (first k1 neighbours);
+    mode "aug":  F^(l) = Eq. 10, the mean of the database activations F_i^(l)
+                 over the shape's first k2 neighbours under measure l;
+    mode "co":   Eq. 11, the same mean over the first k2 neighbours under the
+                 other measure;
+    then Eq. 9 fuses F^(1) and F^(2). ``F1_db``/``F2_db`` are the database
+    activations (Eq. 7 rows, ``db_memberships``).
+    """
+    if mode == "none":
+        A1, A2 = membership(S1, k1), membership(S2, k1)
+    else:
+        n1 = rank(S1, k2)[0]
+        n2 = rank(S2, k2)[0]
+        if mode == "aug":
+            A1, A2 = augment(F1_db, n1), augment(F2_db, n2)
+        elif mode == "co":
+            A1, A2 = augment(F1_db, n2), augment(F2_db, n1)
+        else:
+            raise ValueError(mode)
+    return aca_fuse(A1, A2, alpha)
+
+
+def aca_db(S1_db, S2_db, k1, k2, alpha, mode):
+    """ACA rows of every database shape, float64 [N, N]; row p uses the score
+    rows of p matched as a query under each measure (self included)."""
+    F1_db, F2_db = db_memberships(S1_db, k1), db_memberships(S2_db, k1)
+    N = F1_db.shape[0]
+    return np.stack([aca_activation(S1_db[p], S2_db[p], F1_db, F2_db, k1, k2, alpha, mode) for p in range(N)])
+
+
+def rerank_aca(S1_q, S2_q, S1_db, S2_db, k1, k2, alpha, mode, k):
+    """Re-ranked top-k with two similarity measures (the paper's default re-ranking):
+    ACA of the query and of every database shape (``aca_activation``), S' of
+    Eq. 8 between them over all N shapes, order (S' desc, S^(1) desc, id asc).
+    Returns (ids int64 [B, k], S' float64 [B, k])."""
+    S1_q = np.atleast_2d(_f64(S1_q))
+    S2_q = np.atleast_2d(_f64(S2_q))
+    F1_db, F2_db = db_memberships(S1_db, k1), db_memberships(S2_db, k1)
+    A_db = aca_db(S1_db, S2_db, k1, k2, alpha, mode)
+    B, N = S1_q.shape
+    ids = np.zeros((B, k), np.int64)
+    sp = np.zeros((B, k))
+    for b in range(B):
+        Fq = aca_activation(S1_q[b], S2_q[b], F1_db, F2_db, k1, k2, alpha, mode)
+        Sprime = np.array([contextual(Fq, A_db[p]) for p in range(N)])
+        order = np.lexsort((np.arange(N), -S1_q[b], -Sprime))[:k]
         ids[b] = order
         sp[b] = Sprime[order]
     return ids, sp

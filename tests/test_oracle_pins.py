@@ -430,3 +430,103 @@ def test_backward_identity_projection():
     assert np.allclose(dQ0, dQ1, atol=1e-14) and np.allclose(dP0, dP1, atol=1e-14)
     S0, j0 = O.match_forward(Q, off, P, None)
     assert np.allclose(S0, O.exact_scores(Q, off, P), atol=1e-14)
+
+
+# ----------------------------------------------------------------- two measures: Eqs. 9-11
+def _score_matrix(g, N, ties=False):
+    S = g.random((N, N))
+    if ties:
+        S = np.round(S, 1)
+    np.fill_diagonal(S, 1.0)  # a database shape matched with itself scores 1 (self-match)
+    return S
+
+
+def py_genmean(a, b, alpha):
+    return ((a ** alpha + b ** alpha) / 2.0) ** (1.0 / alpha)
+
+
+def py_aca(S1, S2, F1_db, F2_db, k1, k2, alpha, mode):
+    """ACA by explicit loops: sorted neighbour lists, per-coordinate sums, Eq. 9 per coordinate."""
+    N = len(S1)
+
+    def first(S, k):
+        return [i for _, i in sorted((-S[i], i) for i in range(N))[:k]]
+
+    def eq7(S):
+        F = [0.0] * N
+        for i in first(S, k1):
+            F[i] = float(S[i])
+        return F
+
+    def mean_rows(F, nbrs):
+        return [sum(F[i][j] for i in nbrs) / len(nbrs) for j in range(N)]
+
+    if mode == "none":
+        A1, A2 = eq7(S1), eq7(S2)
+    elif mode == "aug":
+        A1, A2 = mean_rows(F1_db, first(S1, k2)), mean_rows(F2_db, first(S2, k2))
+    else:
+        A1, A2 = mean_rows(F1_db, first(S2, k2)), mean_rows(F2_db, first(S1, k2))
+    return [py_genmean(a, b, alpha) for a, b in zip(A1, A2)]
+
+
+def test_generalised_mean_eq9_closed_forms():
+    a = np.array([0.0, 0.25, 0.5, 1.0, 0.9])
+    b = np.array([0.0, 0.0, 0.5, 0.04, 0.1])
+    assert np.allclose(O.aca_fuse(a, b, 1.0), (a + b) / 2, atol=1e-15)
+    assert np.allclose(O.aca_fuse(a, b, 0.5), ((np.sqrt(a) + np.sqrt(b)) / 2) ** 2, atol=1e-15)
+    assert np.allclose(O.aca_fuse(a, a, 0.5), a, atol=1e-15) and np.allclose(O.aca_fuse(b, b, 0.3), b, atol=1e-15)
+    f = O.aca_fuse(a, b, 0.5)
+    assert np.all(f >= np.minimum(a, b) - 1e-15) and np.all(f <= np.maximum(a, b) + 1e-15)
+    assert f[1] == pytest.approx(0.25 / 4)  # one activation zero: (sqrt(a)/2)^2
+
+
+@pytest.mark.parametrize("mode,alpha,k1,k2", [("none", 0.5, 4, 2), ("aug", 0.5, 5, 3), ("co", 0.5, 5, 3),
+                                              ("co", 1.0, 3, 2), ("co", 0.5, 6, 1)])
+def test_aca_matches_loops(mode, alpha, k1, k2):
+    g = np.random.default_rng(31)
+    N = 12
+    S1_db, S2_db = _score_matrix(g, N), _score_matrix(g, N)
+    S1_q, S2_q = g.random(N), g.random(N)
+    F1_db, F2_db = O.db_memberships(S1_db, k1), O.db_memberships(S2_db, k1)
+    got = O.aca_activation(S1_q, S2_q, F1_db, F2_db, k1, k2, alpha, mode)
+    ref = py_aca(list(S1_q), list(S2_q), F1_db.tolist(), F2_db.tolist(), k1, k2, alpha, mode)
+    assert np.allclose(got, ref, atol=1e-15)
+    A = O.aca_db(S1_db, S2_db, k1, k2, alpha, mode)
+    for p in (0, 7):
+        assert np.allclose(A[p], py_aca(list(S1_db[p]), list(S2_db[p]), F1_db.tolist(), F2_db.tolist(), k1, k2,
+                                        alpha, mode), atol=1e-15)
+
+
+def test_aca_reduces_to_one_measure():
+    """Equal measures make Eq. 9 the identity: ACA without augmentation is Eq. 7, co-augmentation is
+    augmentation, and with k2 = 1 a database shape's augmented activation is its own (self ranks first)."""
+    g = np.random.default_rng(32)
+    N, k1 = 15, 5
+    S_db = _score_matrix(g, N)
+    S_q = g.random((3, N))
+    F_db = O.db_memberships(S_db, k1)
+    for b in range(3):
+        assert np.allclose(O.aca_activation(S_q[b], S_q[b], F_db, F_db, k1, 4, 0.5, "none"),
+                           O.membership(S_q[b], k1), atol=1e-15)
+        assert np.allclose(O.aca_activation(S_q[b], S_q[b], F_db, F_db, k1, 4, 0.5, "co"),
+                           O.aca_activation(S_q[b], S_q[b], F_db, F_db, k1, 4, 0.5, "aug"), atol=1e-15)
+    assert np.allclose(O.aca_db(S_db, S_db, k1, 1, 0.5, "aug"), F_db, atol=1e-15)
+    ids_a, sp_a = O.rerank_aca(S_q, S_q, S_db, S_db, k1, 4, 0.5, "none", 8)
+    ids_r, sp_r = O.rerank(S_q, F_db, k1, 8)
+    assert np.array_equal(ids_a, ids_r) and np.allclose(sp_a, sp_r, atol=1e-15)
+
+
+def test_aca_inverted_route_equals_dense_eq8():
+    """ACA activations are non-negative, so Eq. 13/14 through the second inverted file give Eq. 8."""
+    g = np.random.default_rng(33)
+    N = 14
+    S1_db, S2_db = _score_matrix(g, N, ties=True), _score_matrix(g, N, ties=True)
+    A = O.aca_db(S1_db, S2_db, 4, 2, 0.5, "co")
+    assert np.all(A >= 0) and np.all((A > 0).sum(axis=1) <= 2 * 2 * 4)
+    card, entries = O.build_sif(A)
+    F1_db, F2_db = O.db_memberships(S1_db, 4), O.db_memberships(S2_db, 4)
+    Fq = O.aca_activation(g.random(N), g.random(N), F1_db, F2_db, 4, 2, 0.5, "co")
+    inv = O.sif_scores_inverted(Fq, card, entries)
+    dense = np.array([O.contextual(Fq, A[p]) for p in range(N)])
+    assert np.allclose(inv, dense, atol=1e-14)
