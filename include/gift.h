@@ -227,6 +227,49 @@ GIFT_API gift_status gift_rerank_noalloc(gift_index* index, const int32_t* cand_
                                          float* out_sprime, cudaStream_t stream);
 
 /*
+ * Re-ranking with two similarity measures (Sec. 2.4: Eqs. 9, 10, 11; the
+ * paper's default uses two CNN layers, co-augmentation and alpha = 0.5).
+ * measure1 and measure2 are indices of the same N database shapes under two
+ * feature sets, both with an S-IF of the same k1; they must outlive the
+ * gift_aca object, which reads their ranked neighbour rows N_k1(p).
+ *  - Contextual activation of a shape under measure l, by mode:
+ *      GIFT_ACA_NONE        its Eq. 7 activation F^(l) (first k1 neighbours);
+ *      GIFT_ACA_AUGMENT     Eq. 10: the mean of the Eq. 7 activations F_i^(l)
+ *                           of its first k2 neighbours i under measure l;
+ *      GIFT_ACA_CO_AUGMENT  Eq. 11: the same mean over its first k2 neighbours
+ *                           under the other measure.
+ *    The two are fused per coordinate by the generalised mean of Eq. 9 with
+ *    exponent alpha (> 0), and S' of Eq. 8 compares fused activations.
+ *  - gift_aca_build computes the fused activation of every database shape
+ *    and transposes it into a second inverted file of its own (entries in
+ *    ascending shape id; memberships uint32 fixed point round(F * 2^31);
+ *    norms uint64 in the same fixed point). 1 <= k2 <= k1; k2 * k1 <= 2048
+ *    (k1 <= 1024 without augmentation).
+ *  - gift_aca_rerank: cand_ids1/cand_scores1 and cand_ids2/cand_scores2 are
+ *    the ranked [B, n_cand] results of gift_query on measure1 and measure2
+ *    (n_cand >= k1). Output: the top-k of all N shapes by (S' desc, S^(1)
+ *    desc, id asc), S^(1) taken from the first list (-inf when absent); ids and
+ *    S' [B, topk]; device or host buffers.
+ *  - gift_aca_export copies the transposed activations (device or host
+ *    buffers; offsets [N + 1], ids and members [pairs], norms [N]); pairs from
+ *    gift_aca_pairs.
+ * Errors: EINVAL (sizes, k2, alpha, mismatched indices), EUNSUPPORTED (an
+ * index without S-IF), ESTATE (an index still being built), ENOMEM, ECUDA.
+ */
+typedef struct gift_aca gift_aca; /* opaque; owns its device memory */
+typedef enum { GIFT_ACA_NONE = 0, GIFT_ACA_AUGMENT = 1, GIFT_ACA_CO_AUGMENT = 2 } gift_aca_mode;
+GIFT_API gift_status gift_aca_build(const gift_index* measure1, const gift_index* measure2, int32_t k2,
+                                    float alpha, int32_t mode, cudaStream_t stream, gift_aca** out);
+GIFT_API gift_status gift_aca_rerank(gift_aca* aca, const int32_t* cand_ids1, const float* cand_scores1,
+                                     const int32_t* cand_ids2, const float* cand_scores2, int32_t B,
+                                     int32_t n_cand, int32_t topk, int32_t* out_ids, float* out_sprime,
+                                     cudaStream_t stream);
+GIFT_API gift_status gift_aca_pairs(const gift_aca* aca, int64_t* pairs);
+GIFT_API gift_status gift_aca_export(const gift_aca* aca, int64_t* entry_offsets, int32_t* entry_ids,
+                                     uint32_t* entry_members, uint64_t* card, cudaStream_t stream);
+GIFT_API void gift_aca_destroy(gift_aca* aca);
+
+/*
  * The quantiser alone (Sec. 2.3): out_codes[v * ma + a] is the a-th nearest
  * codeword of row v by (squared distance, index), c(x) = argmin_k ||x - b_k||^2.
  *  - feats: device float [n * D]; out_codes: device int32 [n * ma]; 1 <= ma <= 8.

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "GiftError", "load", "lib_path", "Index", "match_forward", "match_backward", "GiftMatch",
-    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF",
+    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF", "Aca",
 ]
 
 F32, BF16, FP8_E4M3 = 0, 1, 2
@@ -88,6 +88,11 @@ _SIGS = {
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
+    "gift_aca_build": (_I32, [_P, _P, _I32, ctypes.c_float, _I32, _P, ctypes.POINTER(_P)]),
+    "gift_aca_rerank": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_aca_pairs": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "gift_aca_export": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "gift_aca_destroy": (None, [_P]),
     "gift_export_fif": (_I32, [_P, _P, _P, _P, _P]),
     "gift_export_sif": (_I32, [_P, _P, _P, _P, _P, _P]),
     "gift_index_info": (_I32, [_P, ctypes.POINTER(_Info)]),
@@ -392,6 +397,64 @@ GiftMatch = _Lazy()
 
 
 # ---------------------------------------------------------------- serving
+ACA_NONE, ACA_AUGMENT, ACA_CO_AUGMENT = 0, 1, 2
+_ACA_MODES = {"none": ACA_NONE, "aug": ACA_AUGMENT, "co": ACA_CO_AUGMENT}
+
+
+class Aca:
+    """Re-ranking with two similarity measures (Eqs. 9-11) over two indices of the same shapes.
+
+    mode: "none" (Eq. 7 per measure), "aug" (Eq. 10) or "co" (Eq. 11, the paper's default);
+    the indices must stay open while this object is used.
+    """
+
+    def __init__(self, measure1: Index, measure2: Index, k2: int = 4, alpha: float = 0.5, mode="co",
+                 stream=None):
+        self.m1, self.m2 = measure1, measure2
+        self.k1, self.k2, self.alpha = measure1.sif_k1, int(k2), float(alpha)
+        self.mode = _ACA_MODES[mode] if isinstance(mode, str) else int(mode)
+        self.n_shapes = measure1.n_shapes
+        self._h = ctypes.c_void_p()
+        _check(load().gift_aca_build(measure1._h, measure2._h, self.k2, self.alpha, self.mode, _stream(stream),
+                                     ctypes.byref(self._h)))
+
+    def rerank(self, cand1, cand2, topk: int = 10, out=None, stream=None):
+        """cand1 / cand2: (ids, scores) [B, n_cand] from each measure's query; returns (ids, S') [B, topk]."""
+        import torch
+        ids1, sc1 = cand1
+        ids2, sc2 = cand2
+        B, n_cand = ids1.shape
+        if out is None:
+            dev = ids1.device if hasattr(ids1, "is_cuda") and ids1.is_cuda else torch.device("cuda")
+            out = (torch.empty((B, topk), dtype=torch.int32, device=dev),
+                   torch.empty((B, topk), dtype=torch.float32, device=dev))
+        _check(load().gift_aca_rerank(self._h, _ptr(ids1), _ptr(sc1), _ptr(ids2), _ptr(sc2), int(B), int(n_cand),
+                                      int(topk), _ptr(out[0]), _ptr(out[1]), _stream(stream)))
+        return out
+
+    def export(self):
+        """(entry_offsets [N+1], entry_ids, entry_members uint32, card uint64 [N]) as numpy arrays."""
+        n = ctypes.c_int64()
+        _check(load().gift_aca_pairs(self._h, ctypes.byref(n)))
+        off = np.empty(self.n_shapes + 1, np.int64)
+        ids = np.empty(max(1, n.value), np.int32)
+        mem = np.empty(max(1, n.value), np.uint32)
+        card = np.empty(self.n_shapes, np.uint64)
+        _check(load().gift_aca_export(self._h, _ptr(off), _ptr(ids), _ptr(mem), _ptr(card), _stream()))
+        return off, ids[:n.value], mem[:n.value], card
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().gift_aca_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Request loop over a resident index (gift_server_*): continuous batching of
     queries with mixed view counts, memory-based admission, p50/p99 latency."""

@@ -623,8 +623,8 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
     ix->sif_ids = ix->alloc<int32_t>((size_t)N * p.sif_k1);
     ix->sif_mem = ix->alloc<uint32_t>((size_t)N * p.sif_k1);
     ix->sif_card = ix->alloc<uint64_t>(N);
-    int32_t* nbr_ids = sc.get<int32_t>((size_t)N * p.sif_k1);
-    float* nbr_sc = sc.get<float>((size_t)N * p.sif_k1);
+    int32_t* nbr_ids = ix->row_ids = ix->alloc<int32_t>((size_t)N * p.sif_k1);
+    float* nbr_sc = ix->row_sc = ix->alloc<float>((size_t)N * p.sif_k1);
     // batches of database shapes, bounded by the dense score block
     const int64_t per = std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)1 << 26) / std::max(1, N)));
     const int topk = p.rescore_r > 0 ? std::min(p.sif_k1, p.rescore_r) : p.sif_k1;
@@ -749,8 +749,8 @@ void stream_add(Index& ix, int pass, const float* feats, int32_t first, int32_t 
       Scratch bsc(s);
       StageTimer none(nullptr, s);
       const int64_t shape0 = first + b0;
-      run_fif(ix, x + b0 * Nv * (int64_t)D, (int64_t)nb * Nv, h, nb, topk, ix.sb->nbr_ids + shape0 * k1,
-              ix.sb->nbr_sc + shape0 * k1, bsc, s, none, nullptr);
+      run_fif(ix, x + b0 * Nv * (int64_t)D, (int64_t)nb * Nv, h, nb, topk, ix.row_ids + shape0 * k1,
+              ix.row_sc + shape0 * k1, bsc, s, none, nullptr);
     }
   }
   GIFT_CUDA(cudaStreamSynchronize(s));  // the chunk buffer may be reused by the caller
@@ -796,8 +796,8 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
       const int64_t n = (int64_t)ix.prm.n_shapes * ix.prm.sif_k1;
       GIFT_CUDA(cudaFree(ix.sb->pos));
       ix.sb->pos = nullptr;
-      GIFT_CUDA(cudaMalloc(&ix.sb->nbr_ids, n * sizeof(int32_t)));
-      GIFT_CUDA(cudaMalloc(&ix.sb->nbr_sc, n * sizeof(float)));
+      ix.row_ids = ix.alloc<int32_t>(n);
+      ix.row_sc = ix.alloc<float>(n);
       ix.sb->stage = 3;
     } else {
       ix.sb->stage = 4;
@@ -810,7 +810,7 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
     ix.sif_ids = ix.alloc<int32_t>(n);
     ix.sif_mem = ix.alloc<uint32_t>(n);
     ix.sif_card = ix.alloc<uint64_t>(ix.prm.n_shapes);
-    sif_build(ix, ix.sb->nbr_ids, ix.sb->nbr_sc, sc, s);
+    sif_build(ix, ix.row_ids, ix.row_sc, sc, s);
     ix.sb->stage = 4;
   }
   GIFT_CUDA(cudaStreamSynchronize(s));
@@ -940,6 +940,91 @@ gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, const float*
     ix.stats_valid = false;
     tm.finish();
   });
+}
+
+gift_status gift_aca_build(const gift_index* measure1, const gift_index* measure2, int32_t k2, float alpha,
+                           int32_t mode, cudaStream_t stream, gift_aca** out) {
+  return gift::guard("gift_aca_build", [&] {
+    GIFT_REQUIRE(measure1 && measure2 && out, "NULL argument");
+    const Index& a = *reinterpret_cast<const Index*>(measure1);
+    const Index& b = *reinterpret_cast<const Index*>(measure2);
+    if (!a.ready() || !b.ready()) gift::fail(GIFT_ESTATE, "the streamed build of an index is not complete");
+    if (!a.sif_off || !b.sif_off || !a.row_ids || !b.row_ids)
+      gift::fail(GIFT_EUNSUPPORTED, "both indices need an S-IF (sif_k1 > 0)");
+    GIFT_REQUIRE(a.prm.n_shapes == b.prm.n_shapes, "the two indices must hold the same number of shapes");
+    GIFT_REQUIRE(a.k1 == b.k1, "the two indices must have the same k1");
+    GIFT_REQUIRE(mode >= GIFT_ACA_NONE && mode <= GIFT_ACA_CO_AUGMENT, "unknown mode");
+    GIFT_REQUIRE(alpha > 0.f && alpha <= 16.f, "alpha must be in (0, 16]");
+    GIFT_REQUIRE(mode == GIFT_ACA_NONE || (k2 >= 1 && k2 <= a.k1 && k2 * a.k1 <= 2048),
+                 "need 1 <= k2 <= k1 and k2 * k1 <= 2048");
+    GIFT_REQUIRE(mode != GIFT_ACA_NONE || a.k1 <= 1024, "k1 must be <= 1024");
+    int dev = 0;
+    GIFT_CUDA(cudaGetDevice(&dev));
+    std::unique_ptr<gift::Aca> x(new gift::Aca());
+    x->m[0] = &a;
+    x->m[1] = &b;
+    x->N = a.prm.n_shapes;
+    x->k1 = a.k1;
+    x->k2 = mode == GIFT_ACA_NONE ? 1 : k2;
+    x->mode = mode;
+    x->alpha = alpha;
+    x->device = dev;
+    gift::Scratch sc(stream);
+    gift::aca_build(*x, sc, stream);
+    *out = reinterpret_cast<gift_aca*>(x.release());
+  });
+}
+
+gift_status gift_aca_rerank(gift_aca* aca, const int32_t* cand_ids1, const float* cand_scores1,
+                            const int32_t* cand_ids2, const float* cand_scores2, int32_t B, int32_t n_cand,
+                            int32_t topk, int32_t* out_ids, float* out_sprime, cudaStream_t stream) {
+  return gift::guard("gift_aca_rerank", [&] {
+    GIFT_REQUIRE(aca && cand_ids1 && cand_scores1 && cand_ids2 && cand_scores2 && out_ids && out_sprime,
+                 "NULL argument");
+    const gift::Aca& x = *reinterpret_cast<const gift::Aca*>(aca);
+    GIFT_REQUIRE(B > 0 && n_cand >= x.k1, "need B > 0 and n_cand >= k1");
+    GIFT_REQUIRE(topk > 0 && topk <= 1024, "topk must be in [1, 1024]");
+    gift::Scratch sc(stream);
+    std::vector<gift::OutBuf> outs;
+    const size_t nc = (size_t)B * n_cand;
+    const int32_t* c1 = gift::stage_in(cand_ids1, nc, sc, stream);
+    const float* s1 = gift::stage_in(cand_scores1, nc, sc, stream);
+    const int32_t* c2 = gift::stage_in(cand_ids2, nc, sc, stream);
+    const float* s2 = gift::stage_in(cand_scores2, nc, sc, stream);
+    int32_t* oid = gift::stage_out(out_ids, (size_t)B * topk, sc, outs);
+    float* osp = gift::stage_out(out_sprime, (size_t)B * topk, sc, outs);
+    gift::aca_rerank(x, c1, s1, c2, s2, B, n_cand, topk, oid, osp, sc, stream);
+    gift::flush_out(outs, stream);
+  });
+}
+
+gift_status gift_aca_pairs(const gift_aca* aca, int64_t* pairs) {
+  return gift::guard("gift_aca_pairs", [&] {
+    GIFT_REQUIRE(aca && pairs, "NULL argument");
+    *pairs = reinterpret_cast<const gift::Aca*>(aca)->pairs;
+  });
+}
+
+gift_status gift_aca_export(const gift_aca* aca, int64_t* entry_offsets, int32_t* entry_ids,
+                            uint32_t* entry_members, uint64_t* card, cudaStream_t stream) {
+  return gift::guard("gift_aca_export", [&] {
+    GIFT_REQUIRE(aca, "NULL argument");
+    const gift::Aca& x = *reinterpret_cast<const gift::Aca*>(aca);
+    if (entry_offsets)
+      GIFT_CUDA(cudaMemcpyAsync(entry_offsets, x.off, ((size_t)x.N + 1) * 8, cudaMemcpyDefault, stream));
+    if (entry_ids && x.pairs)
+      GIFT_CUDA(cudaMemcpyAsync(entry_ids, x.ids, (size_t)x.pairs * 4, cudaMemcpyDefault, stream));
+    if (entry_members && x.pairs)
+      GIFT_CUDA(cudaMemcpyAsync(entry_members, x.mem, (size_t)x.pairs * 4, cudaMemcpyDefault, stream));
+    if (card) GIFT_CUDA(cudaMemcpyAsync(card, x.card, (size_t)x.N * 8, cudaMemcpyDefault, stream));
+    GIFT_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+void gift_aca_destroy(gift_aca* aca) {
+  if (!aca) return;
+  cudaDeviceSynchronize();
+  delete reinterpret_cast<gift::Aca*>(aca);
 }
 
 gift_status gift_assign(gift_index* index, const float* feats, int64_t n, int32_t ma, int32_t* out_codes,

@@ -71,13 +71,7 @@ struct StreamBuild {
   int64_t rows_added = 0;      // rows added in the current pass
   std::vector<uint8_t> seen;   // [N] shapes added in the current pass
   int32_t* pos = nullptr;      // [n_rows] list position of each database row (pass 2)
-  int32_t* nbr_ids = nullptr;  // [N * k1] neighbours of every database shape (pass 3)
-  float* nbr_sc = nullptr;
-  ~StreamBuild() {  // the pass buffers are freed once the build completes
-    cudaFree(pos);
-    cudaFree(nbr_ids);
-    cudaFree(nbr_sc);
-  }
+  ~StreamBuild() { cudaFree(pos); }  // freed once the build completes
 };
 
 struct Index {
@@ -131,6 +125,8 @@ struct Index {
   uint32_t* sif_mem = nullptr;   // [N*k1]
   uint64_t* sif_card = nullptr;  // [N]
   int32_t max_sif_entry = 0;
+  int32_t* row_ids = nullptr;    // [N*k1] N_k1(p) of every database shape, ranked (score desc, id asc)
+  float* row_sc = nullptr;       // [N*k1] their scores S(x_p, x_i): the rows of F_p (Eq. 7)
 
   int* d_err = nullptr;          // device error flag set by bounded waits (0 = none)
   StreamBuild* sb = nullptr;     // non-null while a streamed build is in progress
@@ -215,6 +211,31 @@ size_t sif_rerank_scratch_bytes(int32_t B, int32_t N, int32_t topk);
 void sif_rerank_into(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B, int32_t n_cand,
                      int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, void* scratch,
                      size_t scratch_bytes, cudaStream_t s);
+
+// Two-measure contextual re-ranking (Sec. 2.4: Eqs. 9-11) over two indices of
+// the same database shapes: the aggregated contextual activation of every
+// database shape, transposed into its own second inverted file.
+struct Aca {
+  const Index* m[2] = {nullptr, nullptr};
+  int32_t N = 0;
+  int k1 = 0, k2 = 0, mode = 0, cap = 0;
+  float alpha = 0.5f;
+  int device = 0;
+  int64_t* off = nullptr;              // [N+1]
+  int32_t* ids = nullptr;              // [pairs] shapes p of entry i, ascending
+  uint32_t* mem = nullptr;             // [pairs] round(F_p[i] * 2^31)
+  unsigned long long* card = nullptr;  // [N] ||F_p||_1 in the same fixed point
+  int64_t pairs = 0;
+  int32_t max_entry = 0;
+  std::vector<void*> owned;
+  size_t device_bytes = 0;
+  template <class T> T* alloc(size_t n);
+  ~Aca();
+};
+void aca_build(Aca& a, Scratch& sc, cudaStream_t s);
+void aca_rerank(const Aca& a, const int32_t* cand1, const float* sc1, const int32_t* cand2, const float* sc2,
+                int32_t B, int32_t n_cand, int32_t topk, int32_t* out_ids, float* out_sprime, Scratch& sc,
+                cudaStream_t s);
 
 // k_match.cu (dtype: GIFT_F32 or GIFT_BF16 for q, p and W)
 void match_forward(const void* q, const std::vector<int32_t>& h_qoff, int32_t Bq, const void* p, int32_t Np,
