@@ -280,6 +280,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving session length (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
+    ap.add_argument("--no-aca", action="store_true", help="skip the two-measure re-rank measurement")
     ap.add_argument("--rescore", type=int, default=None, help="override the config's rescore depth R")
     ap.add_argument("--oracle-queries", type=int, default=4, help="sampled queries for recall (large configs)")
     args = ap.parse_args()
@@ -570,6 +571,12 @@ def main():
                    "result": "top-100 after S-IF re-rank"}
         log(f"[bench] serving: {serving}")
 
+    # ---- two similarity measures (Eqs. 9-11): second index, fused activations, re-rank
+    aca = None
+    if not args.no_aca and rank == 0 and not large and cfg.sif_k1 > 0:
+        aca = bench_aca(cfg, gift, torch, dev, stream, ix, batches, topk, R)
+        log(f"[bench] two-measure re-rank: {aca}")
+
     # ---- differentiation: projected match forward + backward at its own workload
     diff = None
     if not args.no_diff and rank == 0 and not large:
@@ -601,6 +608,7 @@ def main():
         "build_s": build_s,
         "serving": serving,
         "differentiation": diff,
+        "two_measure_rerank": aca,
     }
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)
@@ -683,6 +691,58 @@ def main():
     ix.close()
     if rank == 0:
         print(json.dumps(line))
+
+
+def bench_aca(cfg, gift, torch, dev, stream, ix1, batches, topk, R, reps=5):
+    """The paper's default re-ranking: a second measure's index (synthetic stand-in for a
+    second CNN layer), co-augmented activations (Eq. 11, k2 = 4) fused by Eq. 9 (alpha = 0.5),
+    S' through their own inverted file. Step = query on both indices + the fused re-rank."""
+    from synth import make_config_inputs, second_measure
+    c2 = second_measure(cfg)
+    t0 = time.time()
+    d2 = make_config_inputs(c2)
+    ix2 = gift.Index(torch.from_numpy(d2["db"]).to(dev), torch.from_numpy(d2["codebook"]).to(dev), c2.n_shapes,
+                     c2.n_views, c2.n_codewords, storage=c2.storage, query_ma=c2.query_ma, sif_k1=c2.sif_k1,
+                     rescore_r=R, keep_exact=False)
+    torch.cuda.synchronize()
+    t_ix2 = time.time() - t0
+    t0 = time.time()
+    aca = gift.Aca(ix1, ix2, k2=4, alpha=0.5, mode="co")
+    torch.cuda.synchronize()
+    t_aca = time.time() - t0
+    pairs = int(aca.export()[0][-1])
+    q2 = torch.from_numpy(d2["q"]).to(dev)
+    B = batches[0][1].shape[0] - 1
+    qoff2 = np.asarray(d2["q_off"], np.int64)
+    b2 = [(q2[qoff2[i * B]:qoff2[(i + 1) * B]], (qoff2[i * B:(i + 1) * B + 1] - qoff2[i * B]).astype(np.int32))
+          for i in range((len(qoff2) - 1) // B)]
+    nb = min(len(batches), len(b2))
+
+    def step(i):
+        c1 = ix1.query(*batches[i % nb], mode="fif", topk=topk)
+        c2_ = ix2.query(*b2[i % nb], mode="fif", topk=topk)
+        e[1].record(stream)
+        return aca.rerank(c1, c2_, topk=topk)
+
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    step(0)
+    torch.cuda.synchronize()
+    tot, rr = [], []
+    for i in range(reps):
+        e[0].record(stream)
+        step(i)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        tot.append(e[0].elapsed_time(e[2]))
+        rr.append(e[1].elapsed_time(e[2]))
+    aca.close()
+    ix2.close()
+    del q2
+    torch.cuda.empty_cache()
+    t_ms, r_ms = statistics.median(tot), statistics.median(rr)
+    return {"measure2": c2.name, "k1": cfg.sif_k1, "k2": 4, "alpha": 0.5, "mode": "co-augmentation (Eq. 11)",
+            "queries_per_step": B, "step_ms": t_ms, "queries_per_s": B / (t_ms / 1e3), "fused_rerank_ms": r_ms,
+            "fused_sif_pairs": pairs, "build_index2_s": t_ix2, "build_fused_sif_s": t_aca}
 
 
 def bench_differentiation(gift, torch, dev, stream, reps=3):

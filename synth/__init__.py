@@ -14,6 +14,7 @@ from .workload import (  # noqa: F401
     make_config_inputs,
     config_views,
     config_codebook,
+    second_measure,
     projection_matrix,
     upstream_grad,
     DIFF_WORKLOAD,

@@ -99,6 +99,15 @@ CONFIGS = {
 }
 
 
+def second_measure(cfg: Config) -> Config:
+    """A second feature set of the same shapes, standing in for the paper's second CNN layer
+    (Sec. 3 uses two layers): same shapes, views and classes, half the dimension, its own
+    centres, noise, queries and codebook (seeds shifted by 50)."""
+    import dataclasses
+    return dataclasses.replace(cfg, name=cfg.name + "_m2", dim=max(16, cfg.dim // 2), seed=cfg.seed + 50,
+                               query_views=(cfg.n_views,))
+
+
 def _gen(seed: int, block: int) -> np.random.Generator:
     return np.random.default_rng([int(seed), int(block)])
 
