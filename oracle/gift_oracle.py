@@ -10,6 +10,7 @@ as library steps. What each function computes, with the passage it follows:
 * ``cosine``               s(a, b), the cosine similarity used in Eq. 3 (Sec. 2.3)
 * ``quantize``             c(x) = argmin_k ||x - b_k||^2 (Sec. 2.3, after Eq. 4),
                            with multiple assignment (Sec. 2.3, last paragraph)
+* ``kmeans_lloyd``         the off-line vocabulary: Lloyd's k-means (Sec. 2.3)
 * ``build_fif``            the first inverted file (Sec. 2.3, Fig. 2)
 * ``exact_scores``         S(x_q, x_p), Eq. 3
 * ``fif_scores``           the approximate match of Eq. 4, literally (Kronecker delta)
@@ -100,6 +101,36 @@ def quantize(X, codebook, ma=1):
         # a stable sort on distance puts equal distances in index order
         out[lo:lo + _CHUNK_ROWS] = np.argsort(d, axis=1, kind="stable")[:, :ma]
     return out
+
+
+def kmeans_lloyd(X, init_rows, iters):
+    """Lloyd's k-means for the vocabulary B of Sec. 2.3 (trained off-line with
+    k-means; the paper gives no details), float64 [K, D].
+
+    Starts from the rows ``init_rows``; each iteration assigns every row to its
+    nearest centre (``quantize``: ties to the lowest index) and moves each centre
+    to the mean of its rows. A centre left without rows takes the row farthest
+    from the centre it was assigned to in that iteration (rows by distance
+    desc, index asc), the empty centres served in ascending order.
+    """
+    X = _f64(X)
+    C = X[np.asarray(init_rows, np.int64)].copy()
+    K = C.shape[0]
+    for _ in range(iters):
+        lab = quantize(X, C, 1)[:, 0]
+        d = ((X - C[lab]) ** 2).sum(axis=1)
+        far = np.lexsort((np.arange(X.shape[0]), -d))
+        fi = 0
+        newC = C.copy()
+        for c in range(K):
+            rows = np.nonzero(lab == c)[0]
+            if len(rows):
+                newC[c] = X[rows].sum(axis=0) / len(rows)
+            else:
+                newC[c] = X[far[fi]]
+                fi += 1
+        C = newC
+    return C
 
 
 def build_fif(db_codes, n_codewords):

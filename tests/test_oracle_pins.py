@@ -530,3 +530,53 @@ def test_aca_inverted_route_equals_dense_eq8():
     inv = O.sif_scores_inverted(Fq, card, entries)
     dense = np.array([O.contextual(Fq, A[p]) for p in range(N)])
     assert np.allclose(inv, dense, atol=1e-14)
+
+
+# ----------------------------------------------------------------- k-means vocabulary
+def py_lloyd(X, init, iters):
+    X = [list(map(float, r)) for r in X]
+    C = [list(X[i]) for i in init]
+    for _ in range(iters):
+        lab, dist = [], []
+        for x in X:
+            ds = [(sum((a - b) ** 2 for a, b in zip(x, c)), k) for k, c in enumerate(C)]
+            d, k = min(ds)
+            lab.append(k)
+            dist.append(d)
+        far = [i for _, i in sorted((-d, i) for i, d in enumerate(dist))]
+        fi, newC = 0, []
+        for c in range(len(C)):
+            rows = [i for i, l in enumerate(lab) if l == c]
+            if rows:
+                newC.append([sum(X[i][d] for i in rows) / len(rows) for d in range(len(X[0]))])
+            else:
+                newC.append(list(X[far[fi]]))
+                fi += 1
+        C = newC
+    return np.array(C)
+
+
+def test_lloyd_matches_loops_and_reseeds_empty_centres():
+    g = np.random.default_rng(41)
+    X = g.standard_normal((40, 3))
+    assert np.allclose(O.kmeans_lloyd(X, [0, 5, 9, 13], 4), py_lloyd(X, [0, 5, 9, 13], 4), atol=1e-12)
+    # a duplicated initial centre leaves the second copy empty: it takes the farthest row
+    Y = np.array([[0.0, 0], [0, 1], [10, 0], [10, 1], [50, 50]])
+    C = O.kmeans_lloyd(Y, [0, 0, 2], 1)
+    assert np.allclose(C, py_lloyd(Y, [0, 0, 2], 1))
+    assert np.allclose(C[1], [50, 50]) and np.allclose(C[0], [0, 0.5])
+
+
+def test_lloyd_separated_blobs_and_monotone_objective():
+    g = np.random.default_rng(42)
+    centres = np.array([[0.0, 0, 0], [20, 0, 0], [0, 20, 0]])
+    X = np.concatenate([c + g.standard_normal((30, 3)) for c in centres])
+    C = O.kmeans_lloyd(X, [0, 30, 60], 3)
+    for b in range(3):
+        assert np.allclose(C[b], X[30 * b:30 * (b + 1)].mean(axis=0), atol=1e-12)
+    obj = []
+    for it in range(5):
+        Ck = O.kmeans_lloyd(X, [0, 1, 2], it)
+        lab = O.quantize(X, Ck, 1)[:, 0]
+        obj.append(((X - Ck[lab]) ** 2).sum())
+    assert all(b <= a + 1e-9 for a, b in zip(obj, obj[1:]))
