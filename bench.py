@@ -281,6 +281,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     ap.add_argument("--no-aca", action="store_true", help="skip the two-measure re-rank measurement")
+    ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU k-means measurement")
     ap.add_argument("--rescore", type=int, default=None, help="override the config's rescore depth R")
     ap.add_argument("--oracle-queries", type=int, default=4, help="sampled queries for recall (large configs)")
     args = ap.parse_args()
@@ -577,6 +578,12 @@ def main():
         aca = bench_aca(cfg, gift, torch, dev, stream, ix, batches, topk, R)
         log(f"[bench] two-measure re-rank: {aca}")
 
+    # ---- the off-line vocabulary: Lloyd's k-means on the GPU at the fixture's size
+    km = None
+    if not args.no_kmeans and rank == 0 and not large:
+        km = bench_kmeans(cfg, gift, torch, dev, stream, data)
+        log(f"[bench] k-means: {km}")
+
     # ---- differentiation: projected match forward + backward at its own workload
     diff = None
     if not args.no_diff and rank == 0 and not large:
@@ -609,6 +616,7 @@ def main():
         "serving": serving,
         "differentiation": diff,
         "two_measure_rerank": aca,
+        "kmeans": km,
     }
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)
@@ -743,6 +751,31 @@ def bench_aca(cfg, gift, torch, dev, stream, ix1, batches, topk, R, reps=5):
     return {"measure2": c2.name, "k1": cfg.sif_k1, "k2": 4, "alpha": 0.5, "mode": "co-augmentation (Eq. 11)",
             "queries_per_step": B, "step_ms": t_ms, "queries_per_s": B / (t_ms / 1e3), "fused_rerank_ms": r_ms,
             "fused_sif_pairs": pairs, "build_index2_s": t_ix2, "build_fused_sif_s": t_aca}
+
+
+def bench_kmeans(cfg, gift, torch, dev, stream, data):
+    """GPU Lloyd k-means on the codebook fixture's sample (its rows, K, iterations and initial rows),
+    device-timed; the host fixture (numpy, FP32 distances) is timed on one iteration for context."""
+    from synth import codebook_sample_shapes, kmeans_init_rows, kmeans_codebook
+    X = np.ascontiguousarray(data["db"][codebook_sample_shapes(cfg)].reshape(-1, cfg.dim))
+    init = kmeans_init_rows(len(X), cfg.n_codewords, cfg.codebook_seed)
+    Xd = torch.from_numpy(X).to(dev)
+    gift.kmeans(Xd, init, iters=1)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    gift.kmeans(Xd, init, iters=cfg.kmeans_iters)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1])
+    t0 = time.time()
+    kmeans_codebook(X, cfg.n_codewords, cfg.codebook_seed, 1)
+    host_it = time.time() - t0
+    del Xd
+    torch.cuda.empty_cache()
+    return {"rows": len(X), "dim": cfg.dim, "K": cfg.n_codewords, "iters": cfg.kmeans_iters, "gpu_ms": ms,
+            "gpu_ms_per_iter": ms / max(1, cfg.kmeans_iters), "host_fixture_s_per_iter": host_it,
+            "note": "exact assignment (tensor-core quantiser) + float64 means; the host fixture uses FP32 distances"}
 
 
 def bench_differentiation(gift, torch, dev, stream, reps=3):

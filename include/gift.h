@@ -270,6 +270,22 @@ GIFT_API gift_status gift_aca_export(const gift_aca* aca, int64_t* entry_offsets
 GIFT_API void gift_aca_destroy(gift_aca* aca);
 
 /*
+ * Lloyd's k-means on the GPU: the off-line vocabulary B of Sec. 2.3 (the paper
+ * trains it with k-means and gives no details).
+ *  - X: device or host float [n * D] (D a multiple of 16); init_rows: host
+ *    int32 [K], the rows that start as centres; iters >= 0 iterations.
+ *  - Each iteration assigns every row to its nearest centre exactly as
+ *    gift_assign does (ties to the lowest index) and moves every centre to the
+ *    mean of its rows (float64 sums in ascending row order: deterministic); a
+ *    centre left without rows takes the row farthest from the centre it was
+ *    assigned to (distance desc, index asc), empty centres in ascending order.
+ *  - codebook: device or host float [K * D], written when the call returns.
+ * Errors: EINVAL (sizes, rows out of range), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_kmeans(const float* X, int64_t n, int32_t D, int32_t K, const int32_t* init_rows,
+                                 int32_t iters, float* codebook, cudaStream_t stream);
+
+/*
  * The quantiser alone (Sec. 2.3): out_codes[v * ma + a] is the a-th nearest
  * codeword of row v by (squared distance, index), c(x) = argmin_k ||x - b_k||^2.
  *  - feats: device float [n * D]; out_codes: device int32 [n * ma]; 1 <= ma <= 8.

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "GiftError", "load", "lib_path", "Index", "match_forward", "match_backward", "GiftMatch",
-    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF", "Aca",
+    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF", "Aca", "kmeans",
 ]
 
 F32, BF16, FP8_E4M3 = 0, 1, 2
@@ -88,6 +88,7 @@ _SIGS = {
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
+    "gift_kmeans": (_I32, [_P, _I64, _I32, _I32, _P, _I32, _P, _P]),
     "gift_aca_build": (_I32, [_P, _P, _I32, ctypes.c_float, _I32, _P, ctypes.POINTER(_P)]),
     "gift_aca_rerank": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "gift_aca_pairs": (_I32, [_P, ctypes.POINTER(_I64)]),
@@ -397,6 +398,23 @@ GiftMatch = _Lazy()
 
 
 # ---------------------------------------------------------------- serving
+def kmeans(X, init_rows, iters: int, out=None, stream=None):
+    """Lloyd's k-means on the GPU (the off-line vocabulary): centres float32 [K, D].
+
+    X: float32 [n, D] (device tensor or host array); init_rows: the K rows that start as centres.
+    """
+    import torch
+    init = np.ascontiguousarray(np.asarray(init_rows, np.int32))
+    n, D = int(X.shape[0]), int(X.shape[1])
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+    K = len(init)
+    if out is None:
+        out = torch.empty((K, D), dtype=torch.float32, device="cuda")
+    _check(load().gift_kmeans(_ptr(X), n, D, K, _ptr(init), int(iters), _ptr(out), _stream(stream)))
+    return out
+
+
 ACA_NONE, ACA_AUGMENT, ACA_CO_AUGMENT = 0, 1, 2
 _ACA_MODES = {"none": ACA_NONE, "aug": ACA_AUGMENT, "co": ACA_CO_AUGMENT}
 

@@ -33,6 +33,7 @@ SOURCES = [
     "k_noalloc.cu",
     "serve.cu",
     "tc_gemm.cu",
+    "k_kmeans.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

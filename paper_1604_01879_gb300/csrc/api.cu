@@ -214,6 +214,31 @@ __global__ void k_cb_maxnorm(const float* __restrict__ half_sq, int K, float* __
   }
 }
 
+}  // namespace
+
+void prepare_codebook(Index& ix, cudaStream_t s) {
+  const int K = ix.prm.n_codewords, D = ix.prm.dim;
+  if (!ix.cb_half_sq) {
+    ix.cb_half_sq = ix.alloc<float>(K);
+    ix.cb_rows_alloc = (int64_t)K + 256;  // one TMA box of padding rows
+    ix.cb_hi = ix.alloc<__nv_bfloat16>((size_t)ix.cb_rows_alloc * D);
+    ix.cb_lo = ix.alloc<__nv_bfloat16>((size_t)ix.cb_rows_alloc * D);
+    GIFT_CUDA(cudaMemsetAsync(ix.cb_hi, 0, (size_t)ix.cb_rows_alloc * D * 2, s));
+    GIFT_CUDA(cudaMemsetAsync(ix.cb_lo, 0, (size_t)ix.cb_rows_alloc * D * 2, s));
+  }
+  launch_half_sq_norm(ix.codebook, K, D, ix.cb_half_sq, s);
+  split_rows_bf16(ix.codebook, K, D, ix.cb_hi, ix.cb_lo, s);
+  Scratch sc(s);
+  float* d_cbmax = sc.get<float>(1);
+  k_cb_maxnorm<<<1, 1024, 0, s>>>(ix.cb_half_sq, K, d_cbmax);
+  GIFT_LAUNCHED("k_cb_maxnorm");
+  GIFT_CUDA(cudaMemcpyAsync(&ix.cb_max_norm, d_cbmax, 4, cudaMemcpyDeviceToHost, s));
+  GIFT_CUDA(cudaStreamSynchronize(s));
+  ix.cb_max_norm *= 1.0001f;
+}
+
+namespace {
+
 // list position of every database row: pos[list_row[e]] = e
 __global__ void k_list_pos(const int32_t* __restrict__ list_row, int64_t n, int32_t* __restrict__ pos) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -939,6 +964,21 @@ gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, const float*
     gift::flush_out(outs, stream);
     ix.stats_valid = false;
     tm.finish();
+  });
+}
+
+gift_status gift_kmeans(const float* X, int64_t n, int32_t D, int32_t K, const int32_t* init_rows, int32_t iters,
+                        float* codebook, cudaStream_t stream) {
+  return gift::guard("gift_kmeans", [&] {
+    GIFT_REQUIRE(X && init_rows && codebook, "NULL argument");
+    GIFT_REQUIRE(D > 0 && D % 16 == 0, "D must be a positive multiple of 16");
+    GIFT_REQUIRE(K >= 1 && n >= K && n < (int64_t)INT32_MAX, "need 1 <= K <= n < 2^31");
+    GIFT_REQUIRE(iters >= 0, "iters must be >= 0");
+    std::vector<int32_t> init(init_rows, init_rows + K);
+    for (int32_t r : init) GIFT_REQUIRE(r >= 0 && r < n, "an initial row is out of range");
+    gift::Scratch sc(stream);
+    const float* x = gift::stage_in(X, (size_t)n * D, sc, stream);
+    gift::kmeans(x, n, D, K, init, iters, codebook, sc, stream);
   });
 }
 

@@ -176,6 +176,14 @@ void assign_codes(const Index& ix, const float* X, int64_t n, int ma, int32_t* c
 // hi = bf16(x), lo = bf16(x - hi) of a row-major [n, D] FP32 matrix
 void split_rows_bf16(const float* X, int64_t n, int D, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 
+// api.cu: the quantiser's derived codebook arrays (||b||^2 / 2, two-part BF16
+// rows padded by one TMA box, max ||b||) from ix.codebook; allocates them on first use
+void prepare_codebook(Index& ix, cudaStream_t s);
+
+// k_kmeans.cu: Lloyd's k-means from the rows init_rows; C_out [K, D] (device or host)
+void kmeans(const float* X, int64_t n, int D, int K, const std::vector<int32_t>& init_rows, int iters, float* C_out,
+            Scratch& sc, cudaStream_t s);
+
 // k_exact_tc.cu: Eq. 3 over all N shapes on the tensor cores
 void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
                      const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);

@@ -11,9 +11,11 @@ from .workload import (  # noqa: F401
     shape_views,
     query_views,
     kmeans_codebook,
+    kmeans_init_rows,
     make_config_inputs,
     config_views,
     config_codebook,
+    codebook_sample_shapes,
     second_measure,
     projection_matrix,
     upstream_grad,

@@ -216,6 +216,11 @@ def query_views(n_queries: int, view_choices, dim: int, n_classes: int,
     return flat, offs.astype(np.int32), classes
 
 
+def kmeans_init_rows(n: int, k: int, seed: int) -> np.ndarray:
+    """The fixture's initial centres: a seeded choice of k distinct rows of n, ascending (int32 [k])."""
+    return np.sort(_gen(seed, 0).choice(n, size=k, replace=False)).astype(np.int32)
+
+
 def kmeans_codebook(sample: np.ndarray, k: int, seed: int, iters: int) -> np.ndarray:
     """Seeded Lloyd k-means fixture on ``sample`` (float [n, D]) -> float32 [k, D].
 
@@ -227,8 +232,7 @@ def kmeans_codebook(sample: np.ndarray, k: int, seed: int, iters: int) -> np.nda
     n = X.shape[0]
     if k > n:
         raise ValueError("k-means needs at least k sample points")
-    g = _gen(seed, 0)
-    C = X[np.sort(g.choice(n, size=k, replace=False))].copy()
+    C = X[kmeans_init_rows(n, k, seed)].copy()
     X32 = X.astype(np.float32)
     xx = (X * X).sum(1)
     for _ in range(iters):
@@ -288,13 +292,17 @@ def make_config_inputs(cfg: Config, with_db: bool = True, n_queries: int | None 
     return dict(db=db, codebook=codebook, q=q, q_off=q_off, q_class=q_cls)
 
 
-def config_codebook(cfg: Config, db=None) -> np.ndarray:
-    """The codebook fixture of a config: seeded k-means on a seeded sample of its database shapes."""
+def codebook_sample_shapes(cfg: Config) -> np.ndarray:
+    """The database shapes whose views train the codebook fixture (seeded, ascending)."""
     ks = cfg.kmeans_shapes or cfg.n_shapes
     if ks >= cfg.n_shapes:
-        sample_shapes = np.arange(cfg.n_shapes)
-    else:
-        sample_shapes = np.sort(_gen(cfg.codebook_seed, 1).choice(cfg.n_shapes, ks, replace=False))
+        return np.arange(cfg.n_shapes)
+    return np.sort(_gen(cfg.codebook_seed, 1).choice(cfg.n_shapes, ks, replace=False))
+
+
+def config_codebook(cfg: Config, db=None) -> np.ndarray:
+    """The codebook fixture of a config: seeded k-means on a seeded sample of its database shapes."""
+    sample_shapes = codebook_sample_shapes(cfg)
     if db is not None:
         sample = db[sample_shapes].reshape(-1, cfg.dim)
     elif cfg.generator == "counter":
