@@ -134,18 +134,21 @@ def kmeans_lloyd(X, init_rows, iters):
 
 
 def build_fif(db_codes, n_codewords):
-    """First inverted file (Fig. 2): list k holds every (shape, view) whose code is k.
+    """First inverted file (Fig. 2): list k holds every (shape, view) with k among its codes.
 
-    ``db_codes`` is int [N, N_v] (one assignment per database view). Each list
-    is in ascending (shape, view) order. Returns a list of K int64 arrays of
-    shape [L_k, 2].
+    ``db_codes`` is int [N, N_v] (one assignment per database view) or
+    [N, N_v, m] (database-side multiple assignment: a view enters m lists, at
+    the memory cost Sec. 2.3 mentions). Each list is in ascending (shape, view)
+    order. Returns a list of K int64 arrays of shape [L_k, 2].
     """
     db_codes = np.asarray(db_codes)
-    N, Nv = db_codes.shape
+    N, Nv = db_codes.shape[:2]
+    codes = db_codes.reshape(N, Nv, -1)
     lists = [[] for _ in range(n_codewords)]
     for p in range(N):
         for j in range(Nv):
-            lists[int(db_codes[p, j])].append((p, j))
+            for c in codes[p, j]:
+                lists[int(c)].append((p, j))
     return [np.asarray(l, np.int64).reshape(-1, 2) for l in lists]
 
 
@@ -175,12 +178,13 @@ def fif_scores(Q, q_off, q_codes, X, db_codes):
     """Eq. 4 taken literally, float64 [B, N].
 
     S(x_q, x_p) = (1/|V(x_q)|) sum_i max_j s(q_i, p_j) * delta(c(q_i), c(p_j)),
-    where delta is 1 when c(p_j) is one of q_i's assigned codewords (multiple
-    assignment, Sec. 2.3) and 0 otherwise. The max runs over all j, so an
-    unmatched view contributes the candidate value 0.
+    where delta is 1 when q_i's assigned codewords and p_j's share a codeword
+    (multiple assignment, Sec. 2.3, on either side: ``db_codes`` is [N, N_v] or
+    [N, N_v, m]) and 0 otherwise. The max runs over all j, so an unmatched view
+    contributes the candidate value 0.
     """
     rows, N, Nv = _db_rows(X)
-    dbc = np.asarray(db_codes).reshape(N, Nv)
+    dbc = np.asarray(db_codes).reshape(N, Nv, -1)
     q_codes = np.asarray(q_codes)
     q_off = np.asarray(q_off)
     B = len(q_off) - 1
@@ -193,8 +197,8 @@ def fif_scores(Q, q_off, q_codes, X, db_codes):
         for lo in range(0, N, step):
             hi = min(N, lo + step)
             s = cosine(Qb, rows[lo * Nv:hi * Nv]).reshape(V, hi - lo, Nv)
-            # delta[i, p, j] = 1 iff c(p_j) is among q_i's codewords
-            delta = (dbc[None, lo:hi, :, None] == cb[:, None, None, :]).any(axis=3)
+            # delta[i, p, j] = 1 iff a codeword of p_j is among q_i's codewords
+            delta = (dbc[None, lo:hi, :, :, None] == cb[:, None, None, None, :]).any(axis=(3, 4))
             S[b, lo:hi] = (s * delta).max(axis=2).sum(axis=0) / V
     return S
 
@@ -205,7 +209,8 @@ def fif_scores_lists(Q, q_off, q_codes, X, lists):
     For each query view q_i, only the lists of its codewords are visited; per
     shape the max over the visited entries is taken, and 0 joins that max when
     some view of the shape was not visited (those products are 0 in Eq. 4).
-    Shapes never visited score 0 for q_i.
+    Shapes never visited score 0 for q_i. A view reached through several lists
+    (multiple assignment on both sides) counts once.
     """
     X = np.asarray(X)
     N, Nv, D = X.shape
@@ -223,12 +228,12 @@ def fif_scores_lists(Q, q_off, q_codes, X, lists):
                 if len(ent) == 0:
                     continue
                 s = cosine(Q[i:i + 1], X[ent[:, 0], ent[:, 1]])[0]
-                for (p, _j), v in zip(ent, s):
+                for (p, j), v in zip(ent, s):
                     p = int(p)
                     best[p] = max(best.get(p, -np.inf), v)
-                    seen[p] = seen.get(p, 0) + 1
+                    seen.setdefault(p, set()).add(int(j))
             for p, v in best.items():
-                if seen[p] < Nv:
+                if len(seen[p]) < Nv:
                     v = max(v, 0.0)
                 S[b, p] += v / V
     return S

@@ -48,15 +48,17 @@ def py_codes(X, Bk, ma):
 
 
 def py_fif(Q, q_off, qc, X, dbc):
-    """Eq. 4 by explicit loops: product with the Kronecker delta, max over all j."""
+    """Eq. 4 by explicit loops: product with the Kronecker delta, max over all j
+    (``dbc`` [N, N_v] or [N, N_v, m]: a database view matches through any of its codes)."""
     N, Nv, _ = X.shape
+    dbc = np.asarray(dbc).reshape(N, Nv, -1)
     out = []
     for b in range(len(q_off) - 1):
         row = []
         for p in range(N):
             tot = 0.0
             for i in range(q_off[b], q_off[b + 1]):
-                tot += max(py_cos(Q[i], X[p, j]) * (1.0 if dbc[p, j] in set(qc[i]) else 0.0)
+                tot += max(py_cos(Q[i], X[p, j]) * (1.0 if set(dbc[p, j].tolist()) & set(qc[i].tolist()) else 0.0)
                            for j in range(Nv))
             row.append(tot / (q_off[b + 1] - q_off[b]))
         out.append(row)
@@ -580,3 +582,28 @@ def test_lloyd_separated_blobs_and_monotone_objective():
         lab = O.quantize(X, Ck, 1)[:, 0]
         obj.append(((X - Ck[lab]) ** 2).sum())
     assert all(b <= a + 1e-9 for a, b in zip(obj, obj[1:]))
+
+
+# ----------------------------------------------------------------- database-side multiple assignment
+@pytest.mark.parametrize("seed,K,ma_q,ma_db", [(0, 4, 1, 2), (1, 5, 2, 2), (2, 6, 1, 3)])
+def test_database_side_multiple_assignment(seed, K, ma_q, ma_db):
+    Q, off, X = rand_case(seed, N=6, Nv=5, D=4)
+    Bk = np.random.default_rng(200 + seed).standard_normal((K, 4))
+    dbc = O.quantize(X.reshape(-1, 4), Bk, ma_db).reshape(6, 5, ma_db)
+    qc = O.quantize(Q, Bk, ma_q)
+    lit = O.fif_scores(Q, off, qc, X, dbc)
+    assert np.allclose(lit, py_fif(Q, off, qc, X, dbc), atol=1e-13, rtol=0)
+    lists = O.build_fif(dbc, K)
+    assert sum(len(l) for l in lists) == 6 * 5 * ma_db
+    assert np.allclose(O.fif_scores_lists(Q, off, qc, X, lists), lit, atol=1e-13, rtol=0)
+    # more database assignments can only add matches
+    assert np.all(lit >= O.fif_scores(Q, off, qc, X, dbc[..., :1]) - 1e-15)
+
+
+def test_database_side_full_assignment_equals_exact():
+    """m = K on the database side: every view is in every list, so Eq. 4 is Eq. 3."""
+    Q, off, X = rand_case(9, N=5, Nv=4, D=3)
+    Bk = np.random.default_rng(10).standard_normal((3, 3))
+    dbc = O.quantize(X.reshape(-1, 3), Bk, 3).reshape(5, 4, 3)
+    assert np.allclose(O.fif_scores(Q, off, O.quantize(Q, Bk, 1), X, dbc), O.exact_scores(Q, off, X),
+                       atol=1e-14, rtol=0)
