@@ -74,6 +74,9 @@ typedef struct {
   int32_t sif_k1;          /* k1: neighbour-set size of the S-IF (Sec. 2.4); 0 = no S-IF */
   int32_t rescore_r;       /* FP32 rescore of the top-R F-IF candidates; 0 = off */
   int32_t keep_exact;      /* 1 = keep the FP32 feature master (exact match, rescore) */
+  int32_t db_ma;           /* database views go to this many codewords, 1..8 (0 = 1);
+                              each view is stored once per list it enters (Sec. 2.3:
+                              multiple assignment at the cost of memory)               */
 } gift_index_params;
 
 typedef struct gift_index gift_index; /* opaque; owns all its device memory */
@@ -87,6 +90,7 @@ typedef struct {
   int64_t n_runs;           /* runs of equal shape id over all lists       */
   int32_t max_runs;         /* most runs in one list                       */
   int32_t max_sif_entry;    /* longest S-IF entry                          */
+  int64_t n_entries;        /* F-IF entries: n_rows * db_ma                */
 } gift_index_info_t;
 
 /* Per-stage device times of the last timed gift_query / gift_rerank call

@@ -45,14 +45,14 @@ def lib_path() -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_shapes", "views_per_shape", "dim", "n_codewords", "storage", "query_ma", "sif_k1",
-        "rescore_r", "keep_exact")]
+        "rescore_r", "keep_exact", "db_ma")]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("n_rows", ctypes.c_int64),
                 ("n_lists_nonempty", ctypes.c_int32), ("max_list_len", ctypes.c_int32),
                 ("n_runs", ctypes.c_int64), ("max_runs", ctypes.c_int32),
-                ("max_sif_entry", ctypes.c_int32)]
+                ("max_sif_entry", ctypes.c_int32), ("n_entries", ctypes.c_int64)]
 
 
 class _Timing(ctypes.Structure):
@@ -175,12 +175,12 @@ class Index:
 
     def __init__(self, db_feats, codebook, n_shapes: int, views_per_shape: int, n_codewords: int,
                  storage="f32", query_ma: int = 1, sif_k1: int = 0, rescore_r: int = 0,
-                 keep_exact: bool = True, stream=None):
+                 keep_exact: bool = True, db_ma: int = 1, stream=None):
         lib = load()
         dim = int(codebook.shape[-1])
         self.params = _Params(int(n_shapes), int(views_per_shape), dim, int(n_codewords),
                               _STORAGE[storage] if isinstance(storage, str) else int(storage),
-                              int(query_ma), int(sif_k1), int(rescore_r), int(bool(keep_exact)))
+                              int(query_ma), int(sif_k1), int(rescore_r), int(bool(keep_exact)), int(db_ma))
         self._h = ctypes.c_void_p()
         _check(lib.gift_build_index(ctypes.byref(self.params), _ptr(db_feats), _ptr(codebook),
                                     _stream(stream), ctypes.byref(self._h)))
@@ -191,7 +191,7 @@ class Index:
     @classmethod
     def streamed(cls, chunk_fn, codebook, n_shapes: int, views_per_shape: int, n_codewords: int,
                  chunk_shapes: int = 1024, storage="bf16", query_ma: int = 1, sif_k1: int = 0,
-                 rescore_r: int = 0, stream=None):
+                 rescore_r: int = 0, db_ma: int = 1, stream=None):
         """Build an index from chunks in three passes (gift_build_begin / add / end_pass).
 
         chunk_fn(first_shape, n_shapes) returns the float32 views [n_shapes, N_v, D] of
@@ -203,7 +203,7 @@ class Index:
         dim = int(codebook.shape[-1])
         self.params = _Params(int(n_shapes), int(views_per_shape), dim, int(n_codewords),
                               _STORAGE[storage] if isinstance(storage, str) else int(storage),
-                              int(query_ma), int(sif_k1), int(rescore_r), 0)
+                              int(query_ma), int(sif_k1), int(rescore_r), 0, int(db_ma))
         self._h = ctypes.c_void_p()
         st = _stream(stream)
         _check(lib.gift_build_begin(ctypes.byref(self.params), _ptr(codebook), st, ctypes.byref(self._h)))
@@ -267,8 +267,8 @@ class Index:
 
     # -- inspection ----------------------------------------------------------
     def export_fif(self):
-        """(db_codes [N*Nv], list_offsets [K+1], list_rows [N*Nv]) as numpy arrays."""
-        n = self.n_shapes * self.views_per_shape
+        """(db_codes [N*Nv*db_ma], list_offsets [K+1], list_rows [entries]) as numpy arrays."""
+        n = int(self.info()["n_entries"])
         codes = np.empty(n, np.int32)
         off = np.empty(self.n_codewords + 1, np.int64)
         rows = np.empty(n, np.int32)

@@ -239,16 +239,10 @@ void prepare_codebook(Index& ix, cudaStream_t s) {
 
 namespace {
 
-// list position of every database row: pos[list_row[e]] = e
-__global__ void k_list_pos(const int32_t* __restrict__ list_row, int64_t n, int32_t* __restrict__ pos) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) pos[list_row[e]] = (int32_t)e;
-}
-
 // pass 2 of a streamed build: pack the rows of one chunk into their list
 // positions (store dtype + cosine factor; BF16 parts for the rescore)
 template <typename TO>
-__global__ void k_scatter_pack(const float* __restrict__ chunk, int64_t row0, int64_t n, int D,
+__global__ void k_scatter_pack(const float* __restrict__ chunk, int64_t row0, int64_t n, int D, int ma,
                                const int32_t* __restrict__ pos, const float* __restrict__ row_inv,
                                TO* __restrict__ out, float* __restrict__ scale_out, int fp8,
                                __nv_bfloat16* __restrict__ hi, float* __restrict__ scale_hi,
@@ -257,7 +251,6 @@ __global__ void k_scatter_pack(const float* __restrict__ chunk, int64_t row0, in
   const int lane = threadIdx.x & 31;
   if (r >= n) return;
   const float* x = chunk + r * D;
-  const int64_t e = pos[row0 + r];
   float sc = 1.f;
   if (fp8) {
     float m = 0.f;
@@ -267,30 +260,45 @@ __global__ void k_scatter_pack(const float* __restrict__ chunk, int64_t row0, in
     sc = m > 0.f ? m / 448.f : 1.f;
   }
   const float inv_sc = 1.f / sc;
-  for (int d = lane; d < D; d += 32) {
-    const float v = x[d];
-    out[e * D + d] = cvt_store<TO>(fp8 ? v * inv_sc : v);
-    if (lo) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      lo[e * D + d] = __float2bfloat16_rn(v - __bfloat162float(h));
-      if (hi) hi[e * D + d] = h;
+  for (int a = 0; a < ma; ++a) {  // one copy per list the view entered
+    const int64_t e = pos[(row0 + r) * ma + a];
+    for (int d = lane; d < D; d += 32) {
+      const float v = x[d];
+      out[e * D + d] = cvt_store<TO>(fp8 ? v * inv_sc : v);
+      if (lo) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        lo[e * D + d] = __float2bfloat16_rn(v - __bfloat162float(h));
+        if (hi) hi[e * D + d] = h;
+      }
     }
-  }
-  if (lane == 0) {
-    scale_out[e] = sc * row_inv[row0 + r];
-    if (scale_hi) scale_hi[e] = row_inv[row0 + r];
+    if (lane == 0) {
+      scale_out[e] = sc * row_inv[row0 + r];
+      if (scale_hi) scale_hi[e] = row_inv[row0 + r];
+    }
   }
 }
 
-// F-IF from the database codes: stable sort of rows by code (lists in
-// (shape, view) order), shape ids, runs of equal shape per list, sizes.
-void build_lists(Index& ix_, Scratch& sc, cudaStream_t s) {
+// (row, assignment) item of each entry -> its row; pos[item] = entry (optional)
+__global__ void k_items_to_rows(int32_t* __restrict__ list_row, int64_t n, int ma, int32_t* __restrict__ pos) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int32_t item = list_row[e];
+  if (pos) pos[item] = (int32_t)e;
+  list_row[e] = item / ma;
+}
+
+// F-IF from the database codes: stable sort of the (row, assignment) items by
+// code (lists in (shape, view) order), shape ids, runs of equal shape per
+// list, sizes. pos (optional, [n_entries]) receives the entry of each item.
+void build_lists(Index& ix_, Scratch& sc, cudaStream_t s, int32_t* pos = nullptr) {
   Index* ix = &ix_;
   const int K = ix->prm.n_codewords, Nv = ix->prm.views_per_shape;
-  const int64_t n_rows = ix->n_rows;
+  const int64_t n_rows = ix->n_entries;  // list entries (views x database-side assignments)
   ix->list_row = ix->alloc<int32_t>(n_rows);
   int32_t* skeys = sc.get<int32_t>(n_rows);
   stable_sort_by_key(ix->db_codes, n_rows, K, ix->list_row, skeys, sc, s);
+  k_items_to_rows<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(ix->list_row, n_rows, ix->db_ma, pos);
+  GIFT_LAUNCHED("k_items_to_rows");
   ix->list_off = ix->alloc<int64_t>(K + 1);
   bin_offsets(skeys, n_rows, K, ix->list_off, s);
   ix->list_shape = ix->alloc<int32_t>(n_rows);
@@ -541,11 +549,16 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   GIFT_REQUIRE(p.rescore_r >= 0 && p.rescore_r <= 1024, "rescore_r must be in [0, 1024]");
   GIFT_REQUIRE(p.views_per_shape <= 32767, "views_per_shape must be <= 32767");
   const int64_t n_rows = (int64_t)p.n_shapes * p.views_per_shape;
-  GIFT_REQUIRE(n_rows < (int64_t)INT32_MAX, "too many database views");
+  GIFT_REQUIRE(p.db_ma >= 0 && p.db_ma <= GIFT_MAX_MA && p.db_ma <= p.n_codewords,
+               "db_ma must be in [0, min(8, K)]");
+  const int db_ma = std::max(1, p.db_ma);
+  GIFT_REQUIRE(n_rows * db_ma < (int64_t)INT32_MAX, "too many database views");
 
   std::unique_ptr<Index> ix(new Index());
   ix->prm = p;
   ix->n_rows = n_rows;
+  ix->db_ma = db_ma;
+  ix->n_entries = n_rows * db_ma;
   GIFT_CUDA(cudaGetDevice(&ix->device));
   {
     // per-call scratch comes from the device's default stream-ordered pool;
@@ -588,44 +601,45 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   ix->cb_max_norm *= 1.0001f;
 
   // database codes (one assignment per view)
-  ix->db_codes = ix->alloc<int32_t>(n_rows);
-  assign_codes(*ix, master, n_rows, 1, ix->db_codes, sc, s, ix->row_inv);
+  ix->db_codes = ix->alloc<int32_t>(n_rows * db_ma);
+  assign_codes(*ix, master, n_rows, db_ma, ix->db_codes, sc, s, ix->row_inv);
 
   build_lists(*ix, sc, s);
 
-  // list-ordered feature store
+  // list-ordered feature store (a view appears once per list it enters)
+  const int64_t n_ent = ix->n_entries;
   const size_t eb = dtype_bytes(p.storage);
-  ix->list_rows_alloc = n_rows + 256;  // one TMA box of padding rows
+  ix->list_rows_alloc = n_ent + 256;  // one TMA box of padding rows
   ix->list_feat = ix->alloc<uint8_t>((size_t)ix->list_rows_alloc * D * eb);
-  GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix->list_feat + (size_t)n_rows * D * eb, 0, (size_t)256 * D * eb, s));
-  ix->list_scale = ix->alloc<float>(n_rows);
-  const unsigned pg = (unsigned)cdiv(n_rows, 8);
+  GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix->list_feat + (size_t)n_ent * D * eb, 0, (size_t)256 * D * eb, s));
+  ix->list_scale = ix->alloc<float>(n_ent);
+  const unsigned pg = (unsigned)cdiv(n_ent, 8);
   switch (p.storage) {
     case GIFT_F32:
-      k_pack_lists<float><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_rows, D,
+      k_pack_lists<float><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_ent, D,
                                              (float*)ix->list_feat, ix->list_scale, 0);
       break;
     case GIFT_BF16:
-      k_pack_lists<__nv_bfloat16><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_rows, D,
+      k_pack_lists<__nv_bfloat16><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_ent, D,
                                                      (__nv_bfloat16*)ix->list_feat, ix->list_scale, 0);
       break;
     default:
-      k_pack_lists<__nv_fp8_e4m3><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_rows, D,
+      k_pack_lists<__nv_fp8_e4m3><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_ent, D,
                                                      (__nv_fp8_e4m3*)ix->list_feat, ix->list_scale, 1);
       break;
   }
   GIFT_LAUNCHED("k_pack_lists");
   if (split_rescore) {
     ix->list_lo = ix->alloc<__nv_bfloat16>((size_t)ix->list_rows_alloc * D);
-    GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_lo + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
-    k_pack_lo<<<pg, 256, 0, s>>>(master, ix->list_row, n_rows, D, (__nv_bfloat16*)ix->list_lo);
+    GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_lo + (size_t)n_ent * D, 0, (size_t)256 * D * 2, s));
+    k_pack_lo<<<pg, 256, 0, s>>>(master, ix->list_row, n_ent, D, (__nv_bfloat16*)ix->list_lo);
     GIFT_LAUNCHED("k_pack_lo");
     if (p.storage == GIFT_FP8_E4M3) {
       // the FP8 store scans; the rescore reads a separate BF16 hi part
       ix->list_hi = ix->alloc<__nv_bfloat16>((size_t)ix->list_rows_alloc * D);
-      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_hi + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
-      ix->list_scale_hi = ix->alloc<float>(n_rows);
-      k_pack_lists<__nv_bfloat16><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_rows, D,
+      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix->list_hi + (size_t)n_ent * D, 0, (size_t)256 * D * 2, s));
+      ix->list_scale_hi = ix->alloc<float>(n_ent);
+      k_pack_lists<__nv_bfloat16><<<pg, 256, 0, s>>>(master, ix->list_row, ix->row_inv, n_ent, D,
                                                      (__nv_bfloat16*)ix->list_hi, ix->list_scale_hi, 0);
       GIFT_LAUNCHED("k_pack_lists");
     }
@@ -684,10 +698,15 @@ void stream_begin(const gift_index_params* prm, const float* codebook, cudaStrea
   GIFT_REQUIRE(!p.keep_exact, "a streamed build keeps no FP32 master (keep_exact must be 0)");
   GIFT_REQUIRE(p.views_per_shape <= 32767, "views_per_shape must be <= 32767");
   const int64_t n_rows = (int64_t)p.n_shapes * p.views_per_shape;
-  GIFT_REQUIRE(n_rows < (int64_t)INT32_MAX, "too many database views");
+  GIFT_REQUIRE(p.db_ma >= 0 && p.db_ma <= GIFT_MAX_MA && p.db_ma <= p.n_codewords,
+               "db_ma must be in [0, min(8, K)]");
+  const int db_ma = std::max(1, p.db_ma);
+  GIFT_REQUIRE(n_rows * db_ma < (int64_t)INT32_MAX, "too many database views");
   std::unique_ptr<Index> ix(new Index());
   ix->prm = p;
   ix->n_rows = n_rows;
+  ix->db_ma = db_ma;
+  ix->n_entries = n_rows * db_ma;
   GIFT_CUDA(cudaGetDevice(&ix->device));
   {
     cudaMemPool_t pool;
@@ -712,7 +731,7 @@ void stream_begin(const gift_index_params* prm, const float* codebook, cudaStrea
   GIFT_LAUNCHED("k_cb_maxnorm");
   GIFT_CUDA(cudaMemcpyAsync(&ix->cb_max_norm, d_cbmax, 4, cudaMemcpyDeviceToHost, s));
   ix->row_inv = ix->alloc<float>(n_rows);
-  ix->db_codes = ix->alloc<int32_t>(n_rows);
+  ix->db_codes = ix->alloc<int32_t>(n_rows * db_ma);
   ix->d_err = ix->alloc<int>(1);
   GIFT_CUDA(cudaMemsetAsync(ix->d_err, 0, sizeof(int), s));
   GIFT_CUDA(cudaStreamSynchronize(s));
@@ -740,23 +759,23 @@ void stream_add(Index& ix, int pass, const float* feats, int32_t first, int32_t 
   }
   if (pass == 1) {
     launch_row_invnorm(x, rows, D, ix.row_inv + row0, s);
-    assign_codes(ix, x, rows, 1, ix.db_codes + row0, sc, s, ix.row_inv + row0);
+    assign_codes(ix, x, rows, ix.db_ma, ix.db_codes + row0 * ix.db_ma, sc, s, ix.row_inv + row0);
   } else if (pass == 2) {
     const unsigned g = (unsigned)cdiv(rows, 8);
     __nv_bfloat16* hi = (__nv_bfloat16*)ix.list_hi;
     __nv_bfloat16* lo = (__nv_bfloat16*)ix.list_lo;
     switch (ix.prm.storage) {
       case GIFT_F32:
-        k_scatter_pack<float><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv, (float*)ix.list_feat,
+        k_scatter_pack<float><<<g, 256, 0, s>>>(x, row0, rows, D, ix.db_ma, ix.sb->pos, ix.row_inv, (float*)ix.list_feat,
                                                 ix.list_scale, 0, nullptr, nullptr, nullptr);
         break;
       case GIFT_BF16:
-        k_scatter_pack<__nv_bfloat16><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv,
+        k_scatter_pack<__nv_bfloat16><<<g, 256, 0, s>>>(x, row0, rows, D, ix.db_ma, ix.sb->pos, ix.row_inv,
                                                         (__nv_bfloat16*)ix.list_feat, ix.list_scale, 0, nullptr,
                                                         nullptr, lo);
         break;
       default:
-        k_scatter_pack<__nv_fp8_e4m3><<<g, 256, 0, s>>>(x, row0, rows, D, ix.sb->pos, ix.row_inv,
+        k_scatter_pack<__nv_fp8_e4m3><<<g, 256, 0, s>>>(x, row0, rows, D, ix.db_ma, ix.sb->pos, ix.row_inv,
                                                         (__nv_fp8_e4m3*)ix.list_feat, ix.list_scale, 1, hi,
                                                         ix.list_scale_hi, lo);
         break;
@@ -791,7 +810,9 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
   const int64_t n_rows = ix.n_rows;
   Scratch sc(s);
   if (pass == 1) {
-    build_lists(ix, sc, s);
+    const int64_t n_ent = ix.n_entries;
+    GIFT_CUDA(cudaMalloc(&ix.sb->pos, n_ent * sizeof(int32_t)));
+    build_lists(ix, sc, s, ix.sb->pos);
     {  // the stores need most of the device: hand cached scratch back first
       cudaMemPool_t pool;
       GIFT_CUDA(cudaDeviceGetDefaultMemPool(&pool, ix.device));
@@ -799,22 +820,19 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
       GIFT_CUDA(cudaMemPoolTrimTo(pool, 0));
     }
     const size_t eb = dtype_bytes(ix.prm.storage);
-    ix.list_rows_alloc = n_rows + 256;
+    ix.list_rows_alloc = n_ent + 256;
     ix.list_feat = ix.alloc<uint8_t>((size_t)ix.list_rows_alloc * D * eb);
-    GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix.list_feat + (size_t)n_rows * D * eb, 0, (size_t)256 * D * eb, s));
-    ix.list_scale = ix.alloc<float>(n_rows);
+    GIFT_CUDA(cudaMemsetAsync((uint8_t*)ix.list_feat + (size_t)n_ent * D * eb, 0, (size_t)256 * D * eb, s));
+    ix.list_scale = ix.alloc<float>(n_ent);
     if (ix.prm.rescore_r > 0) {
       ix.list_lo = ix.alloc<__nv_bfloat16>((size_t)ix.list_rows_alloc * D);
-      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_lo + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
+      GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_lo + (size_t)n_ent * D, 0, (size_t)256 * D * 2, s));
       if (ix.prm.storage == GIFT_FP8_E4M3) {
         ix.list_hi = ix.alloc<__nv_bfloat16>((size_t)ix.list_rows_alloc * D);
-        GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_hi + (size_t)n_rows * D, 0, (size_t)256 * D * 2, s));
-        ix.list_scale_hi = ix.alloc<float>(n_rows);
+        GIFT_CUDA(cudaMemsetAsync((__nv_bfloat16*)ix.list_hi + (size_t)n_ent * D, 0, (size_t)256 * D * 2, s));
+        ix.list_scale_hi = ix.alloc<float>(n_ent);
       }
     }
-    GIFT_CUDA(cudaMalloc(&ix.sb->pos, n_rows * sizeof(int32_t)));
-    k_list_pos<<<(unsigned)cdiv(n_rows, 256), 256, 0, s>>>(ix.list_row, n_rows, ix.sb->pos);
-    GIFT_LAUNCHED("k_list_pos");
     ix.sb->stage = 2;
   } else if (pass == 2) {
     if (ix.prm.sif_k1 > 0) {
@@ -1085,11 +1103,11 @@ gift_status gift_export_fif(const gift_index* index, int32_t* db_codes, int64_t*
     const Index& ix = *reinterpret_cast<const Index*>(index);
     if (!ix.list_off) gift::fail(GIFT_ESTATE, "the F-IF lists of this index are not built yet");
     if (db_codes)
-      GIFT_CUDA(cudaMemcpyAsync(db_codes, ix.db_codes, ix.n_rows * 4, cudaMemcpyDefault, stream));
+      GIFT_CUDA(cudaMemcpyAsync(db_codes, ix.db_codes, ix.n_entries * 4, cudaMemcpyDefault, stream));
     if (list_offsets)
       GIFT_CUDA(cudaMemcpyAsync(list_offsets, ix.list_off, (ix.prm.n_codewords + 1) * 8, cudaMemcpyDefault, stream));
     if (list_rows)
-      GIFT_CUDA(cudaMemcpyAsync(list_rows, ix.list_row, ix.n_rows * 4, cudaMemcpyDefault, stream));
+      GIFT_CUDA(cudaMemcpyAsync(list_rows, ix.list_row, ix.n_entries * 4, cudaMemcpyDefault, stream));
     GIFT_CUDA(cudaStreamSynchronize(stream));
   });
 }
@@ -1116,6 +1134,7 @@ gift_status gift_index_info(const gift_index* index, gift_index_info_t* out) {
     const Index& ix = *reinterpret_cast<const Index*>(index);
     out->device_bytes = ix.device_bytes;
     out->n_rows = ix.n_rows;
+    out->n_entries = ix.n_entries;
     out->n_lists_nonempty = ix.n_nonempty;
     out->max_list_len = ix.max_list;
     out->n_runs = ix.n_runs;

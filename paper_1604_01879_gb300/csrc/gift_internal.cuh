@@ -70,13 +70,15 @@ struct StreamBuild {
   int stage = 1;               // pass accepting chunks: 1 codes, 2 stores, 3 S-IF; 4 = complete
   int64_t rows_added = 0;      // rows added in the current pass
   std::vector<uint8_t> seen;   // [N] shapes added in the current pass
-  int32_t* pos = nullptr;      // [n_rows] list position of each database row (pass 2)
+  int32_t* pos = nullptr;      // [n_entries] list position of each (row, assignment) (pass 2)
   ~StreamBuild() { cudaFree(pos); }  // freed once the build completes
 };
 
 struct Index {
   gift_index_params prm{};
-  int64_t n_rows = 0;  // N * Nv
+  int64_t n_rows = 0;     // N * Nv
+  int db_ma = 1;          // codewords per database view
+  int64_t n_entries = 0;  // F-IF entries: n_rows * db_ma
   int device = 0;
 
   // codebook
@@ -90,25 +92,25 @@ struct Index {
   // database
   float* master = nullptr;     // [n_rows, D] FP32 views (keep_exact)
   float* row_inv = nullptr;    // [n_rows] 1/||x|| (0 for a zero row)
-  int32_t* db_codes = nullptr; // [n_rows]
+  int32_t* db_codes = nullptr; // [n_rows * db_ma]
 
   // F-IF
   int64_t* list_off = nullptr;   // [K+1]
   std::vector<int64_t> h_list_off;
-  int32_t* list_row = nullptr;   // [n_rows] row of each entry (list order)
-  int32_t* list_shape = nullptr; // [n_rows]
-  void* list_feat = nullptr;     // [n_rows, D] in storage dtype
-  void* list_lo = nullptr;       // [n_rows, D] BF16 residual x - bf16(x) (rescore)
-  void* list_hi = nullptr;       // [n_rows, D] BF16 bf16(x) when the store is FP8 (rescore)
-  float* list_scale_hi = nullptr;// [n_rows] 1/||x|| for the BF16 parts when the store is FP8
+  int32_t* list_row = nullptr;   // [n_entries] row of each entry (list order)
+  int32_t* list_shape = nullptr; // [n_entries]
+  void* list_feat = nullptr;     // [n_entries, D] in storage dtype
+  void* list_lo = nullptr;       // [n_entries, D] BF16 residual x - bf16(x) (rescore)
+  void* list_hi = nullptr;       // [n_entries, D] BF16 bf16(x) when the store is FP8 (rescore)
+  float* list_scale_hi = nullptr;// [n_entries] 1/||x|| for the BF16 parts when the store is FP8
   int64_t list_rows_alloc = 0;   // rows of list_feat / list_lo including padding
 
   // exact match: shape-ordered two-part BF16 copy of the views (+ padding rows)
   __nv_bfloat16* ex_hi = nullptr;
   __nv_bfloat16* ex_lo = nullptr;
   int64_t ex_rows = 0;
-  float* list_scale = nullptr;   // [n_rows] factor turning a stored dot into a cosine
-  int32_t* entry_run = nullptr;  // [n_rows] run index within its list
+  float* list_scale = nullptr;   // [n_entries] factor turning a stored dot into a cosine
+  int32_t* entry_run = nullptr;  // [n_entries] run index within its list
   int32_t* nruns = nullptr;      // [K]
   int64_t* run_off = nullptr;    // [K] first global run of each list
   int32_t* run_shape = nullptr;  // [n_runs]

@@ -66,7 +66,7 @@ def test_posting_lists_identical(c1):
     N, Nv = c1["dbc"].shape
     assert_codes(codes.reshape(-1, 1), c1["dbc"].reshape(-1, 1),
                  code_margins(c1["X"].reshape(N * Nv, -1), c1["cb"], 1))
-    lists = O.build_fif(codes.reshape(N, Nv), c1["cb"].shape[0])
+    lists = O.build_fif(c1["dbc"], c1["cb"].shape[0])  # the oracle's lists from the oracle's codes
     assert off[0] == 0 and off[-1] == N * Nv
     for k, l in enumerate(lists):
         assert off[k + 1] - off[k] == len(l)
@@ -352,3 +352,37 @@ def test_rescore_depth_can_change_after_build(gpu_lib):
         with_r.set_rescore_depth(2000)
     with_r.close()
     no_r.close()
+
+
+@pytest.mark.parametrize("db_ma,q_ma,storage", [(2, 1, "f32"), (2, 2, "f32"), (3, 1, "bf16")])
+def test_database_side_multiple_assignment(gpu_lib, db_ma, q_ma, storage):
+    """Each database view enters db_ma lists (stored once per list): codes, lists and Eq. 4
+    scores against the oracle with multiple assignment on the database side."""
+    import torch
+    N, Nv, D, C, K = 120, 16, 64, 4, 12
+    X, cb, Q, qoff, _, _ = _case(N, Nv, D, C, K, 6, (16, 9), 131, ma=q_ma)
+    R = 40 if storage != "f32" else 0
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage=storage, query_ma=q_ma, db_ma=db_ma, rescore_r=R,
+                keep_exact=False)
+    assert ix.info()["n_entries"] == N * Nv * db_ma
+    codes, off, rows = ix.export_fif()
+    rows_x = X.reshape(N * Nv, D)
+    dbc = O.quantize(rows_x, cb, db_ma)
+    assert_codes(codes.reshape(-1, db_ma), dbc, code_margins(rows_x, cb, db_ma))
+    lists = O.build_fif(dbc.reshape(N, Nv, db_ma), K)
+    for k, l in enumerate(lists):
+        ref = (l[:, 0] * Nv + l[:, 1]) if len(l) else np.zeros(0, np.int64)
+        assert np.array_equal(rows[off[k]:off[k + 1]], ref)
+    ref = O.fif_scores(Q, qoff, O.quantize(Q, cb, q_ma), X, dbc.reshape(N, Nv, db_ma))
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=10)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for b in range(len(qoff) - 1):
+        assert_topk(ids[b], sc[b], ref[b], 10)
+    # the streamed build gives the same lists
+    st = gpu_lib.Index.streamed(lambda f, n: X[f:f + n], torch.from_numpy(cb).cuda(), N, Nv, K, chunk_shapes=37,
+                                storage=storage if storage != "f32" else "f32", query_ma=q_ma, rescore_r=R,
+                                db_ma=db_ma)
+    for a, b in zip(ix.export_fif(), st.export_fif()):
+        assert np.array_equal(a, b)
+    st.close()
+    ix.close()
