@@ -18,6 +18,10 @@ as library steps. What each function computes, with the passage it follows:
 * ``fif_upper_bound``/``fif_topk_bounded``  the top-k of Eq. 4 over a database
                            too large to quantise whole: an upper bound of every
                            Eq. 4 term prunes the shapes that cannot rank
+* ``normalize_mesh``/``view_frames``/``raster_depth``/``render_depth``  the
+                           projection front end of Sec. 2.1: scale and translation
+                           normalisation, cameras on the unit sphere by azimuth and
+                           elevation, depth-buffer views
 * ``rank``                 the ranked list, order (score desc, id asc)
 * ``membership``           the sparse activation F_q of Eq. 7
 * ``contextual``           S'(x_q, x_p) of Eq. 8
@@ -41,6 +45,10 @@ Readings where the paper is silent (each also listed in the design notes):
 * ranking ties go to the lower shape id; re-ranking orders by
   (S' desc, S desc, id asc); S' = 0 when both F vectors are zero;
 * a database shape's neighbour set N_k1 includes the shape itself;
+* rendering: the centroid is the area-weighted surface centroid; cameras use
+  orthographic projection along the view axis (the image plane spans the unit
+  sphere's silhouette), elevations avoid the poles, and a pixel samples its
+  centre with closed triangles (edge functions >= 0);
 * with two measures, the re-ranked order breaks S' ties by the first measure's
   score S^(1), then by id; the neighbour sets of Eqs. 10/11 are the first k2
   entries of the same rankings that give N_k1;
@@ -481,6 +489,83 @@ def rerank_aca(S1_q, S2_q, S1_db, S2_db, k1, k2, alpha, mode, k):
         ids[b] = order
         sp[b] = Sprime[order]
     return ids, sp
+
+
+# ---------------------------------------------------------------- projection rendering (Sec. 2.1)
+def normalize_mesh(V, T):
+    """Scale and translation normalisation of Sec. 2.1: the centroid of the surface
+    (triangle centroids weighted by area) goes to the origin and the largest
+    distance of a surface point from it becomes 1. Returns (centre [3], scale)."""
+    V = _f64(V)
+    T = np.asarray(T, np.int64)
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    centre = (area[:, None] * (a + b + c) / 3.0).sum(axis=0) / area.sum()
+    return centre, 1.0 / np.sqrt(((V - centre) ** 2).sum(axis=1)).max()
+
+
+def view_frames(n_az, n_el):
+    """Cameras on the unit sphere at azimuth 2 pi i / n_az and elevation
+    pi ((j + 1/2) / n_el - 1/2), view v = j * n_az + i, each looking at the origin:
+    (position C, forward f = -C, right r = f x z / |f x z|, up u = r x f), [N_v, 3] each."""
+    az = 2 * np.pi * np.arange(n_az) / n_az
+    el = np.pi * ((np.arange(n_el) + 0.5) / n_el - 0.5)
+    E, A = np.meshgrid(el, az, indexing="ij")
+    C = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], axis=-1).reshape(-1, 3)
+    f = -C
+    r = np.cross(f, np.array([0.0, 0.0, 1.0]))
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    u = np.cross(r, f)
+    return C, f, r, u
+
+
+def raster_depth(S, T, H, W, background=2.0):
+    """Depth buffer of triangles given in screen space S [n, 3] = (x, y, depth), x and y
+    in [-1, 1]: pixel (i, j) samples its centre (-1 + (2j + 1)/W, 1 - (2i + 1)/H); a
+    sample is covered when all three edge functions of the triangle, oriented to a
+    positive area, are >= 0 (degenerate triangles cover nothing); its depth is the
+    barycentric interpolation, and the nearest (smallest) depth is kept."""
+    S = _f64(S)
+    T = np.asarray(T, np.int64)
+    D = np.full((H, W), float(background))
+    xs = -1 + (2 * np.arange(W) + 1) / W
+    ys = 1 - (2 * np.arange(H) + 1) / H
+    for t in T:
+        a, b, c = S[t[0]], S[t[1]], S[t[2]]
+        area = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+        if area == 0:
+            continue
+        if area < 0:
+            b, c = c, b
+            area = -area
+        jj = np.nonzero((xs >= min(a[0], b[0], c[0])) & (xs <= max(a[0], b[0], c[0])))[0]
+        ii = np.nonzero((ys >= min(a[1], b[1], c[1])) & (ys <= max(a[1], b[1], c[1])))[0]
+        if len(jj) == 0 or len(ii) == 0:
+            continue
+        X, Y = np.meshgrid(xs[jj], ys[ii])
+        ea = (c[0] - b[0]) * (Y - b[1]) - (c[1] - b[1]) * (X - b[0])  # opposite a
+        eb = (a[0] - c[0]) * (Y - c[1]) - (a[1] - c[1]) * (X - c[0])  # opposite b
+        ec = (b[0] - a[0]) * (Y - a[1]) - (b[1] - a[1]) * (X - a[0])  # opposite c
+        inside = (ea >= 0) & (eb >= 0) & (ec >= 0)
+        z = (ea * a[2] + eb * b[2] + ec * c[2]) / area
+        sub = D[np.ix_(ii, jj)]
+        D[np.ix_(ii, jj)] = np.where(inside, np.minimum(sub, z), sub)
+    return D
+
+
+def render_depth(V, T, n_az, n_el, H, W):
+    """The N_v = n_az * n_el depth views of Sec. 2.1 of one mesh, float64 [N_v, H, W]:
+    normalise (``normalize_mesh``), then for every camera of ``view_frames`` an
+    orthographic depth buffer along its forward axis, depth = distance from the
+    camera's tangent plane, p . f + 1 in [0, 2] (2 where nothing is seen)."""
+    centre, scale = normalize_mesh(V, T)
+    P = (_f64(V) - centre) * scale
+    _, f, r, u = view_frames(n_az, n_el)
+    out = np.empty((len(f), H, W))
+    for v in range(len(f)):
+        S = np.stack([P @ r[v], P @ u[v], P @ f[v] + 1.0], axis=1)
+        out[v] = raster_depth(S, T, H, W)
+    return out
 
 
 def match_forward(Q, q_off, P, W=None):

@@ -607,3 +607,77 @@ def test_database_side_full_assignment_equals_exact():
     dbc = O.quantize(X.reshape(-1, 3), Bk, 3).reshape(5, 4, 3)
     assert np.allclose(O.fif_scores(Q, off, O.quantize(Q, Bk, 1), X, dbc), O.exact_scores(Q, off, X),
                        atol=1e-14, rtol=0)
+
+
+# ----------------------------------------------------------------- projection rendering (Sec. 2.1)
+def py_raster(S, T, H, W):
+    """Depth buffer by explicit loops over pixels and triangles (closed triangles, nearest depth)."""
+    D = [[2.0] * W for _ in range(H)]
+    for i in range(H):
+        for j in range(W):
+            px, py = -1 + (2 * j + 1) / W, 1 - (2 * i + 1) / H
+            for t in T:
+                (ax, ay, az), (bx, by, bz), (cx, cy, cz) = (S[k] for k in t)
+                area = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+                if area == 0:
+                    continue
+                w = [(cx - bx) * (py - by) - (cy - by) * (px - bx), (ax - cx) * (py - cy) - (ay - cy) * (px - cx),
+                     (bx - ax) * (py - ay) - (by - ay) * (px - ax)]
+                if area < 0:
+                    w = [-x for x in w]
+                    area = -area
+                if min(w) >= 0:
+                    D[i][j] = min(D[i][j], (w[0] * az + w[1] * bz + w[2] * cz) / area)
+    return np.array(D)
+
+
+def test_raster_half_screen_and_zbuffer():
+    # the lower-left half-screen triangle at depth 0.5 over a full-screen pair at depth 1.0
+    S = np.array([[-1, -1, 0.5], [1, -1, 0.5], [-1, 1, 0.5], [-1, -1, 1.0], [1, -1, 1.0], [1, 1, 1.0], [-1, 1, 1.0]])
+    T = np.array([[0, 1, 2], [3, 4, 5], [3, 5, 6]])
+    D = O.raster_depth(S, T, 4, 4)
+    X, Y = np.meshgrid(-1 + (2 * np.arange(4) + 1) / 4, 1 - (2 * np.arange(4) + 1) / 4)
+    assert np.array_equal(D, np.where(X + Y <= 0, 0.5, 1.0))
+    g = np.random.default_rng(51)
+    S = np.concatenate([g.uniform(-1.2, 1.2, (9, 2)), g.uniform(0, 2, (9, 1))], axis=1)
+    T = g.integers(0, 9, (6, 3))
+    assert np.allclose(O.raster_depth(S, T, 7, 9), py_raster(S, T, 7, 9), atol=1e-12)
+
+
+def test_normalisation_invariance_and_frames():
+    from synth.meshes import star_mesh
+    V, T = star_mesh(4, 3, 9, n_lat=8, n_lon=12)
+    c, s = O.normalize_mesh(V, T)
+    P = (V - c) * s
+    assert np.sqrt((P ** 2).sum(1)).max() == pytest.approx(1.0)
+    c2, s2 = O.normalize_mesh(P, T)
+    assert np.allclose(c2, 0, atol=1e-12) and s2 == pytest.approx(1.0)
+    a = O.render_depth(V, T, 4, 2, 12, 12)
+    b = O.render_depth(V.astype(np.float64) * 3.5 + np.array([7.0, -2, 5]), T, 4, 2, 12, 12)
+    assert np.allclose(a, b, atol=1e-9)
+    C, f, r, u = O.view_frames(8, 8)
+    assert np.allclose(np.linalg.norm(C, axis=1), 1) and np.allclose((r * f).sum(1), 0)
+    assert np.allclose(np.cross(r, u), -f)  # right-handed: r x u points back at the camera
+
+
+def test_sphere_depth_closed_form():
+    """A finely tessellated sphere: the silhouette covers the disc x^2 + y^2 <= 1 and the
+    front surface lies at depth 1 - sqrt(1 - x^2 - y^2)."""
+    n_lat, n_lon = 64, 128
+    th = np.pi * np.arange(1, n_lat) / n_lat
+    ph = 2 * np.pi * np.arange(n_lon) / n_lon
+    TT, PP = np.meshgrid(th, ph, indexing="ij")
+    ring = np.stack([np.sin(TT) * np.cos(PP), np.sin(TT) * np.sin(PP), np.cos(TT)], -1).reshape(-1, 3)
+    V = np.concatenate([[[0, 0, 1.0]], ring, [[0, 0, -1.0]]])
+    idx = lambda i, j: 1 + i * n_lon + (j % n_lon)
+    T = [(0, idx(0, j), idx(0, j + 1)) for j in range(n_lon)]
+    T += [(len(V) - 1, idx(n_lat - 2, j + 1), idx(n_lat - 2, j)) for j in range(n_lon)]
+    for i in range(n_lat - 2):
+        for j in range(n_lon):
+            T += [(idx(i, j), idx(i + 1, j), idx(i, j + 1)), (idx(i, j + 1), idx(i + 1, j), idx(i + 1, j + 1))]
+    D = O.render_depth(V, np.array(T), 2, 1, 16, 16)[0]
+    X, Y = np.meshgrid(-1 + (2 * np.arange(16) + 1) / 16, 1 - (2 * np.arange(16) + 1) / 16)
+    R2 = X ** 2 + Y ** 2
+    inner = R2 < 0.85
+    assert np.all(D[inner] < 2) and np.all(D[R2 > 1.05] == 2)
+    assert np.abs(D[inner] - (1 - np.sqrt(1 - R2[inner]))).max() < 5e-3
