@@ -274,6 +274,29 @@ GIFT_API gift_status gift_aca_export(const gift_aca* aca, int64_t* entry_offsets
 GIFT_API void gift_aca_destroy(gift_aca* aca);
 
 /*
+ * Projection front end (Sec. 2.1): the depth-buffer views of a batch of meshes.
+ *  - vertices: device or host float [sum V_m * 3]; triangles: device or host
+ *    int32 [sum T_m * 3], vertex indices local to their mesh; vert_off /
+ *    tri_off: host int64 [M + 1] offsets (in vertices / triangles) of each mesh.
+ *  - Each mesh is normalised: the area-weighted centroid of its surface goes to
+ *    the origin and the largest vertex distance from it becomes 1 (scale and
+ *    translation only, as in the paper).
+ *  - Cameras on the unit sphere at azimuth 2 pi i / n_az and elevation
+ *    pi ((j + 1/2) / n_el - 1/2), view v = j * n_az + i, look at the origin:
+ *    forward f, right r = f x z / |f x z|, up u = r x f. Orthographic H x W
+ *    image over [-1, 1]^2 in (r, u); pixel (y, x) samples its centre
+ *    (-1 + (2x + 1) / W, 1 - (2y + 1) / H); a closed triangle covers the samples
+ *    where its three edge functions are >= 0; depth = p . f + 1 in [0, 2]
+ *    interpolated across the triangle; the nearest depth is kept; 2 where
+ *    nothing is seen.
+ *  - depth: device or host float [M, n_az * n_el, H, W].
+ * Errors: EINVAL (sizes, offsets, a vertex index outside its mesh), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_render_views(const float* vertices, const int32_t* triangles, const int64_t* vert_off,
+                                       const int64_t* tri_off, int32_t M, int32_t n_az, int32_t n_el, int32_t H,
+                                       int32_t W, float* depth, cudaStream_t stream);
+
+/*
  * Lloyd's k-means on the GPU: the off-line vocabulary B of Sec. 2.3 (the paper
  * trains it with k-means and gives no details).
  *  - X: device or host float [n * D] (D a multiple of 16); init_rows: host

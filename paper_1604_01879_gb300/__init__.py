@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "GiftError", "load", "lib_path", "Index", "match_forward", "match_backward", "GiftMatch",
-    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF", "Aca", "kmeans",
+    "F32", "BF16", "FP8_E4M3", "MATCH_EXACT", "MATCH_FIF", "Aca", "kmeans", "render_views",
 ]
 
 F32, BF16, FP8_E4M3 = 0, 1, 2
@@ -88,6 +88,7 @@ _SIGS = {
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
+    "gift_render_views": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _I32, _P, _P]),
     "gift_kmeans": (_I32, [_P, _I64, _I32, _I32, _P, _I32, _P, _P]),
     "gift_aca_build": (_I32, [_P, _P, _I32, ctypes.c_float, _I32, _P, ctypes.POINTER(_P)]),
     "gift_aca_rerank": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
@@ -398,6 +399,24 @@ GiftMatch = _Lazy()
 
 
 # ---------------------------------------------------------------- serving
+def render_views(vertices, triangles, vert_off, tri_off, n_az: int = 8, n_el: int = 8, H: int = 224,
+                 W: int = 224, out=None, stream=None):
+    """Depth-buffer views of a batch of meshes (Sec. 2.1): float32 [M, n_az * n_el, H, W]."""
+    import torch
+    vo = np.ascontiguousarray(np.asarray(vert_off, np.int64))
+    to = np.ascontiguousarray(np.asarray(tri_off, np.int64))
+    M = len(vo) - 1
+    if isinstance(vertices, np.ndarray):
+        vertices = np.ascontiguousarray(vertices, dtype=np.float32)
+    if isinstance(triangles, np.ndarray):
+        triangles = np.ascontiguousarray(triangles, dtype=np.int32)
+    if out is None:
+        out = torch.empty((M, n_az * n_el, H, W), dtype=torch.float32, device="cuda")
+    _check(load().gift_render_views(_ptr(vertices), _ptr(triangles), _ptr(vo), _ptr(to), M, int(n_az), int(n_el),
+                                    int(H), int(W), _ptr(out), _stream(stream)))
+    return out
+
+
 def kmeans(X, init_rows, iters: int, out=None, stream=None):
     """Lloyd's k-means on the GPU (the off-line vocabulary): centres float32 [K, D].
 

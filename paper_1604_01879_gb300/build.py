@@ -34,6 +34,7 @@ SOURCES = [
     "serve.cu",
     "tc_gemm.cu",
     "k_kmeans.cu",
+    "k_render.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

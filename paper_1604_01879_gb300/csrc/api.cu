@@ -807,7 +807,6 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
   GIFT_REQUIRE(pass == ix.sb->stage, "pass " + std::to_string(ix.sb->stage) + " is the open pass");
   GIFT_REQUIRE(ix.sb->rows_added == ix.n_rows, "every database shape must be added once in each pass");
   const int D = ix.prm.dim;
-  const int64_t n_rows = ix.n_rows;
   Scratch sc(s);
   if (pass == 1) {
     const int64_t n_ent = ix.n_entries;
@@ -982,6 +981,29 @@ gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, const float*
     gift::flush_out(outs, stream);
     ix.stats_valid = false;
     tm.finish();
+  });
+}
+
+gift_status gift_render_views(const float* vertices, const int32_t* triangles, const int64_t* vert_off,
+                             const int64_t* tri_off, int32_t M, int32_t n_az, int32_t n_el, int32_t H, int32_t W,
+                             float* depth, cudaStream_t stream) {
+  return gift::guard("gift_render_views", [&] {
+    GIFT_REQUIRE(vertices && triangles && vert_off && tri_off && depth, "NULL argument");
+    GIFT_REQUIRE(M >= 1 && n_az >= 1 && n_el >= 1 && n_az * n_el <= 4096, "need M >= 1 and 1 <= N_v <= 4096");
+    GIFT_REQUIRE(H >= 1 && W >= 1 && H <= 4096 && W <= 4096, "image sides must be in [1, 4096]");
+    std::vector<int64_t> vo(vert_off, vert_off + M + 1), to(tri_off, tri_off + M + 1);
+    GIFT_REQUIRE(vo[0] == 0 && to[0] == 0, "offsets must start at 0");
+    for (int m = 0; m < M; ++m)
+      GIFT_REQUIRE(vo[m + 1] >= vo[m] && to[m + 1] >= to[m], "offsets must not decrease");
+    GIFT_REQUIRE(vo[M] < (int64_t)INT32_MAX && to[M] * (int64_t)n_az * n_el < ((int64_t)1 << 40),
+                 "too many vertices or triangle views");
+    gift::Scratch sc(stream);
+    std::vector<gift::OutBuf> outs;
+    const float* V = gift::stage_in(vertices, (size_t)vo[M] * 3, sc, stream);
+    const int32_t* T = gift::stage_in(triangles, (size_t)to[M] * 3, sc, stream);
+    float* out = gift::stage_out(depth, (size_t)M * n_az * n_el * H * W, sc, outs);
+    gift::render_views(V, T, vo, to, M, n_az, n_el, H, W, out, sc, stream);
+    gift::flush_out(outs, stream);
   });
 }
 

@@ -186,6 +186,11 @@ void prepare_codebook(Index& ix, cudaStream_t s);
 void kmeans(const float* X, int64_t n, int D, int K, const std::vector<int32_t>& init_rows, int iters, float* C_out,
             Scratch& sc, cudaStream_t s);
 
+// k_render.cu: the N_v = n_az * n_el depth views of every mesh (Sec. 2.1); depth [M, N_v, H, W] on the device
+void render_views(const float* V, const int32_t* T, const std::vector<int64_t>& h_voff,
+                  const std::vector<int64_t>& h_toff, int M, int n_az, int n_el, int H, int W, float* depth,
+                  Scratch& sc, cudaStream_t s);
+
 // k_exact_tc.cu: Eq. 3 over all N shapes on the tensor cores
 void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
                      const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);
