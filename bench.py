@@ -282,6 +282,7 @@ def main():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     ap.add_argument("--no-aca", action="store_true", help="skip the two-measure re-rank measurement")
     ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU k-means measurement")
+    ap.add_argument("--no-render", action="store_true", help="skip the projection front end measurement")
     ap.add_argument("--rescore", type=int, default=None, help="override the config's rescore depth R")
     ap.add_argument("--oracle-queries", type=int, default=4, help="sampled queries for recall (large configs)")
     args = ap.parse_args()
@@ -584,6 +585,12 @@ def main():
         km = bench_kmeans(cfg, gift, torch, dev, stream, data)
         log(f"[bench] k-means: {km}")
 
+    # ---- projection front end: 64 depth views per mesh
+    rend = None
+    if not args.no_render and rank == 0 and not large:
+        rend = bench_render(gift, torch, dev, stream)
+        log(f"[bench] rendering: {rend}")
+
     # ---- differentiation: projected match forward + backward at its own workload
     diff = None
     if not args.no_diff and rank == 0 and not large:
@@ -617,6 +624,7 @@ def main():
         "differentiation": diff,
         "two_measure_rerank": aca,
         "kmeans": km,
+        "rendering": rend,
     }
 
     # ---- roofline of the dominant kernel (CUDA events around the launch itself)
@@ -751,6 +759,30 @@ def bench_aca(cfg, gift, torch, dev, stream, ix1, batches, topk, R, reps=5):
     return {"measure2": c2.name, "k1": cfg.sif_k1, "k2": 4, "alpha": 0.5, "mode": "co-augmentation (Eq. 11)",
             "queries_per_step": B, "step_ms": t_ms, "queries_per_s": B / (t_ms / 1e3), "fused_rerank_ms": r_ms,
             "fused_sif_pairs": pairs, "build_index2_s": t_ix2, "build_fused_sif_s": t_aca}
+
+
+def bench_render(gift, torch, dev, stream, n_meshes=256, reps=3):
+    """Depth-buffer views (Sec. 2.1) of a batch of seeded meshes: 8 azimuths x 8 elevations
+    at 224 x 224, device inputs, device-timed."""
+    from synth.meshes import mesh_batch
+    V, T, vo, to = mesh_batch(0, n_meshes, 40, 61)
+    Vd, Td = torch.from_numpy(V).to(dev), torch.from_numpy(T).to(dev)
+    out = torch.empty((n_meshes, 64, 224, 224), dtype=torch.float32, device=dev)
+    gift.render_views(Vd, Td, vo, to, 8, 8, 224, 224, out=out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    for _ in range(reps):
+        gift.render_views(Vd, Td, vo, to, 8, 8, 224, 224, out=out)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / reps
+    covered = float((out < 2).float().mean().item())
+    del out, Vd, Td
+    torch.cuda.empty_cache()
+    return {"meshes": n_meshes, "triangles_per_mesh": int(to[1] - to[0]), "views": 64, "image": [224, 224],
+            "ms": ms, "ms_per_mesh": ms / n_meshes, "meshes_per_s": n_meshes / (ms / 1e3),
+            "covered_pixel_fraction": covered, "output_gb": n_meshes * 64 * 224 * 224 * 4 / 1e9}
 
 
 def bench_kmeans(cfg, gift, torch, dev, stream, data):
