@@ -6,10 +6,14 @@
 // segmented-max contraction of U and V (two-part split, FP32-level) gives
 // S and the first argmax j* of every (query view, shape).
 // Backward, with c = grad_S[b, p] / |V(x_b)| and s = u_i.v_j*/(|u_i||v_j*|):
-//   dU_i  = (1/|u_i|)  ( sum_p c v_j*/|v_j*|  - (sum_p c s) u_i/|u_i| )
-//   dV_r  = (1/|v_r|)  ( sum_{(i,p): j*=r} c u_i/|u_i| - (sum c s) v_r/|v_r| )
-// gathered on the CUDA cores (one block per query view for dU; per shape, a
-// shared-memory accumulation over query views for dV, no atomics), then
+//   dU_i  = (1/|u_i|)  ( g_i - (g_i . u_i/|u_i|) u_i/|u_i| ),  g_i = sum_p c v_j*/|v_j*|
+//   dV_r  = (1/|v_r|)  ( h_r - (h_r . v_r/|v_r|) v_r/|v_r| ),  h_r = sum_{(i,p): j*=r} c u_i/|u_i|
+// (the projections use s = g-weighted cosines: sum_p c s = g_i . u_i/|u_i|).
+// G = A V and H = A^T U are GEMMs with the one-hot matrix A[i, r] =
+// c v-norm-weight where r is the argmax view of (i, shape(r)); A is never
+// stored: the engine's producer warp writes each A tile from the argmax
+// (transposed to shape-major) into shared memory, and the tensor cores
+// multiply it with two-part operands. Then
 //   dW = dU^T Q + dV^T P,  dQ = dU W,  dP = dV W
 // as engine GEMMs on transposed two-part operands.
 #include "gift_internal.cuh"
@@ -70,141 +74,171 @@ __global__ void k_transpose_split(const T* __restrict__ in, int64_t rows, int64_
   }
 }
 
-// dU_i and s[i, p] = cos(u_i, v_{p*nv + j*}) for one query view per block:
-// each warp walks a subset of the shapes, keeps u_i and its share of the dU
-// accumulator in registers (lane owns dims lane, lane+32, ...), and the
-// warps' partials are summed through shared memory at the end.
-template <int DPL>  // dims per lane: dout <= 32 * DPL
-__global__ __launch_bounds__(256) void k_grad_u(const float* __restrict__ U, const float* __restrict__ uinv,
-                                                 const float* __restrict__ V, const float* __restrict__ vinv,
-                                                 const int16_t* __restrict__ argmax, const float* __restrict__ gS,
-                                                 const int32_t* __restrict__ vquery, const int32_t* __restrict__ qoff,
-                                                 int Np, int nv, int dout, float* __restrict__ s_out,
-                                                 float* __restrict__ dU) {
-  __shared__ float part[8][DPL * 32];
-  __shared__ float tot_w[8];
-  const int64_t i = blockIdx.x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = vquery[i];
-  const float invV = 1.f / (float)(qoff[b + 1] - qoff[b]);
-  const float ui = uinv[i];
-  float u[DPL], acc[DPL];
-#pragma unroll
-  for (int k = 0; k < DPL; ++k) {
-    const int d = lane + 32 * k;
-    u[k] = d < dout ? U[i * dout + d] : 0.f;
-    acc[k] = 0.f;
-  }
-  float tot = 0.f;
-#pragma unroll 2
-  for (int p = w; p < Np; p += 8) {
-    const int64_t wi = i * Np + p;
-    int j = argmax[wi];
-    if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; never index outside the shape
-    const int64_t r = (int64_t)p * nv + j;
-    const float* v = V + r * dout;
-    float vv[DPL];
-    float dot = 0.f;
-#pragma unroll
-    for (int k = 0; k < DPL; ++k) {
-      const int d = lane + 32 * k;
-      vv[k] = d < dout ? v[d] : 0.f;
-      dot = fmaf(u[k], vv[k], dot);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-    const float vi = vinv[r];
-    const float sc = dot * ui * vi;
-    if (lane == 0) s_out[wi] = sc;
-    const float c = gS[(int64_t)b * Np + p] * invV;
-    const float cv = c * vi;
-#pragma unroll
-    for (int k = 0; k < DPL; ++k) acc[k] = fmaf(cv, vv[k], acc[k]);
-    tot = fmaf(c, sc, tot);
-  }
-#pragma unroll
-  for (int k = 0; k < DPL; ++k) part[w][lane + 32 * k] = acc[k];  // lanes past dout hold 0
-  if (lane == 0) tot_w[w] = tot;
-  __syncthreads();
-  float T = 0.f;
-#pragma unroll
-  for (int ww = 0; ww < 8; ++ww) T += tot_w[ww];
-  for (int d = threadIdx.x; d < dout; d += 256) {
-    float a = 0.f;
-#pragma unroll
-    for (int ww = 0; ww < 8; ++ww) a += part[ww][d];
-    dU[i * dout + d] = ui * (a - T * U[i * dout + d] * ui);
-  }
-}
+// ---------------------------------------------------------------- one-hot gradient GEMMs
+// k-blocks per accumulator chunk: 16 x 4 sub-steps x 3 products = 192 MMA steps
+constexpr int kOneHotChunkKB = 16;
 
-// dV rows of shape p: one block per shape, 16 warps; warp w owns the shape's
-// rows j = w, w + 16, ... (accumulators in registers, lane owns dims lane,
-// lane + 32, ...), scans the argmax column of the shape for the query views
-// that selected one of its rows and adds c * u_i / |u_i| there. No atomics;
-// every row of U is read once per shape, from L2.
-template <int DPL>
-__global__ __launch_bounds__(512) void k_grad_v(const float* __restrict__ U, const float* __restrict__ uinv,
-                                                 const float* __restrict__ V, const float* __restrict__ vinv,
-                                                 const int16_t* __restrict__ argmax, const float* __restrict__ s,
-                                                 const float* __restrict__ gS, const int32_t* __restrict__ vquery,
-                                                 const int32_t* __restrict__ qoff, int64_t nq, int Np, int nv,
-                                                 int dout, float* __restrict__ dV) {
-  constexpr int RPW = 4;  // rows per warp per pass
-  const int p = blockIdx.x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j0 = w * RPW; j0 < nv; j0 += 16 * RPW) {
-    float acc[RPW][DPL];
-    float ct[RPW];
-#pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      ct[t] = 0.f;
-#pragma unroll
-      for (int k = 0; k < DPL; ++k) acc[t][k] = 0.f;
+// ROWS_Q: rows are query views i and the reduction runs over database views r
+// (G = A V); otherwise rows are database views r and the reduction runs over
+// query views i (H = A^T U). B is the transposed two-part operand of V or U.
+template <bool ROWS_Q>
+struct OneHotPolicy {
+  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
+  static constexpr bool GEN_A = true;
+  static constexpr int kWarpSmem = 16;
+  int64_t M, N;             // rows (query or database views), dout
+  int nkb;                  // 64-wide k-blocks of the reduction
+  int64_t nq, nr;           // query views, database views
+  int Np, nv;               // shapes, views per shape
+  const int16_t* amT;       // [Np, nq] argmax view of (i, p), shape-major
+  const float* gS;          // [B, Np]
+  const int32_t* vquery;    // [nq] query of each view
+  const float* vcoef;       // [nq] 1 / |V(x_b)| of the view's query
+  const float* kinv;        // ROWS_Q: 1/|v_r| [nr]; else 1/|u_i| [nq]
+  float* C;                 // [M, N]
+  struct Item {
+    int64_t r0, c0;
+    int nr, nc;
+  };
+  struct Ctx {
+    float sum[TN];
+  };
+  struct GenRegs {};
+  __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
+  __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    Item it;
+    const int64_t mt = n_mt();
+    const int64_t ct = item / mt, rt = item % mt;
+    it.r0 = rt * tc::kTM;
+    it.c0 = ct * TN;
+    it.nr = (int)min((int64_t)tc::kTM, M - it.r0);
+    it.nc = (int)min((int64_t)TN, N - it.c0);
+    return it;
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return (int)cdiv(nkb, kOneHotChunkKB); }
+  __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
+    br = (int)it.c0;
+    kb0 = c * kOneHotChunkKB;
+    kb1 = min(nkb, kb0 + kOneHotChunkKB);
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
+  __device__ __forceinline__ void gen_load(const Item&, int, int, GenRegs&) const {}
+  // one non-zero of the A tile, hi and lo parts, 128-byte swizzled K-major layout
+  __device__ __forceinline__ static void put(uint8_t* a_hi, uint8_t* a_lo, int row, int col, float w) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+    const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
+    const int off = row * 128 + ((((col >> 3) ^ (row & 7))) << 4) + ((col & 7) << 1);
+    *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
+  }
+  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs&, uint8_t* a_hi,
+                                            uint8_t* a_lo) const {
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int o = lane * 16; o < tc::kTM * 128; o += 32 * 16) {
+      *reinterpret_cast<uint4*>(a_hi + o) = z;
+      *reinterpret_cast<uint4*>(a_lo + o) = z;
     }
-    for (int64_t i0 = 0; i0 < nq; i0 += 32) {
-      const int64_t i = i0 + lane;
-      int j = -1;
-      if (i < nq) {
-        j = argmax[i * Np + p];
-        if (j < 0 || j >= nv) j = 0;
+    __syncwarp();
+    const int64_t k0 = (int64_t)kb * 64;
+    if (ROWS_Q) {
+      if (k0 >= nr) return;
+      const int p0 = (int)(k0 / nv), p1 = (int)min((int64_t)Np - 1, (k0 + 63) / nv);
+      for (int q = 0; q < 4; ++q) {
+        const int row = lane + 32 * q;
+        const int64_t i = it.r0 + row;
+        if (row >= it.nr) continue;
+        const int b = vquery[i];
+        const float cb = vcoef[i];
+        for (int p = p0; p <= p1; ++p) {
+          int j = amT[(int64_t)p * nq + i];
+          if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; stay inside the shape
+          const int64_t r = (int64_t)p * nv + j;
+          if (r < k0 || r >= k0 + 64) continue;
+          put(a_hi, a_lo, row, (int)(r - k0), gS[(int64_t)b * Np + p] * cb * kinv[r]);
+        }
       }
-      unsigned hit = __ballot_sync(0xffffffffu, j >= j0 && j < j0 + RPW);
-      while (hit) {
-        const int src = __ffs(hit) - 1;
-        hit &= hit - 1;
-        const int64_t ii = i0 + src;
-        const int jj = __shfl_sync(0xffffffffu, j, src) - j0;
-        const int b = vquery[ii];
-        const float c = gS[(int64_t)b * Np + p] / (float)(qoff[b + 1] - qoff[b]);
-        const float cu = c * uinv[ii];
-        const float sc = s[ii * Np + p];
-        const float* u = U + ii * dout;
-#pragma unroll
-        for (int t = 0; t < RPW; ++t) {
-          if (t == jj) {
-#pragma unroll
-            for (int k = 0; k < DPL; ++k) {
-              const int d = lane + 32 * k;
-              if (d < dout) acc[t][k] = fmaf(cu, u[d], acc[t][k]);
-            }
-            ct[t] = fmaf(c, sc, ct[t]);
-          }
+    } else {
+      if (k0 >= nq) return;
+      const int p0 = (int)(it.r0 / nv), p1 = (int)min((int64_t)Np - 1, (it.r0 + it.nr - 1) / nv);
+      for (int q = 0; q < 2; ++q) {
+        const int col = lane + 32 * q;
+        const int64_t i = k0 + col;
+        if (i >= nq) continue;
+        const int b = vquery[i];
+        const float cu = vcoef[i] * kinv[i];
+        for (int p = p0; p <= p1; ++p) {
+          int j = amT[(int64_t)p * nq + i];
+          if (j < 0 || j >= nv) j = 0;
+          const int64_t r = (int64_t)p * nv + j;
+          if (r < it.r0 || r >= it.r0 + it.nr) continue;
+          put(a_hi, a_lo, (int)(r - it.r0), col, gS[(int64_t)b * Np + p] * cu);
         }
       }
     }
+  }
+  __device__ __forceinline__ void epi_begin(const Item&, Ctx& x, int, int, uint8_t*) const {
 #pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      const int j = j0 + t;
-      if (j >= nv) continue;
-      const int64_t r = (int64_t)p * nv + j;
-      const float vi = vinv[r];
+    for (int j = 0; j < TN; ++j) x.sum[j] = 0.f;
+  }
+  __device__ __forceinline__ void epi_chunk(const Item&, int, uint32_t taddr, Ctx& x, int, uint8_t*) const {
 #pragma unroll
-      for (int k = 0; k < DPL; ++k) {
-        const int d = lane + 32 * k;
-        if (d < dout) dV[r * dout + d] = vi * (acc[t][k] - ct[t] * V[r * dout + d] * vi);
-      }
+    for (int pc = 0; pc < TN / 32; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
     }
   }
+  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int m, uint8_t*) const {
+    if (m >= it.nr) return;
+    float* crow = C + (it.r0 + m) * N + it.c0;
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+      if (j < it.nc) crow[j] = x.sum[j];
+  }
+};
+
+// argmax [nq, Np] -> shape-major [Np, nq] (32 x 32 tiles through shared memory)
+__global__ void k_transpose_i16(const int16_t* __restrict__ in, int64_t rows, int64_t cols,
+                                int16_t* __restrict__ out) {
+  __shared__ int16_t t[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[k][threadIdx.x] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][k];
+  }
+}
+
+__global__ void k_view_coef(const int32_t* __restrict__ vquery, const int32_t* __restrict__ qoff, int64_t nq,
+                            float* __restrict__ coef) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int b = vquery[i];
+  coef[i] = 1.f / (float)(qoff[b + 1] - qoff[b]);
+}
+
+// out_r = inv_r (g_r - (g_r . x_r inv_r) x_r inv_r): the gradient through x / |x| (warp per row)
+__global__ void k_tangent(const float* __restrict__ X, const float* __restrict__ inv, const float* __restrict__ G,
+                          int64_t n, int dout, float* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const float iv = inv[r];
+  const float* x = X + r * dout;
+  const float* g = G + r * dout;
+  float dot = 0.f;
+  for (int d = lane; d < dout; d += 32) dot = fmaf(x[d], g[d], dot);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  const float t = dot * iv * iv;
+  for (int d = lane; d < dout; d += 32) out[r * dout + d] = iv * (g[d] - t * x[d]);
 }
 
 __global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restrict__ vq) {
@@ -329,45 +363,65 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   int32_t* vquery = sc.get<int32_t>(nq);
   k_view_query<<<(unsigned)Bq, 128, 0, s>>>(d_qoff, vquery);
   GIFT_LAUNCHED("k_view_query");
-  float* sv = sc.get<float>((size_t)nq * Np);
   // gradients w.r.t. the projected views (without a projection these are dQ, dP)
   float* dU = (W || !dQ) ? sc.get<float>((size_t)nq * dout) : dQ;
   float* dV = (W || !dP) ? sc.get<float>((size_t)nr * dout) : dP;
-  const int dpl = (int)cdiv(dout, 32);
-  switch (dpl <= 1 ? 1 : dpl <= 2 ? 2 : dpl <= 4 ? 4 : dpl <= 8 ? 8 : dpl <= 16 ? 16 : dpl <= 32 ? 32 : 0) {
-#define GIFT_GRAD_U(n)                                                                                      \
-  case n:                                                                                                   \
-    k_grad_u<n><<<(unsigned)nq, 256, 0, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, gS, vquery, d_qoff, Np, nv, \
-                                             dout, sv, dU);                                                 \
-    break;
-    GIFT_GRAD_U(1)
-    GIFT_GRAD_U(2)
-    GIFT_GRAD_U(4)
-    GIFT_GRAD_U(8)
-    GIFT_GRAD_U(16)
-    GIFT_GRAD_U(32)
-#undef GIFT_GRAD_U
-    default:
-      fail(GIFT_EINVAL, "d_out must be at most 1024 for the backward");
+  int16_t* amT = sc.get<int16_t>((size_t)nq * Np);
+  k_transpose_i16<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(nq, 32)), dim3(32, 8), 0, s>>>(argmax, nq, Np, amT);
+  GIFT_LAUNCHED("k_transpose_i16");
+  float* vcoef = sc.get<float>(nq);
+  k_view_coef<<<(unsigned)cdiv(nq, 256), 256, 0, s>>>(vquery, d_qoff, nq, vcoef);
+  GIFT_LAUNCHED("k_view_coef");
+  float* G = sc.get<float>((size_t)std::max(nq, nr) * dout);  // G = A V, then H = A^T U
+  const int sms = device_sm_count();
+  {
+    int64_t ldr = 0;
+    const Operand Vt = make_transposed(P.V, GIFT_F32, nr, dout, ldr, sc, s);  // [dout, ldr], K = database views
+    OneHotPolicy<true> pol;
+    pol.M = nq;
+    pol.N = dout;
+    pol.nkb = (int)(ldr / 64);
+    pol.nq = nq;
+    pol.nr = nr;
+    pol.Np = Np;
+    pol.nv = nv;
+    pol.amT = amT;
+    pol.gS = gS;
+    pol.vquery = vquery;
+    pol.vcoef = vcoef;
+    pol.kinv = P.vinv;
+    pol.C = G;
+    const CUtensorMap tB = make_tmap_bf16(Vt.hi, Vt.rows_alloc, ldr, 128);
+    const CUtensorMap tB2 = make_tmap_bf16(Vt.lo, Vt.rows_alloc, ldr, 128);
+    tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nq, tc::kTM) * cdiv(dout, 128)),
+                      s);
+    k_tangent<<<(unsigned)cdiv(nq, 8), 256, 0, s>>>(P.U, P.uinv, G, nq, dout, dU);
+    GIFT_LAUNCHED("k_tangent");
   }
-  GIFT_LAUNCHED("k_grad_u");
-  switch (dpl <= 1 ? 1 : dpl <= 2 ? 2 : dpl <= 4 ? 4 : dpl <= 8 ? 8 : dpl <= 16 ? 16 : dpl <= 32 ? 32 : 0) {
-#define GIFT_GRAD_V(n)                                                                                      \
-  case n:                                                                                                   \
-    k_grad_v<n><<<(unsigned)Np, 512, 0, s>>>(P.U, P.uinv, P.V, P.vinv, argmax, sv, gS, vquery, d_qoff, nq, Np, \
-                                             nv, dout, dV);                                                 \
-    break;
-    GIFT_GRAD_V(1)
-    GIFT_GRAD_V(2)
-    GIFT_GRAD_V(4)
-    GIFT_GRAD_V(8)
-    GIFT_GRAD_V(16)
-    GIFT_GRAD_V(32)
-#undef GIFT_GRAD_V
-    default:
-      fail(GIFT_EINVAL, "d_out must be at most 1024 for the backward");
+  {
+    int64_t ldq = 0;
+    const Operand Ut = make_transposed(P.U, GIFT_F32, nq, dout, ldq, sc, s);  // [dout, ldq], K = query views
+    OneHotPolicy<false> pol;
+    pol.M = nr;
+    pol.N = dout;
+    pol.nkb = (int)(ldq / 64);
+    pol.nq = nq;
+    pol.nr = nr;
+    pol.Np = Np;
+    pol.nv = nv;
+    pol.amT = amT;
+    pol.gS = gS;
+    pol.vquery = vquery;
+    pol.vcoef = vcoef;
+    pol.kinv = P.uinv;
+    pol.C = G;
+    const CUtensorMap tB = make_tmap_bf16(Ut.hi, Ut.rows_alloc, ldq, 128);
+    const CUtensorMap tB2 = make_tmap_bf16(Ut.lo, Ut.rows_alloc, ldq, 128);
+    tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nr, tc::kTM) * cdiv(dout, 128)),
+                      s);
+    k_tangent<<<(unsigned)cdiv(nr, 8), 256, 0, s>>>(P.V, P.vinv, G, nr, dout, dV);
+    GIFT_LAUNCHED("k_tangent");
   }
-  GIFT_LAUNCHED("k_grad_v");
   if (!W) return;
   if (dW) {
     int64_t ldq = 0, ldr = 0;

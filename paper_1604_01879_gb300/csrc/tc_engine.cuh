@@ -28,7 +28,14 @@
 //   void epi_chunk(const Item&, int c, uint32_t taddr, Ctx&, int m, uint8_t* warp_smem) const;
 //   void epi_end(const Item&, Ctx&, int m, uint8_t* warp_smem) const;
 //   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
+// Optionally (GEN_A = true) the A operand is not loaded by TMA but written by
+// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major):
+//   struct GenRegs;                                           (per-lane values of one k-block)
+//   void gen_load(const Item&, int kb, int lane, GenRegs&) const;
+//   void gen_store(const Item&, int kb, int lane, const GenRegs&, uint8_t* a_hi, uint8_t* a_lo) const;
 #pragma once
+#include <type_traits>
+
 #include "tc_common.cuh"
 
 namespace gift {
@@ -37,6 +44,11 @@ namespace tc {
 constexpr int kTM = 128;
 constexpr int kTK = 64;
 constexpr int kEngineThreads = 192;
+
+template <class P, class = void>
+struct gen_a_of : std::false_type {};
+template <class P>
+struct gen_a_of<P, std::void_t<decltype(P::GEN_A)>> : std::integral_constant<bool, P::GEN_A> {};
 
 template <class P>
 struct EngineLayout {
@@ -101,36 +113,43 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   constexpr int KE = L::kKElems;
 
   if (warp == 0) {
-    if (lane == 0) {
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+    if constexpr (gen_a_of<P>::value) {
+      // all lanes write the A tile of every k-block; lane 0 loads B by TMA
+      if (lane == 0) prefetch_tmap(&tmB);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       int last_phase[S];
 #pragma unroll
-      for (int s = 0; s < S; ++s) last_phase[s] = -1;
+      for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
+      constexpr uint32_t kBTx = L::kParts * L::kBBytes;
       for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
         const typename P::Item it = p.decode(item);
-        const int ar = p.a_row(it);
         const int nch = p.nchunks(it);
         for (int c = 0; ok && c < nch; ++c) {
           int br, kb0, kb1;
           p.chunk(it, c, br, kb0, kb1);
           for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer)) {
+            typename P::GenRegs g;
+            p.gen_load(it, kb, lane, g);  // global loads in flight while the stage frees up
+            int w_ok = 1;
+            if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
+            w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+            if (!w_ok) {
               ok = false;
               break;
             }
-            const uint32_t st = smem_u32(tiles + stage * L::kStageBytes);
-            mbar_expect_tx(full0 + 8 * stage, L::kStageBytes);
-            tma_load_2d(st, &tmA, kb * KE, ar, full0 + 8 * stage);
-            tma_load_2d(st + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
-            if (P::SPLIT == 3) {
-              tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * KE, ar, full0 + 8 * stage);
-              tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
+            uint8_t* st = tiles + stage * L::kStageBytes;
+            p.gen_store(it, kb, lane, g, st, st + L::kABytes + L::kBBytes);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              const uint32_t sa = smem_u32(st);
+              mbar_expect_tx(full0 + 8 * stage, kBTx);
+              tma_load_2d(sa + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
+              if (P::SPLIT == 3) tma_load_2d(sa + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
+              last_phase[stage] = (int)phase;
             }
-            last_phase[stage] = (int)phase;
             if (++stage == S) {
               stage = 0;
               phase ^= 1;
@@ -138,16 +157,64 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
           }
         }
       }
-      if (!ok) {
-        for (int s = 0; s < S; ++s) {  // let issued copies land before exiting (bounded)
-          if (last_phase[s] < 0) continue;
+      if (!ok && lane == 0) {
+        for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
+          if (last_phase[s2] < 0) continue;
           const long long t0 = clock64();
-          while (!mbar_try_wait(full0 + 8 * s, (uint32_t)last_phase[s]) && clock64() - t0 < kWaitCycles / 4) {
+          while (!mbar_try_wait(full0 + 8 * s2, (uint32_t)last_phase[s2]) && clock64() - t0 < kWaitCycles / 4) {
           }
         }
       }
+      __syncwarp();
+    } else {
+      if (lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        int last_phase[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) last_phase[s] = -1;
+        for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
+          const typename P::Item it = p.decode(item);
+          const int ar = p.a_row(it);
+          const int nch = p.nchunks(it);
+          for (int c = 0; ok && c < nch; ++c) {
+            int br, kb0, kb1;
+            p.chunk(it, c, br, kb0, kb1);
+            for (int kb = kb0; kb < kb1; ++kb) {
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer)) {
+                ok = false;
+                break;
+              }
+              const uint32_t st = smem_u32(tiles + stage * L::kStageBytes);
+              mbar_expect_tx(full0 + 8 * stage, L::kStageBytes);
+              tma_load_2d(st, &tmA, kb * KE, ar, full0 + 8 * stage);
+              tma_load_2d(st + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
+              if (P::SPLIT == 3) {
+                tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * KE, ar, full0 + 8 * stage);
+                tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
+              }
+              last_phase[stage] = (int)phase;
+              if (++stage == S) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+          }
+        }
+        if (!ok) {
+          for (int s = 0; s < S; ++s) {  // let issued copies land before exiting (bounded)
+            if (last_phase[s] < 0) continue;
+            const long long t0 = clock64();
+            while (!mbar_try_wait(full0 + 8 * s, (uint32_t)last_phase[s]) && clock64() - t0 < kWaitCycles / 4) {
+            }
+          }
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       int stage = 0;
