@@ -91,6 +91,7 @@ struct OneHotPolicy {
   int64_t nq, nr;           // query views, database views
   int Np, nv;               // shapes, views per shape
   const int16_t* amT;       // [Np, nq] argmax view of (i, p), shape-major
+  const float* wT;          // [Np, nq] weight of that non-zero (ROWS_Q: c / |v_r|; else c / |u_i|)
   const float* gS;          // [B, Np]
   const int32_t* vquery;    // [nq] query of each view
   const float* vcoef;       // [nq] 1 / |V(x_b)| of the view's query
@@ -103,7 +104,14 @@ struct OneHotPolicy {
   struct Ctx {
     float sum[TN];
   };
-  struct GenRegs {};
+  // non-zeros of one k-block prefetched by each lane (fast layouts: ROWS_Q with
+  // N_v a multiple of 64, one shape per k-block; !ROWS_Q with N_v >= 64, at most
+  // three shapes per 128-row tile); other layouts gather inside gen_store
+  bool fast;
+  struct GenRegs {
+    int pos[6];   // row * 64 + column in the A tile, -1 = none
+    float w[6];
+  };
   __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
   __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
   __device__ __forceinline__ Item decode(int64_t item) const {
@@ -123,7 +131,62 @@ struct OneHotPolicy {
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
-  __device__ __forceinline__ void gen_load(const Item&, int, int, GenRegs&) const {}
+  __device__ __forceinline__ void gen_load(const Item& it, int kb, int lane, GenRegs& g) const {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) g.pos[e] = -1;
+    if (!fast) return;
+    const int64_t k0 = (int64_t)kb * 64;
+    if (ROWS_Q) {
+      if (k0 >= nr) return;
+      const int p = (int)(k0 / nv);
+      int jj[4];
+      float ww[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // coalesced, independent loads (no shared-memory stores in between)
+        const int row = lane + 32 * q;
+        const int64_t e = (int64_t)p * nq + it.r0 + row;
+        const bool ok = row < it.nr;
+        jj[q] = ok ? amT[e] : -1;
+        ww[q] = ok ? wT[e] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (jj[q] < 0) continue;
+        const int64_t r = (int64_t)p * nv + (jj[q] < nv ? jj[q] : 0);
+        if (r < k0 || r >= k0 + 64) continue;
+        g.pos[q] = (lane + 32 * q) * 64 + (int)(r - k0);
+        g.w[q] = ww[q];
+      }
+    } else {
+      if (k0 >= nq) return;
+      const int p0 = (int)(it.r0 / nv);
+      int jj[6];
+      float ww[6];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t i = k0 + lane + 32 * q;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int64_t e = (int64_t)(p0 + t) * nq + i;
+          const bool ok = i < nq && p0 + t < Np;
+          jj[q * 3 + t] = ok ? amT[e] : -1;
+          ww[q * 3 + t] = ok ? wT[e] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int j = jj[q * 3 + t];
+          if (j < 0) continue;
+          const int64_t r = (int64_t)(p0 + t) * nv + (j < nv ? j : 0);
+          if (r < it.r0 || r >= it.r0 + it.nr) continue;
+          g.pos[q * 3 + t] = (int)(r - it.r0) * 64 + lane + 32 * q;
+          g.w[q * 3 + t] = ww[q * 3 + t];
+        }
+      }
+    }
+  }
   // one non-zero of the A tile, hi and lo parts, 128-byte swizzled K-major layout
   __device__ __forceinline__ static void put(uint8_t* a_hi, uint8_t* a_lo, int row, int col, float w) {
     const __nv_bfloat16 h = __float2bfloat16_rn(w);
@@ -132,7 +195,7 @@ struct OneHotPolicy {
     *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
   }
-  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs&, uint8_t* a_hi,
+  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs& g, uint8_t* a_hi,
                                             uint8_t* a_lo) const {
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     for (int o = lane * 16; o < tc::kTM * 128; o += 32 * 16) {
@@ -140,6 +203,12 @@ struct OneHotPolicy {
       *reinterpret_cast<uint4*>(a_lo + o) = z;
     }
     __syncwarp();
+    if (fast) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        if (g.pos[e] >= 0) put(a_hi, a_lo, g.pos[e] >> 6, g.pos[e] & 63, g.w[e]);
+      return;
+    }
     const int64_t k0 = (int64_t)kb * 64;
     if (ROWS_Q) {
       if (k0 >= nr) return;
@@ -200,19 +269,30 @@ struct OneHotPolicy {
   }
 };
 
-// argmax [nq, Np] -> shape-major [Np, nq] (32 x 32 tiles through shared memory)
-__global__ void k_transpose_i16(const int16_t* __restrict__ in, int64_t rows, int64_t cols,
-                                int16_t* __restrict__ out) {
+// shape-major argmax and one-hot weights: for every (query view i, shape p),
+// j = argmax[i, p], wU = c / |v_{p nv + j}|, wV = c / |u_i| with c = grad_S[b, p] / |V(x_b)|
+__global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, int Np, int nv,
+                              const int32_t* __restrict__ vquery, const float* __restrict__ vcoef,
+                              const float* __restrict__ gS, const float* __restrict__ vinv,
+                              const float* __restrict__ uinv, int16_t* __restrict__ amT, float* __restrict__ wU,
+                              float* __restrict__ wV) {
   __shared__ int16_t t[32][33];
-  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  const int64_t p0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t r = r0 + k, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) t[k][threadIdx.x] = in[r * cols + c];
+    const int64_t i = i0 + k, p = p0 + threadIdx.x;
+    if (i < nq && p < Np) t[k][threadIdx.x] = argmax[i * Np + p];
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t c = c0 + k, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][k];
+    const int64_t p = p0 + k, i = i0 + threadIdx.x;
+    if (i >= nq || p >= Np) continue;
+    int j = t[threadIdx.x][k];
+    const int16_t js = (int16_t)j;
+    if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; stay inside the shape
+    const float c = gS[(int64_t)vquery[i] * Np + p] * vcoef[i];
+    amT[p * nq + i] = js;
+    wU[p * nq + i] = c * vinv[p * nv + j];
+    wV[p * nq + i] = c * uinv[i];
   }
 }
 
@@ -366,12 +446,15 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   // gradients w.r.t. the projected views (without a projection these are dQ, dP)
   float* dU = (W || !dQ) ? sc.get<float>((size_t)nq * dout) : dQ;
   float* dV = (W || !dP) ? sc.get<float>((size_t)nr * dout) : dP;
-  int16_t* amT = sc.get<int16_t>((size_t)nq * Np);
-  k_transpose_i16<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(nq, 32)), dim3(32, 8), 0, s>>>(argmax, nq, Np, amT);
-  GIFT_LAUNCHED("k_transpose_i16");
   float* vcoef = sc.get<float>(nq);
   k_view_coef<<<(unsigned)cdiv(nq, 256), 256, 0, s>>>(vquery, d_qoff, nq, vcoef);
   GIFT_LAUNCHED("k_view_coef");
+  int16_t* amT = sc.get<int16_t>((size_t)nq * Np);
+  float* wU = sc.get<float>((size_t)nq * Np);
+  float* wV = sc.get<float>((size_t)nq * Np);
+  k_onehot_prep<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(nq, 32)), dim3(32, 8), 0, s>>>(
+      argmax, nq, Np, nv, vquery, vcoef, gS, P.vinv, P.uinv, amT, wU, wV);
+  GIFT_LAUNCHED("k_onehot_prep");
   float* G = sc.get<float>((size_t)std::max(nq, nr) * dout);  // G = A V, then H = A^T U
   const int sms = device_sm_count();
   {
@@ -390,7 +473,9 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.vquery = vquery;
     pol.vcoef = vcoef;
     pol.kinv = P.vinv;
+    pol.wT = wU;
     pol.C = G;
+    pol.fast = nv % 64 == 0;
     const CUtensorMap tB = make_tmap_bf16(Vt.hi, Vt.rows_alloc, ldr, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Vt.lo, Vt.rows_alloc, ldr, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nq, tc::kTM) * cdiv(dout, 128)),
@@ -414,7 +499,9 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.vquery = vquery;
     pol.vcoef = vcoef;
     pol.kinv = P.uinv;
+    pol.wT = wV;
     pol.C = G;
+    pol.fast = nv >= 64;
     const CUtensorMap tB = make_tmap_bf16(Ut.hi, Ut.rows_alloc, ldq, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Ut.lo, Ut.rows_alloc, ldq, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nr, tc::kTM) * cdiv(dout, 128)),

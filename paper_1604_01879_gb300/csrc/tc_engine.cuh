@@ -114,8 +114,58 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 
   if (warp == 0) {
     if constexpr (gen_a_of<P>::value) {
-      // all lanes write the A tile of every k-block; lane 0 loads B by TMA
+      // all lanes write the A tile of every k-block, with the loads for the next
+      // two k-blocks in flight; lane 0 loads B by TMA
       if (lane == 0) prefetch_tmap(&tmB);
+      struct Cur {
+        int64_t item;
+        typename P::Item it;
+        int nch, c, kb, kb1, br;
+        bool valid;
+      };
+      auto seek = [&](Cur& x) {  // first k-block at or after x.kb
+        while (x.valid && x.kb >= x.kb1) {
+          if (++x.c < x.nch) {
+            p.chunk(x.it, x.c, x.br, x.kb, x.kb1);
+          } else {
+            x.item += gridDim.x;
+            if (x.item >= total) {
+              x.valid = false;
+            } else {
+              x.it = p.decode(x.item);
+              x.nch = p.nchunks(x.it);
+              x.c = 0;
+              p.chunk(x.it, 0, x.br, x.kb, x.kb1);
+            }
+          }
+        }
+      };
+      Cur c0;
+      c0.item = blockIdx.x;
+      c0.valid = c0.item < total;
+      c0.c = 0;
+      c0.kb = c0.kb1 = 0;
+      c0.nch = 0;
+      c0.br = 0;
+      if (c0.valid) {
+        c0.it = p.decode(c0.item);
+        c0.nch = p.nchunks(c0.it);
+        p.chunk(c0.it, 0, c0.br, c0.kb, c0.kb1);
+        seek(c0);
+      }
+      Cur c1 = c0;
+      if (c1.valid) {
+        ++c1.kb;
+        seek(c1);
+      }
+      Cur c2 = c1;
+      if (c2.valid) {
+        ++c2.kb;
+        seek(c2);
+      }
+      typename P::GenRegs g0, g1, g2;
+      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, g0);
+      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, g1);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -123,38 +173,38 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kParts * L::kBBytes;
-      for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
-        const typename P::Item it = p.decode(item);
-        const int nch = p.nchunks(it);
-        for (int c = 0; ok && c < nch; ++c) {
-          int br, kb0, kb1;
-          p.chunk(it, c, br, kb0, kb1);
-          for (int kb = kb0; kb < kb1; ++kb) {
-            typename P::GenRegs g;
-            p.gen_load(it, kb, lane, g);  // global loads in flight while the stage frees up
-            int w_ok = 1;
-            if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
-            w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-            if (!w_ok) {
-              ok = false;
-              break;
-            }
-            uint8_t* st = tiles + stage * L::kStageBytes;
-            p.gen_store(it, kb, lane, g, st, st + L::kABytes + L::kBBytes);
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              const uint32_t sa = smem_u32(st);
-              mbar_expect_tx(full0 + 8 * stage, kBTx);
-              tma_load_2d(sa + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
-              if (P::SPLIT == 3) tma_load_2d(sa + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
-              last_phase[stage] = (int)phase;
-            }
-            if (++stage == S) {
-              stage = 0;
-              phase ^= 1;
-            }
-          }
+      while (ok && c0.valid) {
+        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, g2);  // two k-blocks ahead
+        int w_ok = 1;
+        if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
+        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+        if (!w_ok) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = tiles + stage * L::kStageBytes;
+        p.gen_store(c0.it, c0.kb, lane, g0, st, st + L::kABytes + L::kBBytes);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          const uint32_t sa = smem_u32(st);
+          mbar_expect_tx(full0 + 8 * stage, kBTx);
+          tma_load_2d(sa + L::kABytes, &tmB, c0.kb * KE, c0.br, full0 + 8 * stage);
+          if (P::SPLIT == 3)
+            tma_load_2d(sa + 2 * L::kABytes + L::kBBytes, &tmB2, c0.kb * KE, c0.br, full0 + 8 * stage);
+          last_phase[stage] = (int)phase;
+        }
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1;
+        }
+        c0 = c1;
+        g0 = g1;
+        c1 = c2;
+        g1 = g2;
+        if (c2.valid) {
+          ++c2.kb;
+          seek(c2);
         }
       }
       if (!ok && lane == 0) {
