@@ -195,8 +195,19 @@ struct OneHotPolicy {
     *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
   }
-  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs& g, uint8_t* a_hi,
-                                            uint8_t* a_lo) const {
+  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs& g, const GenRegs* prev,
+                                            uint8_t* a_hi, uint8_t* a_lo) const {
+    if (fast && prev) {
+      // the tile is zero but for the entries this lane wrote into it last time
+      // (a position belongs to one lane: its row, or its column, is the lane's)
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        if (prev->pos[e] >= 0) put(a_hi, a_lo, prev->pos[e] >> 6, prev->pos[e] & 63, 0.f);
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        if (g.pos[e] >= 0) put(a_hi, a_lo, g.pos[e] >> 6, g.pos[e] & 63, g.w[e]);
+      return;
+    }
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     for (int o = lane * 16; o < tc::kTM * 128; o += 32 * 16) {
       *reinterpret_cast<uint4*>(a_hi + o) = z;

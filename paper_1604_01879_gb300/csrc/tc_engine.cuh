@@ -32,7 +32,8 @@
 // the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major):
 //   struct GenRegs;                                           (per-lane values of one k-block)
 //   void gen_load(const Item&, int kb, int lane, GenRegs&) const;
-//   void gen_store(const Item&, int kb, int lane, const GenRegs&, uint8_t* a_hi, uint8_t* a_lo) const;
+//   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
+//                  uint8_t* a_lo) const;             (prev: what this stage held last time, null on first use)
 #pragma once
 #include <type_traits>
 
@@ -164,6 +165,10 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         seek(c2);
       }
       typename P::GenRegs g0, g1, g2;
+      typename P::GenRegs held[S];  // what each stage's A tile holds (its previous k-block)
+      bool used[S];
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
       if (c0.valid) p.gen_load(c0.it, c0.kb, lane, g0);
       if (c1.valid) p.gen_load(c1.it, c1.kb, lane, g1);
       int stage = 0;
@@ -183,7 +188,9 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
           break;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, lane, g0, st, st + L::kABytes + L::kBBytes);
+        p.gen_store(c0.it, c0.kb, lane, g0, used[stage] ? &held[stage] : nullptr, st, st + L::kABytes + L::kBBytes);
+        held[stage] = g0;
+        used[stage] = true;
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
