@@ -164,13 +164,15 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         ++c2.kb;
         seek(c2);
       }
-      typename P::GenRegs g0, g1, g2;
+      // three register sets rotate by name, so the loads for a k-block are
+      // issued two k-blocks before their values are used (no copies between)
+      typename P::GenRegs ga, gb, gc;
       typename P::GenRegs held[S];  // what each stage's A tile holds (its previous k-block)
       bool used[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
-      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, g0);
-      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, g1);
+      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, ga);
+      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, gb);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -178,18 +180,21 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kParts * L::kBBytes;
-      while (ok && c0.valid) {
-        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, g2);  // two k-blocks ahead
+      // one k-block: prefetch into `fill` for c2, write c0's tile from `use`
+      auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill) -> bool {
+        if (!ok || !c0.valid) return false;
+        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, fill);
         int w_ok = 1;
         if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
         if (!w_ok) {
           ok = false;
-          break;
+          return false;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, lane, g0, used[stage] ? &held[stage] : nullptr, st, st + L::kABytes + L::kBBytes);
-        held[stage] = g0;
+        p.gen_store(c0.it, c0.kb, lane, use, used[stage] ? &held[stage] : nullptr, st,
+                    st + L::kABytes + L::kBBytes);
+        held[stage] = use;
         used[stage] = true;
         fence_proxy_async_smem();
         __syncwarp();
@@ -206,13 +211,14 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
           phase ^= 1;
         }
         c0 = c1;
-        g0 = g1;
         c1 = c2;
-        g1 = g2;
         if (c2.valid) {
           ++c2.kb;
           seek(c2);
         }
+        return true;
+      };
+      while (step(ga, gc) && step(gb, ga) && step(gc, gb)) {
       }
       if (!ok && lane == 0) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
