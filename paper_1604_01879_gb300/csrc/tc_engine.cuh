@@ -29,9 +29,14 @@
 //   void epi_end(const Item&, Ctx&, int m, uint8_t* warp_smem) const;
 //   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
 // Optionally (GEN_A = true) the A operand is not loaded by TMA but written by
-// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major):
+// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major), from
+// per-k-block data that lane 0 brings into a ring of shared-memory slots with
+// 1-D bulk copies kMetaSlots k-blocks ahead:
+//   static constexpr int kMetaBytes;                          (slot size, multiple of 128)
+//   uint32_t meta_issue(const Item&, int kb, uint32_t slot, uint32_t bar) const;  (lane 0; bytes issued)
+//   uint32_t meta_bytes(const Item&, int kb) const;           (bytes meta_issue will issue)
 //   struct GenRegs;                                           (per-lane values of one k-block)
-//   void gen_load(const Item&, int kb, int lane, GenRegs&) const;
+//   void gen_load(const Item&, int kb, int lane, GenRegs&, const uint8_t* slot) const;
 //   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
 //                  uint8_t* a_lo) const;             (prev: what this stage held last time, null on first use)
 #pragma once
@@ -51,6 +56,13 @@ struct gen_a_of : std::false_type {};
 template <class P>
 struct gen_a_of<P, std::void_t<decltype(P::GEN_A)>> : std::integral_constant<bool, P::GEN_A> {};
 
+template <class P, class = void>
+struct meta_bytes_of : std::integral_constant<int, 0> {};
+template <class P>
+struct meta_bytes_of<P, std::void_t<decltype(P::kMetaBytes)>> : std::integral_constant<int, P::kMetaBytes> {};
+
+constexpr int kMetaSlots = 8;
+
 template <class P>
 struct EngineLayout {
   // one k-block = one 128-byte swizzle row of K: 64 BF16 or 128 E4M3 elements
@@ -61,7 +73,9 @@ struct EngineLayout {
   static constexpr int kParts = P::SPLIT == 1 ? 1 : 2;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem;
+  static constexpr int kMetaOff = ((P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem) + 127) & ~127;
+  static constexpr int kSmem = 1024 + kMetaOff + kMetaSlots * meta_bytes_of<P>::value;
+  static_assert(2 * P::STAGES + 2 * P::NBUF + 2 + kMetaSlots <= kBarBytes / 8, "barrier area");
   static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
   static_assert(kSmem <= 232448, "shared memory per CTA");
 };
@@ -80,6 +94,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   uint8_t* tiles = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * L::kStageBytes);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB);
+  uint64_t* meta_bars = bars + 2 * S + 2 * NB + 2;  // generated-A data slots
+  uint8_t* meta_smem = smem + L::kMetaOff;
   uint8_t* wsm = smem + S * L::kStageBytes + L::kBarBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -99,6 +115,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       mbar_init(tfull0 + 8 * b, 1);
       mbar_init(tempty0 + 8 * b, 4);
     }
+    if constexpr (gen_a_of<P>::value)
+      for (int m = 0; m < kMetaSlots; ++m) mbar_init(smem_u32(meta_bars + m), 1);
     fence_barrier_init();
   }
   if (warp == 0) {
@@ -115,8 +133,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 
   if (warp == 0) {
     if constexpr (gen_a_of<P>::value) {
-      // all lanes write the A tile of every k-block, with the loads for the next
-      // two k-blocks in flight; lane 0 loads B by TMA
+      // all lanes write the A tile of every k-block from its data slot; lane 0
+      // keeps the slots filled ahead and loads B by TMA
       if (lane == 0) prefetch_tmap(&tmB);
       struct Cur {
         int64_t item;
@@ -154,25 +172,11 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         p.chunk(c0.it, 0, c0.br, c0.kb, c0.kb1);
         seek(c0);
       }
-      Cur c1 = c0;
-      if (c1.valid) {
-        ++c1.kb;
-        seek(c1);
-      }
-      Cur c2 = c1;
-      if (c2.valid) {
-        ++c2.kb;
-        seek(c2);
-      }
-      // three register sets rotate by name, so the loads for a k-block are
-      // issued two k-blocks before their values are used (no copies between)
-      typename P::GenRegs ga, gb, gc;
+      typename P::GenRegs g;
       typename P::GenRegs held[S];  // what each stage's A tile holds (its previous k-block)
       bool used[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
-      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, ga);
-      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, gb);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -180,21 +184,51 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kParts * L::kBBytes;
-      // one k-block: prefetch into `fill` for c2, write c0's tile from `use`
-      auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill) -> bool {
-        if (!ok || !c0.valid) return false;
-        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, fill);
+      constexpr int kMB = meta_bytes_of<P>::value;
+      int meta_last[kMetaSlots];  // parity of the last fill of each slot (-1: none in flight)
+#pragma unroll
+      for (int m = 0; m < kMetaSlots; ++m) meta_last[m] = -1;
+      // the data of k-block number q (in this CTA's order) goes to slot q % kMetaSlots
+      Cur cm = c0;
+      int64_t q_issue = 0;
+      auto issue = [&]() {
+        if (!cm.valid) return;
+        const int slot = (int)(q_issue % kMetaSlots);
+        const uint32_t bar = smem_u32(meta_bars + slot);
+        if (lane == 0) {
+          mbar_expect_tx(bar, p.meta_bytes(cm.it, cm.kb));
+          p.meta_issue(cm.it, cm.kb, smem_u32(meta_smem + slot * kMB), bar);
+        }
+        meta_last[slot] = (int)((q_issue / kMetaSlots) & 1);
+        ++q_issue;
+        ++cm.kb;
+        seek(cm);
+      };
+      for (int m = 0; m < kMetaSlots; ++m) issue();
+      int64_t q = 0;
+      while (ok && c0.valid) {
+        const int slot = (int)(q % kMetaSlots);
+        if (!mbar_wait(smem_u32(meta_bars + slot), (uint32_t)((q / kMetaSlots) & 1), err, kErrProducer)) {
+          ok = false;
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        p.gen_load(c0.it, c0.kb, lane, g, meta_smem + slot * kMB);
+        __syncwarp();  // every lane has read the slot
+        meta_last[slot] = -1;
+        issue();  // refill the slot just read, kMetaSlots k-blocks ahead
         int w_ok = 1;
         if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
         if (!w_ok) {
           ok = false;
-          return false;
+          break;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, lane, use, used[stage] ? &held[stage] : nullptr, st,
-                    st + L::kABytes + L::kBBytes);
-        held[stage] = use;
+        p.gen_store(c0.it, c0.kb, lane, g, used[stage] ? &held[stage] : nullptr, st, st + L::kABytes + L::kBBytes);
+        held[stage] = g;
         used[stage] = true;
         fence_proxy_async_smem();
         __syncwarp();
@@ -210,15 +244,17 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
           stage = 0;
           phase ^= 1;
         }
-        c0 = c1;
-        c1 = c2;
-        if (c2.valid) {
-          ++c2.kb;
-          seek(c2);
+        ++q;
+        ++c0.kb;
+        seek(c0);
+      }
+      if (lane == 0) {  // data copies still in flight land before the CTA exits (bounded)
+        for (int m = 0; m < kMetaSlots; ++m) {
+          if (meta_last[m] < 0) continue;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(smem_u32(meta_bars + m), (uint32_t)meta_last[m]) && clock64() - t0 < kWaitCycles / 4) {
+          }
         }
-        return true;
-      };
-      while (step(ga, gc) && step(gb, ga) && step(gc, gb)) {
       }
       if (!ok && lane == 0) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
