@@ -134,32 +134,50 @@ struct OneHotPolicy {
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
-  __device__ __forceinline__ uint32_t meta_bytes(const Item& it, int kb) const {
-    if (!meta) return 0;
+  // loader warp: the k-block's argmax and weights, global -> shared slot
+  __device__ __forceinline__ void meta_fill(const Item& it, int kb, int lane, uint8_t* slot) const {
+    if (!meta) return;
     const int64_t k0 = (int64_t)kb * 64;
-    if (ROWS_Q) return k0 < nr ? 768u : 0u;
-    if (k0 >= nq) return 0;
-    const int p0 = (int)(it.r0 / nv);
-    const int ns = min(3, Np - p0);
-    return (uint32_t)(ns * 384);
-  }
-  __device__ __forceinline__ uint32_t meta_issue(const Item& it, int kb, uint32_t slot, uint32_t bar) const {
-    const uint32_t n = meta_bytes(it, kb);
-    if (n == 0) return 0;
-    const int64_t k0 = (int64_t)kb * 64;
+    int16_t* s_am = reinterpret_cast<int16_t*>(slot);
     if (ROWS_Q) {
-      const int64_t e = (int64_t)(k0 / nv) * nq + it.r0;
-      tc::bulk_load(slot, amT + e, 256, bar);
-      tc::bulk_load(slot + 256, wT + e, 512, bar);
-    } else {
-      const int p0 = (int)(it.r0 / nv);
-      for (int t = 0; t < (int)(n / 384); ++t) {
-        const int64_t e = (int64_t)(p0 + t) * nq + k0;
-        tc::bulk_load(slot + t * 128, amT + e, 128, bar);
-        tc::bulk_load(slot + 384 + t * 256, wT + e, 256, bar);
+      if (k0 >= nr) return;
+      const int64_t e0 = (int64_t)(k0 / nv) * nq + it.r0;
+      float* s_w = reinterpret_cast<float*>(slot + 256);
+      int16_t j[4];
+      float w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        j[q] = amT[e0 + lane + 32 * q];
+        w[q] = wT[e0 + lane + 32 * q];
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s_am[lane + 32 * q] = j[q];
+        s_w[lane + 32 * q] = w[q];
+      }
+    } else {
+      if (k0 >= nq) return;
+      const int p0 = (int)(it.r0 / nv);
+      float* s_w = reinterpret_cast<float*>(slot + 384);
+      int16_t j[6];
+      float w[6];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const bool ok = p0 + t < Np;
+          const int64_t e = (int64_t)(p0 + t) * nq + k0 + lane + 32 * q;
+          j[t * 2 + q] = ok ? amT[e] : (int16_t)-1;
+          w[t * 2 + q] = ok ? wT[e] : 0.f;
+        }
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          s_am[t * 64 + lane + 32 * q] = j[t * 2 + q];
+          s_w[t * 64 + lane + 32 * q] = w[t * 2 + q];
+        }
     }
-    return n;
   }
   __device__ __forceinline__ void gen_load(const Item& it, int kb, int lane, GenRegs& g, const uint8_t* slot) const {
 #pragma unroll

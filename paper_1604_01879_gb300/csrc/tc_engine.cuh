@@ -30,11 +30,11 @@
 //   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
 // Optionally (GEN_A = true) the A operand is not loaded by TMA but written by
 // the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major), from
-// per-k-block data that lane 0 brings into a ring of shared-memory slots with
-// 1-D bulk copies kMetaSlots k-blocks ahead:
+// per-k-block data that a seventh warp (the loader) reads from global memory
+// into a ring of kMetaSlots shared-memory slots ahead of use; warp 0 then
+// touches no global memory, so its proxy fences never wait on loads:
 //   static constexpr int kMetaBytes;                          (slot size, multiple of 128)
-//   uint32_t meta_issue(const Item&, int kb, uint32_t slot, uint32_t bar) const;  (lane 0; bytes issued)
-//   uint32_t meta_bytes(const Item&, int kb) const;           (bytes meta_issue will issue)
+//   void meta_fill(const Item&, int kb, int lane, uint8_t* slot) const;   (loader warp, all lanes)
 //   struct GenRegs;                                           (per-lane values of one k-block)
 //   void gen_load(const Item&, int kb, int lane, GenRegs&, const uint8_t* slot) const;
 //   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
@@ -49,7 +49,7 @@ namespace tc {
 
 constexpr int kTM = 128;
 constexpr int kTK = 64;
-constexpr int kEngineThreads = 192;
+constexpr int kEngineThreads = 192;  // + one loader warp for generated A operands
 
 template <class P, class = void>
 struct gen_a_of : std::false_type {};
@@ -75,13 +75,15 @@ struct EngineLayout {
   static constexpr int kBarBytes = 256;
   static constexpr int kMetaOff = ((P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem) + 127) & ~127;
   static constexpr int kSmem = 1024 + kMetaOff + kMetaSlots * meta_bytes_of<P>::value;
-  static_assert(2 * P::STAGES + 2 * P::NBUF + 2 + kMetaSlots <= kBarBytes / 8, "barrier area");
+  static_assert(2 * P::STAGES + 2 * P::NBUF + 2 + (gen_a_of<P>::value ? 2 * kMetaSlots : 0) <= kBarBytes / 8,
+                "barrier area");
+  static constexpr int kThreads = gen_a_of<P>::value ? kEngineThreads + 32 : kEngineThreads;
   static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
   static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
 template <class P>
-__global__ void __launch_bounds__(kEngineThreads, 1)
+__global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
     tc_engine(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const P p,
               int* err) {
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   uint8_t* tiles = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * L::kStageBytes);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB);
-  uint64_t* meta_bars = bars + 2 * S + 2 * NB + 2;  // generated-A data slots
+  uint64_t* meta_bars = bars + 2 * S + 2 * NB + 2;  // generated-A data slots: full [kMetaSlots], empty [kMetaSlots]
   uint8_t* meta_smem = smem + L::kMetaOff;
   uint8_t* wsm = smem + S * L::kStageBytes + L::kBarBytes;
 
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       mbar_init(tempty0 + 8 * b, 4);
     }
     if constexpr (gen_a_of<P>::value)
-      for (int m = 0; m < kMetaSlots; ++m) mbar_init(smem_u32(meta_bars + m), 1);
+      for (int m = 0; m < 2 * kMetaSlots; ++m) mbar_init(smem_u32(meta_bars + m), 1);
     fence_barrier_init();
   }
   if (warp == 0) {
@@ -185,40 +187,18 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kParts * L::kBBytes;
       constexpr int kMB = meta_bytes_of<P>::value;
-      int meta_last[kMetaSlots];  // parity of the last fill of each slot (-1: none in flight)
-#pragma unroll
-      for (int m = 0; m < kMetaSlots; ++m) meta_last[m] = -1;
-      // the data of k-block number q (in this CTA's order) goes to slot q % kMetaSlots
-      Cur cm = c0;
-      int64_t q_issue = 0;
-      auto issue = [&]() {
-        if (!cm.valid) return;
-        const int slot = (int)(q_issue % kMetaSlots);
-        const uint32_t bar = smem_u32(meta_bars + slot);
-        if (lane == 0) {
-          mbar_expect_tx(bar, p.meta_bytes(cm.it, cm.kb));
-          p.meta_issue(cm.it, cm.kb, smem_u32(meta_smem + slot * kMB), bar);
-        }
-        meta_last[slot] = (int)((q_issue / kMetaSlots) & 1);
-        ++q_issue;
-        ++cm.kb;
-        seek(cm);
-      };
-      for (int m = 0; m < kMetaSlots; ++m) issue();
       int64_t q = 0;
       while (ok && c0.valid) {
         const int slot = (int)(q % kMetaSlots);
-        if (!mbar_wait(smem_u32(meta_bars + slot), (uint32_t)((q / kMetaSlots) & 1), err, kErrProducer)) {
-          ok = false;
-        }
+        // the loader's data for this k-block (every lane acquires it)
+        if (!mbar_wait(smem_u32(meta_bars + slot), (uint32_t)((q / kMetaSlots) & 1), err, kErrProducer)) ok = false;
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
           break;
         }
         p.gen_load(c0.it, c0.kb, lane, g, meta_smem + slot * kMB);
         __syncwarp();  // every lane has read the slot
-        meta_last[slot] = -1;
-        issue();  // refill the slot just read, kMetaSlots k-blocks ahead
+        if (lane == 0) mbar_arrive(smem_u32(meta_bars + kMetaSlots + slot));
         int w_ok = 1;
         if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
@@ -247,14 +227,6 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         ++q;
         ++c0.kb;
         seek(c0);
-      }
-      if (lane == 0) {  // data copies still in flight land before the CTA exits (bounded)
-        for (int m = 0; m < kMetaSlots; ++m) {
-          if (meta_last[m] < 0) continue;
-          const long long t0 = clock64();
-          while (!mbar_try_wait(smem_u32(meta_bars + m), (uint32_t)meta_last[m]) && clock64() - t0 < kWaitCycles / 4) {
-          }
-        }
       }
       if (!ok && lane == 0) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
@@ -313,6 +285,34 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         }
       }
       __syncwarp();
+    }
+  } else if (gen_a_of<P>::value && warp == kEngineThreads / 32) {
+    if constexpr (gen_a_of<P>::value) {
+      // loader: fills data slot q % kMetaSlots for the q-th k-block of this CTA
+      constexpr int kMB = meta_bytes_of<P>::value;
+      int64_t q = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
+        const typename P::Item it = p.decode(item);
+        const int nch = p.nchunks(it);
+        for (int c = 0; ok && c < nch; ++c) {
+          int br, kb0, kb1;
+          p.chunk(it, c, br, kb0, kb1);
+          for (int kb = kb0; kb < kb1; ++kb, ++q) {
+            const int slot = (int)(q % kMetaSlots);
+            if (!mbar_wait(smem_u32(meta_bars + kMetaSlots + slot), (uint32_t)(((q / kMetaSlots) & 1) ^ 1), err,
+                           kErrProducer))
+              ok = false;
+            if (!__all_sync(0xffffffffu, ok)) {
+              ok = false;
+              break;
+            }
+            p.meta_fill(it, kb, lane, meta_smem + slot * kMB);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(meta_bars + slot));
+          }
+        }
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -421,7 +421,7 @@ void launch_engine(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap
                    const P& p, int* err, int grid, cudaStream_t s) {
   using L = EngineLayout<P>;
   GIFT_CUDA(cudaFuncSetAttribute(tc_engine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem));
-  tc_engine<P><<<grid, kEngineThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
+  tc_engine<P><<<grid, L::kThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
   GIFT_LAUNCHED("tc_engine");
 }
 
