@@ -134,48 +134,59 @@ struct OneHotPolicy {
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
-  // loader warp: the k-block's argmax and weights, global -> shared slot
-  __device__ __forceinline__ void meta_fill(const Item& it, int kb, int lane, uint8_t* slot) const {
+  // loader warp: the k-block's argmax and weights, global -> registers -> shared slot
+  struct MetaRegs {
+    int16_t j[6];
+    float w[6];
+  };
+  __device__ __forceinline__ void meta_load(const Item& it, int kb, int lane, MetaRegs& m) const {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      m.j[e] = -1;
+      m.w[e] = 0.f;
+    }
     if (!meta) return;
     const int64_t k0 = (int64_t)kb * 64;
-    int16_t* s_am = reinterpret_cast<int16_t*>(slot);
     if (ROWS_Q) {
       if (k0 >= nr) return;
       const int64_t e0 = (int64_t)(k0 / nv) * nq + it.r0;
-      float* s_w = reinterpret_cast<float*>(slot + 256);
-      int16_t j[4];
-      float w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        j[q] = amT[e0 + lane + 32 * q];
-        w[q] = wT[e0 + lane + 32 * q];
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        s_am[lane + 32 * q] = j[q];
-        s_w[lane + 32 * q] = w[q];
+        m.j[q] = amT[e0 + lane + 32 * q];
+        m.w[q] = wT[e0 + lane + 32 * q];
       }
     } else {
       if (k0 >= nq) return;
       const int p0 = (int)(it.r0 / nv);
-      float* s_w = reinterpret_cast<float*>(slot + 384);
-      int16_t j[6];
-      float w[6];
 #pragma unroll
       for (int t = 0; t < 3; ++t)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const bool ok = p0 + t < Np;
+          if (p0 + t >= Np) continue;
           const int64_t e = (int64_t)(p0 + t) * nq + k0 + lane + 32 * q;
-          j[t * 2 + q] = ok ? amT[e] : (int16_t)-1;
-          w[t * 2 + q] = ok ? wT[e] : 0.f;
+          m.j[t * 2 + q] = amT[e];
+          m.w[t * 2 + q] = wT[e];
         }
+    }
+  }
+  __device__ __forceinline__ void meta_store(int lane, const MetaRegs& m, uint8_t* slot) const {
+    if (!meta) return;
+    int16_t* s_am = reinterpret_cast<int16_t*>(slot);
+    if (ROWS_Q) {
+      float* s_w = reinterpret_cast<float*>(slot + 256);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s_am[lane + 32 * q] = m.j[q];
+        s_w[lane + 32 * q] = m.w[q];
+      }
+    } else {
+      float* s_w = reinterpret_cast<float*>(slot + 384);
 #pragma unroll
       for (int t = 0; t < 3; ++t)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          s_am[t * 64 + lane + 32 * q] = j[t * 2 + q];
-          s_w[t * 64 + lane + 32 * q] = w[t * 2 + q];
+          s_am[t * 64 + lane + 32 * q] = m.j[t * 2 + q];
+          s_w[t * 64 + lane + 32 * q] = m.w[t * 2 + q];
         }
     }
   }

@@ -34,7 +34,9 @@
 // into a ring of kMetaSlots shared-memory slots ahead of use; warp 0 then
 // touches no global memory, so its proxy fences never wait on loads:
 //   static constexpr int kMetaBytes;                          (slot size, multiple of 128)
-//   void meta_fill(const Item&, int kb, int lane, uint8_t* slot) const;   (loader warp, all lanes)
+//   struct MetaRegs;  void meta_load(const Item&, int kb, int lane, MetaRegs&) const;
+//   void meta_store(int lane, const MetaRegs&, uint8_t* slot) const;     (loader warp, all lanes;
+//                                        the loads of kMetaGroup k-blocks are in flight together)
 //   struct GenRegs;                                           (per-lane values of one k-block)
 //   void gen_load(const Item&, int kb, int lane, GenRegs&, const uint8_t* slot) const;
 //   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
@@ -62,6 +64,7 @@ template <class P>
 struct meta_bytes_of<P, std::void_t<decltype(P::kMetaBytes)>> : std::integral_constant<int, P::kMetaBytes> {};
 
 constexpr int kMetaSlots = 8;
+constexpr int kMetaGroup = 4;  // k-blocks whose data the loader fetches at once
 
 template <class P>
 struct EngineLayout {
@@ -288,30 +291,75 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
     }
   } else if (gen_a_of<P>::value && warp == kEngineThreads / 32) {
     if constexpr (gen_a_of<P>::value) {
-      // loader: fills data slot q % kMetaSlots for the q-th k-block of this CTA
+      // loader: fills data slot q % kMetaSlots for the q-th k-block of this CTA,
+      // kMetaGroup k-blocks at a time (their loads overlap)
       constexpr int kMB = meta_bytes_of<P>::value;
-      int64_t q = 0;
-      bool ok = true;
-      for (int64_t item = blockIdx.x; ok && item < total; item += gridDim.x) {
-        const typename P::Item it = p.decode(item);
-        const int nch = p.nchunks(it);
-        for (int c = 0; ok && c < nch; ++c) {
-          int br, kb0, kb1;
-          p.chunk(it, c, br, kb0, kb1);
-          for (int kb = kb0; kb < kb1; ++kb, ++q) {
-            const int slot = (int)(q % kMetaSlots);
-            if (!mbar_wait(smem_u32(meta_bars + kMetaSlots + slot), (uint32_t)(((q / kMetaSlots) & 1) ^ 1), err,
-                           kErrProducer))
-              ok = false;
-            if (!__all_sync(0xffffffffu, ok)) {
-              ok = false;
-              break;
+      struct Cur {
+        int64_t item;
+        typename P::Item it;
+        int nch, c, kb, kb1, br;
+        bool valid;
+      };
+      auto seek = [&](Cur& x) {
+        while (x.valid && x.kb >= x.kb1) {
+          if (++x.c < x.nch) {
+            p.chunk(x.it, x.c, x.br, x.kb, x.kb1);
+          } else {
+            x.item += gridDim.x;
+            if (x.item >= total) {
+              x.valid = false;
+            } else {
+              x.it = p.decode(x.item);
+              x.nch = p.nchunks(x.it);
+              x.c = 0;
+              p.chunk(x.it, 0, x.br, x.kb, x.kb1);
             }
-            p.meta_fill(it, kb, lane, meta_smem + slot * kMB);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(meta_bars + slot));
           }
         }
+      };
+      Cur cur;
+      cur.item = blockIdx.x;
+      cur.valid = cur.item < total;
+      cur.c = cur.kb = cur.kb1 = cur.nch = cur.br = 0;
+      if (cur.valid) {
+        cur.it = p.decode(cur.item);
+        cur.nch = p.nchunks(cur.it);
+        p.chunk(cur.it, 0, cur.br, cur.kb, cur.kb1);
+        seek(cur);
+      }
+      int64_t q = 0;
+      bool ok = true;
+      while (ok && cur.valid) {
+        typename P::MetaRegs r[kMetaGroup];
+        int n = 0;
+#pragma unroll
+        for (int g = 0; g < kMetaGroup; ++g) {
+          if (!cur.valid) break;
+          const int64_t qq = q + g;
+          const int slot = (int)(qq % kMetaSlots);
+          if (!mbar_wait(smem_u32(meta_bars + kMetaSlots + slot), (uint32_t)(((qq / kMetaSlots) & 1) ^ 1), err,
+                         kErrProducer))
+            ok = false;
+          if (!__all_sync(0xffffffffu, ok)) {
+            ok = false;
+            break;
+          }
+          p.meta_load(cur.it, cur.kb, lane, r[g]);
+          ++n;
+          ++cur.kb;
+          seek(cur);
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int g = 0; g < kMetaGroup; ++g) {
+          if (g >= n) break;
+          const int slot = (int)((q + g) % kMetaSlots);
+          p.meta_store(lane, r[g], meta_smem + slot * kMB);
+        }
+        __syncwarp();
+        if (lane == 0)
+          for (int g = 0; g < n; ++g) mbar_arrive(smem_u32(meta_bars + (int)((q + g) % kMetaSlots)));
+        q += n;
       }
     }
   } else if (warp == 1) {
