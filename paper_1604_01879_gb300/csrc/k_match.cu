@@ -104,13 +104,10 @@ struct OneHotPolicy {
   struct Ctx {
     float sum[TN];
   };
-  // non-zeros of one k-block read by each lane (fast layouts: ROWS_Q with N_v a
-  // multiple of 64, one shape per k-block; !ROWS_Q with N_v >= 64, at most three
-  // shapes per 128-row tile); other layouts gather inside gen_store. With meta,
-  // the k-block's argmax and weights arrive in a shared-memory slot by bulk copy
-  // (ROWS_Q: 128 rows of one shape; else 64 columns of up to three shapes).
-  bool fast, meta;
-  static constexpr int kMetaBytes = 1152;
+  // non-zeros of one k-block prefetched by each lane (fast layouts: ROWS_Q with
+  // N_v a multiple of 64, one shape per k-block; !ROWS_Q with N_v >= 64, at most
+  // three shapes per 128-row tile); other layouts gather inside gen_store
+  bool fast;
   struct GenRegs {
     int pos[6];   // row * 64 + column in the A tile, -1 = none
     float w[6];
@@ -134,81 +131,23 @@ struct OneHotPolicy {
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
-  // loader warp: the k-block's argmax and weights, global -> registers -> shared slot
-  struct MetaRegs {
-    int16_t j[6];
-    float w[6];
-  };
-  __device__ __forceinline__ void meta_load(const Item& it, int kb, int lane, MetaRegs& m) const {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      m.j[e] = -1;
-      m.w[e] = 0.f;
-    }
-    if (!meta) return;
-    const int64_t k0 = (int64_t)kb * 64;
-    if (ROWS_Q) {
-      if (k0 >= nr) return;
-      const int64_t e0 = (int64_t)(k0 / nv) * nq + it.r0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        m.j[q] = amT[e0 + lane + 32 * q];
-        m.w[q] = wT[e0 + lane + 32 * q];
-      }
-    } else {
-      if (k0 >= nq) return;
-      const int p0 = (int)(it.r0 / nv);
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (p0 + t >= Np) continue;
-          const int64_t e = (int64_t)(p0 + t) * nq + k0 + lane + 32 * q;
-          m.j[t * 2 + q] = amT[e];
-          m.w[t * 2 + q] = wT[e];
-        }
-    }
-  }
-  __device__ __forceinline__ void meta_store(int lane, const MetaRegs& m, uint8_t* slot) const {
-    if (!meta) return;
-    int16_t* s_am = reinterpret_cast<int16_t*>(slot);
-    if (ROWS_Q) {
-      float* s_w = reinterpret_cast<float*>(slot + 256);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        s_am[lane + 32 * q] = m.j[q];
-        s_w[lane + 32 * q] = m.w[q];
-      }
-    } else {
-      float* s_w = reinterpret_cast<float*>(slot + 384);
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          s_am[t * 64 + lane + 32 * q] = m.j[t * 2 + q];
-          s_w[t * 64 + lane + 32 * q] = m.w[t * 2 + q];
-        }
-    }
-  }
-  __device__ __forceinline__ void gen_load(const Item& it, int kb, int lane, GenRegs& g, const uint8_t* slot) const {
+  __device__ __forceinline__ void gen_load(const Item& it, int kb, int lane, GenRegs& g) const {
 #pragma unroll
     for (int e = 0; e < 6; ++e) g.pos[e] = -1;
     if (!fast) return;
     const int64_t k0 = (int64_t)kb * 64;
-    const int16_t* s_am = reinterpret_cast<const int16_t*>(slot);
     if (ROWS_Q) {
       if (k0 >= nr) return;
       const int p = (int)(k0 / nv);
-      const float* s_w = reinterpret_cast<const float*>(slot + 256);
       int jj[4];
       float ww[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 4; ++q) {  // coalesced, independent loads (no shared-memory stores in between)
         const int row = lane + 32 * q;
         const int64_t e = (int64_t)p * nq + it.r0 + row;
         const bool ok = row < it.nr;
-        jj[q] = !ok ? -1 : meta ? s_am[row] : amT[e];
-        ww[q] = !ok ? 0.f : meta ? s_w[row] : wT[e];
+        jj[q] = ok ? amT[e] : -1;
+        ww[q] = ok ? wT[e] : 0.f;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -221,19 +160,17 @@ struct OneHotPolicy {
     } else {
       if (k0 >= nq) return;
       const int p0 = (int)(it.r0 / nv);
-      const float* s_w = reinterpret_cast<const float*>(slot + 384);
       int jj[6];
       float ww[6];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int col = lane + 32 * q;
-        const int64_t i = k0 + col;
+        const int64_t i = k0 + lane + 32 * q;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           const int64_t e = (int64_t)(p0 + t) * nq + i;
           const bool ok = i < nq && p0 + t < Np;
-          jj[q * 3 + t] = !ok ? -1 : meta ? s_am[t * 64 + col] : amT[e];
-          ww[q * 3 + t] = !ok ? 0.f : meta ? s_w[t * 64 + col] : wT[e];
+          jj[q * 3 + t] = ok ? amT[e] : -1;
+          ww[q * 3 + t] = ok ? wT[e] : 0.f;
         }
       }
 #pragma unroll
@@ -550,7 +487,6 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.wT = wU;
     pol.C = G;
     pol.fast = nv % 64 == 0;
-    pol.meta = pol.fast && nq % 128 == 0;
     const CUtensorMap tB = make_tmap_bf16(Vt.hi, Vt.rows_alloc, ldr, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Vt.lo, Vt.rows_alloc, ldr, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nq, tc::kTM) * cdiv(dout, 128)),
@@ -577,7 +513,6 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.wT = wV;
     pol.C = G;
     pol.fast = nv >= 64;
-    pol.meta = pol.fast && nq % 64 == 0;
     const CUtensorMap tB = make_tmap_bf16(Ut.hi, Ut.rows_alloc, ldq, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Ut.lo, Ut.rows_alloc, ldq, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nr, tc::kTM) * cdiv(dout, 128)),

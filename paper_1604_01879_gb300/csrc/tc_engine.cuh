@@ -29,16 +29,9 @@
 //   void epi_end(const Item&, Ctx&, int m, uint8_t* warp_smem) const;
 //   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
 // Optionally (GEN_A = true) the A operand is not loaded by TMA but written by
-// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major), from
-// per-k-block data that a seventh warp (the loader) reads from global memory
-// into a ring of kMetaSlots shared-memory slots ahead of use; warp 0 then
-// touches no global memory, so its proxy fences never wait on loads:
-//   static constexpr int kMetaBytes;                          (slot size, multiple of 128)
-//   struct MetaRegs;  void meta_load(const Item&, int kb, int lane, MetaRegs&) const;
-//   void meta_store(int lane, const MetaRegs&, uint8_t* slot) const;     (loader warp, all lanes;
-//                                        the loads of kMetaGroup k-blocks are in flight together)
+// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major):
 //   struct GenRegs;                                           (per-lane values of one k-block)
-//   void gen_load(const Item&, int kb, int lane, GenRegs&, const uint8_t* slot) const;
+//   void gen_load(const Item&, int kb, int lane, GenRegs&) const;
 //   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
 //                  uint8_t* a_lo) const;             (prev: what this stage held last time, null on first use)
 #pragma once
@@ -51,20 +44,12 @@ namespace tc {
 
 constexpr int kTM = 128;
 constexpr int kTK = 64;
-constexpr int kEngineThreads = 192;  // + one loader warp for generated A operands
+constexpr int kEngineThreads = 192;
 
 template <class P, class = void>
 struct gen_a_of : std::false_type {};
 template <class P>
 struct gen_a_of<P, std::void_t<decltype(P::GEN_A)>> : std::integral_constant<bool, P::GEN_A> {};
-
-template <class P, class = void>
-struct meta_bytes_of : std::integral_constant<int, 0> {};
-template <class P>
-struct meta_bytes_of<P, std::void_t<decltype(P::kMetaBytes)>> : std::integral_constant<int, P::kMetaBytes> {};
-
-constexpr int kMetaSlots = 8;
-constexpr int kMetaGroup = 4;  // k-blocks whose data the loader fetches at once
 
 template <class P>
 struct EngineLayout {
@@ -76,17 +61,13 @@ struct EngineLayout {
   static constexpr int kParts = P::SPLIT == 1 ? 1 : 2;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kBarBytes = 256;
-  static constexpr int kMetaOff = ((P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem) + 127) & ~127;
-  static constexpr int kSmem = 1024 + kMetaOff + kMetaSlots * meta_bytes_of<P>::value;
-  static_assert(2 * P::STAGES + 2 * P::NBUF + 2 + (gen_a_of<P>::value ? 2 * kMetaSlots : 0) <= kBarBytes / 8,
-                "barrier area");
-  static constexpr int kThreads = gen_a_of<P>::value ? kEngineThreads + 32 : kEngineThreads;
+  static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem;
   static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
   static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
 template <class P>
-__global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
+__global__ void __launch_bounds__(kEngineThreads, 1)
     tc_engine(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const P p,
               int* err) {
@@ -99,8 +80,6 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
   uint8_t* tiles = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * L::kStageBytes);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB);
-  uint64_t* meta_bars = bars + 2 * S + 2 * NB + 2;  // generated-A data slots: full [kMetaSlots], empty [kMetaSlots]
-  uint8_t* meta_smem = smem + L::kMetaOff;
   uint8_t* wsm = smem + S * L::kStageBytes + L::kBarBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,8 +99,6 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
       mbar_init(tfull0 + 8 * b, 1);
       mbar_init(tempty0 + 8 * b, 4);
     }
-    if constexpr (gen_a_of<P>::value)
-      for (int m = 0; m < 2 * kMetaSlots; ++m) mbar_init(smem_u32(meta_bars + m), 1);
     fence_barrier_init();
   }
   if (warp == 0) {
@@ -138,8 +115,8 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
 
   if (warp == 0) {
     if constexpr (gen_a_of<P>::value) {
-      // all lanes write the A tile of every k-block from its data slot; lane 0
-      // keeps the slots filled ahead and loads B by TMA
+      // all lanes write the A tile of every k-block, with the loads for the next
+      // two k-blocks in flight; lane 0 loads B by TMA
       if (lane == 0) prefetch_tmap(&tmB);
       struct Cur {
         int64_t item;
@@ -177,11 +154,25 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
         p.chunk(c0.it, 0, c0.br, c0.kb, c0.kb1);
         seek(c0);
       }
-      typename P::GenRegs g;
+      Cur c1 = c0;
+      if (c1.valid) {
+        ++c1.kb;
+        seek(c1);
+      }
+      Cur c2 = c1;
+      if (c2.valid) {
+        ++c2.kb;
+        seek(c2);
+      }
+      // three register sets rotate by name, so the loads for a k-block are
+      // issued two k-blocks before their values are used (no copies between)
+      typename P::GenRegs ga, gb, gc;
       typename P::GenRegs held[S];  // what each stage's A tile holds (its previous k-block)
       bool used[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
+      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, ga);
+      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, gb);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -189,29 +180,21 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kParts * L::kBBytes;
-      constexpr int kMB = meta_bytes_of<P>::value;
-      int64_t q = 0;
-      while (ok && c0.valid) {
-        const int slot = (int)(q % kMetaSlots);
-        // the loader's data for this k-block (every lane acquires it)
-        if (!mbar_wait(smem_u32(meta_bars + slot), (uint32_t)((q / kMetaSlots) & 1), err, kErrProducer)) ok = false;
-        if (!__all_sync(0xffffffffu, ok)) {
-          ok = false;
-          break;
-        }
-        p.gen_load(c0.it, c0.kb, lane, g, meta_smem + slot * kMB);
-        __syncwarp();  // every lane has read the slot
-        if (lane == 0) mbar_arrive(smem_u32(meta_bars + kMetaSlots + slot));
+      // one k-block: prefetch into `fill` for c2, write c0's tile from `use`
+      auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill) -> bool {
+        if (!ok || !c0.valid) return false;
+        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, fill);
         int w_ok = 1;
         if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
         if (!w_ok) {
           ok = false;
-          break;
+          return false;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, lane, g, used[stage] ? &held[stage] : nullptr, st, st + L::kABytes + L::kBBytes);
-        held[stage] = g;
+        p.gen_store(c0.it, c0.kb, lane, use, used[stage] ? &held[stage] : nullptr, st,
+                    st + L::kABytes + L::kBBytes);
+        held[stage] = use;
         used[stage] = true;
         fence_proxy_async_smem();
         __syncwarp();
@@ -227,9 +210,15 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
           stage = 0;
           phase ^= 1;
         }
-        ++q;
-        ++c0.kb;
-        seek(c0);
+        c0 = c1;
+        c1 = c2;
+        if (c2.valid) {
+          ++c2.kb;
+          seek(c2);
+        }
+        return true;
+      };
+      while (step(ga, gc) && step(gb, ga) && step(gc, gb)) {
       }
       if (!ok && lane == 0) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
@@ -288,79 +277,6 @@ __global__ void __launch_bounds__(EngineLayout<P>::kThreads, 1)
         }
       }
       __syncwarp();
-    }
-  } else if (gen_a_of<P>::value && warp == kEngineThreads / 32) {
-    if constexpr (gen_a_of<P>::value) {
-      // loader: fills data slot q % kMetaSlots for the q-th k-block of this CTA,
-      // kMetaGroup k-blocks at a time (their loads overlap)
-      constexpr int kMB = meta_bytes_of<P>::value;
-      struct Cur {
-        int64_t item;
-        typename P::Item it;
-        int nch, c, kb, kb1, br;
-        bool valid;
-      };
-      auto seek = [&](Cur& x) {
-        while (x.valid && x.kb >= x.kb1) {
-          if (++x.c < x.nch) {
-            p.chunk(x.it, x.c, x.br, x.kb, x.kb1);
-          } else {
-            x.item += gridDim.x;
-            if (x.item >= total) {
-              x.valid = false;
-            } else {
-              x.it = p.decode(x.item);
-              x.nch = p.nchunks(x.it);
-              x.c = 0;
-              p.chunk(x.it, 0, x.br, x.kb, x.kb1);
-            }
-          }
-        }
-      };
-      Cur cur;
-      cur.item = blockIdx.x;
-      cur.valid = cur.item < total;
-      cur.c = cur.kb = cur.kb1 = cur.nch = cur.br = 0;
-      if (cur.valid) {
-        cur.it = p.decode(cur.item);
-        cur.nch = p.nchunks(cur.it);
-        p.chunk(cur.it, 0, cur.br, cur.kb, cur.kb1);
-        seek(cur);
-      }
-      int64_t q = 0;
-      bool ok = true;
-      while (ok && cur.valid) {
-        typename P::MetaRegs r[kMetaGroup];
-        int n = 0;
-#pragma unroll
-        for (int g = 0; g < kMetaGroup; ++g) {
-          if (!cur.valid) break;
-          const int64_t qq = q + g;
-          const int slot = (int)(qq % kMetaSlots);
-          if (!mbar_wait(smem_u32(meta_bars + kMetaSlots + slot), (uint32_t)(((qq / kMetaSlots) & 1) ^ 1), err,
-                         kErrProducer))
-            ok = false;
-          if (!__all_sync(0xffffffffu, ok)) {
-            ok = false;
-            break;
-          }
-          p.meta_load(cur.it, cur.kb, lane, r[g]);
-          ++n;
-          ++cur.kb;
-          seek(cur);
-        }
-        if (!ok) break;
-#pragma unroll
-        for (int g = 0; g < kMetaGroup; ++g) {
-          if (g >= n) break;
-          const int slot = (int)((q + g) % kMetaSlots);
-          p.meta_store(lane, r[g], meta_smem + slot * kMB);
-        }
-        __syncwarp();
-        if (lane == 0)
-          for (int g = 0; g < n; ++g) mbar_arrive(smem_u32(meta_bars + (int)((q + g) % kMetaSlots)));
-        q += n;
-      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -469,7 +385,7 @@ void launch_engine(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap
                    const P& p, int* err, int grid, cudaStream_t s) {
   using L = EngineLayout<P>;
   GIFT_CUDA(cudaFuncSetAttribute(tc_engine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem));
-  tc_engine<P><<<grid, L::kThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
+  tc_engine<P><<<grid, kEngineThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
   GIFT_LAUNCHED("tc_engine");
 }
 
