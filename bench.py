@@ -238,6 +238,8 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
             else:
                 table[name] = {"ms": ms, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                                "frac": t_frac, "hbm_frac": h_frac}
+    if not table:  # no engine kernel ran (FP32 store scanned on the CUDA cores, no tensor-core quantiser)
+        return None
     dom = max(table, key=lambda k: table[k]["ms"])
     src_hash = kernel_source_hash(kernels[dom][3] + ["tc_engine.cuh", "tc_common.cuh"])
     traffic, _ = recorded_traffic(dom, src_hash) if with_traffic else (None, None)
@@ -253,7 +255,8 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
             "unit": dt["unit"], "frac": dt["frac"], "traffic": traffic, "peak_source": psrc,
             "kernel_ms": dt["ms"], "work": work, "src_hash": src_hash, "all": table,
             "scan_hbm": {"algorithmic_bytes": scan_bytes,
-                         "achieved_gbs": scan_bytes / (st["scan_kernel_ms"] / 1e3) / 1e9,
+                         "achieved_gbs": (scan_bytes / (st["scan_kernel_ms"] / 1e3) / 1e9
+                                          if st["scan_kernel_ms"] > 0 else None),
                          "peak_gbs": hbm_peak}}
 
 

@@ -30,3 +30,12 @@ def test_roofline_picks_dominant_kernel_and_its_roof():
 
 def test_recorded_traffic_ignores_other_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("no-such-kernel", "0" * 12) == (None, None)
+
+
+def test_roofline_without_tensor_core_scan():
+    """An FP32 store scans on the CUDA cores: no scan or rescore kernel time, only the quantiser."""
+    cfg = CONFIGS["db200x64_d128_k64"]
+    r = bench.roofline(cfg, _st(0.0, 0.0, 0.05), 1e6, 1e8, 0, 640, {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0},
+                       "measured")
+    assert r["kernel"] == "tc_engine<AssignPolicy>" and r["scan_hbm"]["achieved_gbs"] is None
+    assert bench.roofline(cfg, _st(0.0, 0.0, 0.0), 0, 0, 0, 0, {"hbm_gbs": 1.0, "bf16_tflops": 1.0}, "m") is None
