@@ -704,8 +704,9 @@ def main():
         times, _ = cpu_oracle_run(cfg, data, 1, 4, db_codes=db_codes)
         line["cpu_baseline"] = {"value": 1.0 / statistics.mean(times[1:]), "unit": "queries/s",
                                 "cores": blas_threads(), "kind": "oracle",
-                                "sample": "3 queries (after 1 warm-up) through the FP64 oracle: Eq. 4 over all "
-                                          "12,000 shapes, top-100, dense Eq. 8 re-rank over 12,000 shapes"}
+                                "sample": f"3 queries (after 1 warm-up) through the FP64 oracle: Eq. 4 over all "
+                                          f"{cfg.n_shapes:,} shapes, top-{cfg.topk}, dense Eq. 8 re-rank over "
+                                          f"{cfg.n_shapes:,} shapes"}
 
     ix.close()
     if rank == 0:
