@@ -196,11 +196,6 @@ void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_
                      const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);
 
 
-// k_exact.cu
-void exact_scores(const Index& ix, const float* q, const float* q_inv, int64_t nv,
-                  const int32_t* d_vquery, const std::vector<int32_t>& h_qoff, int32_t B,
-                  float* S_dense, Scratch& sc, cudaStream_t s);
-
 // k_topk.cu
 // Per row b of `scores` [B, n] (or of keys64 when scores == nullptr): the k
 // largest by (value desc, index asc). ids_out/val_out [B, k] (val_out may be

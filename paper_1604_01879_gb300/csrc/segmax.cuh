@@ -4,14 +4,6 @@
 
 namespace gift {
 
-// S[b, p] = (1/|V_b|) sum_{i in b} max_j cos(A_i, B_{p*nv + j}); argmax (optional)
-// [n_views, n_shapes] gets the first j attaining each max. inv_a / inv_b are
-// reciprocal row norms (0 for zero rows). d_qoff is the device copy of h_qoff.
-void segmax_scores(const float* A, const float* inv_a, int64_t n_views, const float* Bm,
-                   const float* inv_b, int64_t n_shapes, int nv, int D, const int32_t* d_qoff,
-                   const std::vector<int32_t>& h_qoff, int32_t Bq, float* S, int16_t* argmax,
-                   Scratch& sc, cudaStream_t s);
-
 // S[b, p] (and argmax) from the per-(view, shape) cells of queries [b0, b0 + nq)
 void segmax_reduce(const unsigned long long* cell, int64_t n_shapes, const int32_t* d_qoff, int32_t b0, int32_t nq,
                    int32_t view0, float* S, int16_t* argmax, cudaStream_t s);
