@@ -26,6 +26,10 @@ struct FifPlan {
   int64_t* woff = nullptr;        // [K+1] scan work items per codeword (exclusive)
   int64_t upper_items = 0;        // bound on the number of scan work items
   int64_t table_upper = 0;        // bound on the table cells
+  // slot-ordered two-part BF16 query rows, made by the first tensor-core pass
+  // that needs them and reused by the next (scan, then rescore)
+  mutable __nv_bfloat16* slot_hi = nullptr;
+  mutable __nv_bfloat16* slot_lo = nullptr;
 };
 
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s);

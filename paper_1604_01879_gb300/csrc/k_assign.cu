@@ -13,7 +13,8 @@
 // about five times the representation bound of the split (3 * 2^-16 relative
 // per product) plus the measured accumulation error. When a chunk's 16th kept
 // score is still a candidate, that chunk may hold more, and the row takes the
-// exact pass over every codeword. The candidates' squared distances are
+// exact pass over every codeword. A single candidate with ma = 1 is the code
+// without further work; otherwise the candidates' squared distances are
 // evaluated in two-float (~2^-44 relative) arithmetic; the ma smallest by
 // (distance, index) are the codes. Results equal an exact evaluation except
 // where distances tie to ~1e-13.
@@ -227,6 +228,23 @@ __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__
     if (id[e] != 0x7fffffff && v[e] >= lim && min(TNA, K - c * TNA) > kT) full = true;
   }
   full = __any_sync(kFull, full);
+  if (!full && ma == 1) {
+    // a single candidate is the nearest codeword: the true nearest always lies in
+    // the window, and so would any codeword at an equal true distance
+    int cnt = 0, only = 0x7fffffff;
+    for (int base = 0; base < tot; base += 32) {
+      const int e = base + lane;
+      const int kk = e < tot ? id[e] : 0x7fffffff;
+      const bool take = e < tot && kk != 0x7fffffff && v[e] >= lim;
+      const unsigned m = __ballot_sync(kFull, take);
+      if (m && cnt == 0) only = __shfl_sync(kFull, kk, __ffs(m) - 1);
+      cnt += __popc(m);
+    }
+    if (cnt == 1) {
+      if (lane == 0) codes[r] = only;
+      return;
+    }
+  }
   float H[GIFT_MAX_MA], Lo[GIFT_MAX_MA];
   int Kx[GIFT_MAX_MA];
 #pragma unroll

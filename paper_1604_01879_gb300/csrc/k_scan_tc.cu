@@ -332,11 +332,18 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     q8s = sc.get<float>(ns);
     k_slot_fp8<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, q8, q8s);
     GIFT_LAUNCHED("k_slot_fp8");
+  } else if (P.slot_hi && (P.slot_lo || !rescore)) {
+    qhi = P.slot_hi;  // made by the scan of this batch
+    qlo = P.slot_lo;
   } else {
+    // the low parts too when this index rescores next, so the rescore reuses both
+    const bool want_lo = rescore || (ix.prm.rescore_r > 0 && ix.list_lo != nullptr);
     qhi = sc.get<__nv_bfloat16>((size_t)qrows * D);
-    qlo = rescore ? sc.get<__nv_bfloat16>((size_t)qrows * D) : nullptr;
+    qlo = want_lo ? sc.get<__nv_bfloat16>((size_t)qrows * D) : nullptr;
     k_slot_split<<<(unsigned)ns, 256, 0, s>>>(P.q, P.slot_view, ns, D, qhi, qlo);
     GIFT_LAUNCHED("k_slot_split");
+    P.slot_hi = qhi;
+    P.slot_lo = qlo;
   }
   const int tn = rescore ? kRescTN : kScanTN;
   int64_t* wcnt = sc.get<int64_t>(K + 1);
