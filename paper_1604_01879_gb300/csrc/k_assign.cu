@@ -160,6 +160,58 @@ __device__ void dist_df(const float* __restrict__ x, const float* __restrict__ b
   olo = te;
 }
 
+// the same two-float distances for up to kBatch candidates at once: each chunk
+// of the row is read once and compared with every candidate
+constexpr int kBatch = 8;
+__device__ void dist_df_batch(const float* __restrict__ x, const float* __restrict__ cb, const int (&kc)[kBatch],
+                              int n, int D, int lane, float (&ohi)[kBatch], float (&olo)[kBatch]) {
+  float hi[kBatch], lo[kBatch];
+#pragma unroll
+  for (int c = 0; c < kBatch; ++c) {
+    hi[c] = 0.f;
+    lo[c] = 0.f;
+  }
+  for (int d = lane * 4; d < D; d += 128) {
+    const float4 xv = *reinterpret_cast<const float4*>(x + d);
+    const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+    for (int c = 0; c < kBatch; ++c) {
+      if (c >= n) break;
+      const float4 bv = *reinterpret_cast<const float4*>(cb + (int64_t)kc[c] * D + d);
+      const float bs[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float s2, e;
+        two_sum(xs[q], -bs[q], s2, e);
+        const float p = s2 * s2;
+        float pe = fmaf(s2, s2, -p);
+        pe = fmaf(2.f * s2, e, pe);
+        float t, te;
+        two_sum(hi[c], p, t, te);
+        hi[c] = t;
+        lo[c] += te + pe;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kBatch; ++c) {
+    if (c >= n) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(kFull, hi[c], o);
+      const float l2 = __shfl_xor_sync(kFull, lo[c], o);
+      float t, te;
+      two_sum(hi[c], h2, t, te);
+      hi[c] = t;
+      lo[c] = lo[c] + l2 + te;
+    }
+    float t, te;
+    two_sum(hi[c], lo[c], t, te);
+    ohi[c] = t;
+    olo[c] = te;
+  }
+}
+
 __device__ __forceinline__ bool df_less(float ah, float al, int ak, float bh, float bl, int bk) {
   if (ah != bh) return ah < bh;
   if (al != bl) return al < bl;
@@ -253,7 +305,57 @@ __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__
     Lo[a] = 0.f;
     Kx[a] = 0x7fffffff;
   }
-  const int nscan = full ? K : tot;
+  auto insert = [&](float h, float l, int k) {  // into the ascending list of the ma best (registers, unrolled)
+    if (df_less(h, l, k, H[GIFT_MAX_MA - 1], Lo[GIFT_MAX_MA - 1], Kx[GIFT_MAX_MA - 1])) {
+      H[GIFT_MAX_MA - 1] = h;
+      Lo[GIFT_MAX_MA - 1] = l;
+      Kx[GIFT_MAX_MA - 1] = k;
+#pragma unroll
+      for (int t = GIFT_MAX_MA - 1; t > 0; --t) {
+        if (df_less(H[t], Lo[t], Kx[t], H[t - 1], Lo[t - 1], Kx[t - 1])) {
+          const float th = H[t], tl = Lo[t];
+          const int tk = Kx[t];
+          H[t] = H[t - 1];
+          Lo[t] = Lo[t - 1];
+          Kx[t] = Kx[t - 1];
+          H[t - 1] = th;
+          Lo[t - 1] = tl;
+          Kx[t - 1] = tk;
+        }
+      }
+    }
+  };
+  bool batched = false;
+  if (!full) {
+    // up to kBatch candidates: one pass over the row for all of them
+    int kc[kBatch];
+    int n = 0;
+#pragma unroll
+    for (int c = 0; c < kBatch; ++c) kc[c] = 0;
+    for (int base = 0; base < tot; base += 32) {
+      const int e = base + lane;
+      const int kk = e < tot ? id[e] : 0x7fffffff;
+      unsigned m = __ballot_sync(kFull, e < tot && kk != 0x7fffffff && v[e] >= lim);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const int k = __shfl_sync(kFull, kk, j);
+#pragma unroll
+        for (int c = 0; c < kBatch; ++c)
+          if (c == n) kc[c] = k;
+        ++n;
+      }
+    }
+    if (n <= kBatch) {
+      float hh[kBatch], ll[kBatch];
+      dist_df_batch(x, cb, kc, n, D, lane, hh, ll);
+#pragma unroll
+      for (int c = 0; c < kBatch; ++c)
+        if (c < n) insert(hh[c], ll[c], kc[c]);
+      batched = true;
+    }
+  }
+  const int nscan = batched ? 0 : full ? K : tot;
   for (int base = 0; base < nscan; base += 32) {
     const int e = base + lane;
     bool take;
@@ -272,25 +374,7 @@ __global__ __launch_bounds__(256) void k_assign_refine(const float* __restrict__
       const int k = __shfl_sync(kFull, kk, j);
       float h, l;
       dist_df(x, cb + (int64_t)k * D, D, lane, h, l);
-      // insert into the ascending list of the ma best (registers, unrolled)
-      if (df_less(h, l, k, H[GIFT_MAX_MA - 1], Lo[GIFT_MAX_MA - 1], Kx[GIFT_MAX_MA - 1])) {
-        H[GIFT_MAX_MA - 1] = h;
-        Lo[GIFT_MAX_MA - 1] = l;
-        Kx[GIFT_MAX_MA - 1] = k;
-#pragma unroll
-        for (int t = GIFT_MAX_MA - 1; t > 0; --t) {
-          if (df_less(H[t], Lo[t], Kx[t], H[t - 1], Lo[t - 1], Kx[t - 1])) {
-            const float th = H[t], tl = Lo[t];
-            const int tk = Kx[t];
-            H[t] = H[t - 1];
-            Lo[t] = Lo[t - 1];
-            Kx[t] = Kx[t - 1];
-            H[t - 1] = th;
-            Lo[t - 1] = tl;
-            Kx[t - 1] = tk;
-          }
-        }
-      }
+      insert(h, l, k);
     }
   }
   if (lane < ma) {
