@@ -164,7 +164,9 @@ GIFT_API void gift_destroy_index(gift_index* index);
  *    [q_view_offsets[b], q_view_offsets[b+1]); V_q >= 1. (Host side because
  *    the launch is sized from it; no device-to-host read is needed.)
  *  - mode GIFT_MATCH_EXACT: S(x_q, x_p) of Eq. 3 with the cosine similarity,
- *    (1/|V(x_q)|) sum_i max_j s(q_i, p_j), over all N shapes (needs keep_exact).
+ *    (1/|V(x_q)|) sum_i max_j s(q_i, p_j), over all N shapes (needs keep_exact,
+ *    or a BF16/FP8 index built with rescore_r > 0, whose two-part list store is
+ *    then read in list order).
  *    mode GIFT_MATCH_FIF: Eq. 4: each query view is quantised to its query_ma
  *    nearest codewords, only the F-IF lists of those codewords are scanned,
  *    and a shape's view contributes only when its codeword is one of them;

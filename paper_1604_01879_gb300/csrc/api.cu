@@ -931,14 +931,18 @@ gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q
     int32_t* oid = gift::stage_out(out_ids, (size_t)B * topk, sc, outs);
     float* osc = gift::stage_out(out_scores, (size_t)B * topk, sc, outs);
     if (mode == GIFT_MATCH_EXACT) {
-      if (!ix.ex_hi) gift::fail(GIFT_EUNSUPPORTED, "exact match needs keep_exact");
+      if (!ix.ex_hi && !ix.list_lo)
+        gift::fail(GIFT_EUNSUPPORTED, "exact match needs keep_exact or a two-part rescore store");
       int32_t* d_qoff = sc.get<int32_t>(B + 1);
       GIFT_CUDA(cudaMemcpyAsync(d_qoff, h.data(), (B + 1) * 4, cudaMemcpyHostToDevice, stream));
       float* q_inv = sc.get<float>(nv);
       gift::launch_row_invnorm(q, nv, D, q_inv, stream);
       tm.mark(gift::ST_SCAN);
       float* S = sc.get<float>((size_t)B * ix.prm.n_shapes);
-      gift::exact_scores_tc(ix, q, q_inv, nv, d_qoff, h, B, S, sc, stream);
+      if (ix.ex_hi)
+        gift::exact_scores_tc(ix, q, q_inv, nv, d_qoff, h, B, S, sc, stream);
+      else
+        gift::exact_scores_lists(ix, q, q_inv, nv, d_qoff, h, B, S, sc, stream);
       tm.mark(gift::ST_TOPK);
       gift::topk_rows_f32(S, B, ix.prm.n_shapes, topk, oid, osc, sc, stream);
     } else if (mode == GIFT_MATCH_FIF) {

@@ -194,6 +194,9 @@ void render_views(const float* V, const int32_t* T, const std::vector<int64_t>& 
 // k_exact_tc.cu: Eq. 3 over all N shapes on the tensor cores
 void exact_scores_tc(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
                      const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);
+// the same from the list-ordered two-part store (indices built without keep_exact)
+void exact_scores_lists(const Index& ix, const float* q, const float* q_inv, int64_t nv, const int32_t* d_qoff,
+                        const std::vector<int32_t>& h_qoff, int32_t B, float* S, Scratch& sc, cudaStream_t s);
 
 
 // k_topk.cu

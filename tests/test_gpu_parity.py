@@ -386,3 +386,19 @@ def test_database_side_multiple_assignment(gpu_lib, db_ma, q_ma, storage):
         assert np.array_equal(a, b)
     st.close()
     ix.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_exact_match_from_the_list_store(gpu_lib, storage):
+    """Eq. 3 on an index without the shape-ordered copy: the list-ordered two-part store is read
+    once per query batch, FP32-level against the oracle (several query passes: tiny cell budget)."""
+    import torch
+    N, Nv, D, C, K = 90, 16, 64, 4, 8
+    X, cb, Q, qoff, _, _ = _case(N, Nv, D, C, K, 7, (16, 5), 141)
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage=storage, rescore_r=20, keep_exact=False)
+    ids, sc = ix.query(torch.from_numpy(Q).cuda(), qoff, mode="exact", topk=N)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    ref = O.exact_scores(Q, qoff, X)
+    for b in range(len(qoff) - 1):
+        assert_topk(ids[b], sc[b], ref[b], N)
+    ix.close()
