@@ -391,7 +391,7 @@ def test_database_side_multiple_assignment(gpu_lib, db_ma, q_ma, storage):
 @pytest.mark.parametrize("storage", ["bf16", "fp8"])
 def test_exact_match_from_the_list_store(gpu_lib, storage):
     """Eq. 3 on an index without the shape-ordered copy: the list-ordered two-part store is read
-    once per query batch, FP32-level against the oracle (several query passes: tiny cell budget)."""
+    once per query batch, FP32-level against the oracle."""
     import torch
     N, Nv, D, C, K = 90, 16, 64, 4, 8
     X, cb, Q, qoff, _, _ = _case(N, Nv, D, C, K, 7, (16, 5), 141)
