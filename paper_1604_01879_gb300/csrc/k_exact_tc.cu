@@ -115,6 +115,80 @@ struct ExactPolicy {
   }
 };
 
+// The same contraction for short reductions (one accumulator chunk, at most 16
+// k-blocks: the projected match, D = d_out) with 64 views per shape, so a
+// 128-column tile holds exactly two whole shapes. Each shape's (max, first
+// argmax) is taken straight from the accumulator: the epilogue keeps no
+// per-column sums, which would otherwise bound a kernel with this little MMA
+// work per tile.
+struct ShortSegPolicy {
+  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
+  static constexpr int kNv = 64;
+  static constexpr int kWarpSmem = TN * 4;
+  int64_t rows, ncols, n_rt, n_shapes;
+  int nkb;
+  const float* q_inv;
+  const float* r_inv;
+  unsigned long long* cell;
+  struct Item {
+    int64_t r0, c0;
+    int nr, nc;
+  };
+  struct Ctx {
+    float qi;
+  };
+  __device__ __forceinline__ int64_t total() const { return n_rt * cdiv(ncols, TN); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    Item it;
+    const int64_t ct = item / n_rt, rt = item % n_rt;
+    it.r0 = rt * tc::kTM;
+    it.c0 = ct * TN;
+    it.nr = (int)min((int64_t)tc::kTM, rows - it.r0);
+    it.nc = (int)min((int64_t)TN, ncols - it.c0);
+    return it;
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return 1; }
+  __device__ __forceinline__ void chunk(const Item& it, int, int& br, int& kb0, int& kb1) const {
+    br = (int)it.c0;
+    kb0 = 0;
+    kb1 = nkb;
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int, uint8_t* ws) const {
+    float* ri = reinterpret_cast<float*>(ws);
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < TN; c += 32) ri[c] = c < it.nc ? r_inv[it.c0 + c] : 0.f;
+    x.qi = m < it.nr ? q_inv[it.r0 + m] : 0.f;
+  }
+  __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int m, uint8_t* ws) const {
+    const float* ri = reinterpret_cast<const float*>(ws);
+    unsigned long long* crow = cell + (it.r0 + m) * n_shapes + it.c0 / kNv;
+#pragma unroll
+    for (int g = 0; g < TN / kNv; ++g) {
+      float best = 0.f;
+      int bj = 0;
+#pragma unroll
+      for (int pc = 0; pc < kNv / 32; ++pc) {
+        uint32_t r[32];
+        tc::tmem_ld32(taddr + g * kNv + pc * 32, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = g * kNv + pc * 32 + j;
+          const float v = __uint_as_float(r[j]) * x.qi * ri[c];
+          if ((pc == 0 && j == 0) || v > best) {  // ties keep the first view
+            best = v;
+            bj = pc * 32 + j;
+          }
+        }
+      }
+      if (m < it.nr && g * kNv < it.nc)
+        atomicMax(crow + g, ((unsigned long long)f2key(best) << 32) | (0xFFFFull - (unsigned)bj));
+    }
+  }
+  __device__ __forceinline__ void epi_end(const Item&, Ctx&, int, uint8_t*) const {}
+};
+
 // The same match over the list-ordered two-part store of an index that keeps
 // no shape-ordered copy: columns are list entries, the shape of each comes from
 // the list structure, and each row folds the maximum of every run of equal
@@ -230,6 +304,25 @@ void segmax_tc(const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo, int64_t a_r
       cell_rows = rows;
     }
     GIFT_CUDA(cudaMemsetAsync(cell, 0, (size_t)rows * N * 8, s));
+    const CUtensorMap tA = make_tmap_bf16(a_hi + v0 * D, a_rows_alloc - v0, D, tc::kTM);
+    const CUtensorMap tA2 = make_tmap_bf16(a_lo + v0 * D, a_rows_alloc - v0, D, tc::kTM);
+    const int nkb = (int)cdiv(D, tc::kTK);
+    if (nv == ShortSegPolicy::kNv && nkb <= 16) {
+      ShortSegPolicy p;
+      p.rows = rows;
+      p.ncols = ncols;
+      p.n_rt = cdiv(rows, tc::kTM);
+      p.n_shapes = N;
+      p.nkb = nkb;
+      p.q_inv = a_inv + v0;
+      p.r_inv = b_inv;
+      p.cell = cell;
+      const int grid = (int)std::min<int64_t>(sms, p.n_rt * cdiv(ncols, ShortSegPolicy::TN));
+      tc::launch_engine(tA, tB, tA2, tB2, p, err, grid, s);
+      segmax_reduce(cell, N, d_qoff, b0, b1 - b0, (int32_t)v0, S, argmax, s);
+      b0 = b1;
+      continue;
+    }
     ExactPolicy p;
     p.rows = rows;
     p.ncols = ncols;
@@ -240,8 +333,6 @@ void segmax_tc(const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo, int64_t a_r
     p.q_inv = a_inv + v0;
     p.r_inv = b_inv;
     p.cell = cell;
-    const CUtensorMap tA = make_tmap_bf16(a_hi + v0 * D, a_rows_alloc - v0, D, tc::kTM);
-    const CUtensorMap tA2 = make_tmap_bf16(a_lo + v0 * D, a_rows_alloc - v0, D, tc::kTM);
     const int grid = (int)std::min<int64_t>(sms, p.n_rt * cdiv(ncols, ExactPolicy::TN));
     tc::launch_engine(tA, tB, tA2, tB2, p, err, grid, s);
     segmax_reduce(cell, N, d_qoff, b0, b1 - b0, (int32_t)v0, S, argmax, s);

@@ -46,6 +46,19 @@ __global__ void k_split_any(const T* __restrict__ in, int64_t n, __nv_bfloat16* 
   if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// the same for FP32 input, four elements per thread (n % 4 == 0, 16-byte aligned input, 8-byte aligned output)
+__global__ void k_split4(const float4* __restrict__ in, int64_t n4, uint2* __restrict__ hi, uint2* __restrict__ lo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+    hi[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    if (lo) lo[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+  }
+}
+
 template <typename T>
 __global__ void k_to_float(const T* __restrict__ in, int64_t n, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,6 +98,7 @@ template <bool ROWS_Q>
 struct OneHotPolicy {
   static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
   static constexpr bool GEN_A = true;
+  static constexpr int GEN_WARPS = 4;  // generator thread g: row g (ROWS_Q) or column g % 64
   static constexpr int kWarpSmem = 16;
   int64_t M, N;             // rows (query or database views), dout
   int nkb;                  // 64-wide k-blocks of the reduction
@@ -104,13 +118,15 @@ struct OneHotPolicy {
   struct Ctx {
     float sum[TN];
   };
-  // non-zeros of one k-block prefetched by each lane (fast layouts: ROWS_Q with
-  // N_v a multiple of 64, one shape per k-block; !ROWS_Q with N_v >= 64, at most
-  // three shapes per 128-row tile); other layouts gather inside gen_store
+  // non-zeros of one k-block prefetched by each generator thread (fast
+  // layouts: ROWS_Q with N_v a multiple of 64, one shape per k-block: thread g
+  // owns row g; !ROWS_Q with N_v >= 64, at most three shapes per 128-row tile:
+  // thread g owns column g % 64 of shapes 0 and 2 (g < 64) or shape 1); other
+  // layouts are written by warp 0 alone inside gen_store
   bool fast;
   struct GenRegs {
-    int pos[6];   // row * 64 + column in the A tile, -1 = none
-    float w[6];
+    int pos[2];   // row * 64 + column in the A tile, -1 = none
+    float w[2];
   };
   __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
   __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
@@ -131,59 +147,77 @@ struct OneHotPolicy {
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
-  __device__ __forceinline__ void gen_load(const Item& it, int kb, int lane, GenRegs& g) const {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) g.pos[e] = -1;
+  // the argmax and weight lines of k-block kb + kPrefetchKB are pulled into L2
+  // while this k-block's are loaded: their loads, two k-blocks ahead of use,
+  // then hit L2 instead of waiting on DRAM
+  static constexpr int kPrefetchKB = 8;
+  __device__ __forceinline__ void gen_load(const Item& it, int kb, int g, GenRegs& r) const {
+    r.pos[0] = r.pos[1] = -1;
     if (!fast) return;
     const int64_t k0 = (int64_t)kb * 64;
     if (ROWS_Q) {
       if (k0 >= nr) return;
       const int p = (int)(k0 / nv);
-      int jj[4];
-      float ww[4];
+      {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 0..5
+        const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
+        if (kp < nr && g < 6) {
+          const int64_t e = (kp / nv) * nq + it.r0;
+          const int off = g < 2 ? g * 64 : (g - 2) * 32;  // first row of the line
+          if (it.r0 + off < nq) {
+            if (g < 2)
+              tc::prefetch_l2(amT + e + off);
+            else
+              tc::prefetch_l2(wT + e + off);
+          }
+        }
+      }
+      if (g >= it.nr) return;
+      const int64_t e = (int64_t)p * nq + it.r0 + g;
+      const int j = amT[e];
+      const float w = wT[e];
+      const int64_t rr = (int64_t)p * nv + (j >= 0 && j < nv ? j : 0);
+      if (rr < k0 || rr >= k0 + 64) return;
+      r.pos[0] = g * 64 + (int)(rr - k0);
+      r.w[0] = w;
+    } else {
+      if (k0 >= nq) return;
+      const int p0 = (int)(it.r0 / nv);
+      {  // three shapes x 64 query views: 128 bytes of argmax and 256 of weights each
+        const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
+        if (kp < nq && g < 9) {
+          const int t = g / 3, u = g % 3;
+          const int off = u == 0 ? 0 : (u - 1) * 32;  // first query view of the line
+          if (p0 + t < Np && kp + off < nq) {
+            const int64_t e = (int64_t)(p0 + t) * nq + kp + off;
+            if (u == 0)
+              tc::prefetch_l2(amT + e);
+            else
+              tc::prefetch_l2(wT + e);
+          }
+        }
+      }
+      const int col = g & 63;
+      const int64_t i = k0 + col;
+      if (i >= nq) return;
+      int jj[2];
+      float ww[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {  // coalesced, independent loads (no shared-memory stores in between)
-        const int row = lane + 32 * q;
-        const int64_t e = (int64_t)p * nq + it.r0 + row;
-        const bool ok = row < it.nr;
+      for (int q = 0; q < 2; ++q) {  // independent loads first
+        const int t = (g >> 6) + 2 * q;
+        const bool ok = t < 3 && p0 + t < Np;
+        const int64_t e = (int64_t)(p0 + t) * nq + i;
         jj[q] = ok ? amT[e] : -1;
         ww[q] = ok ? wT[e] : 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (jj[q] < 0) continue;
-        const int64_t r = (int64_t)p * nv + (jj[q] < nv ? jj[q] : 0);
-        if (r < k0 || r >= k0 + 64) continue;
-        g.pos[q] = (lane + 32 * q) * 64 + (int)(r - k0);
-        g.w[q] = ww[q];
-      }
-    } else {
-      if (k0 >= nq) return;
-      const int p0 = (int)(it.r0 / nv);
-      int jj[6];
-      float ww[6];
-#pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int64_t i = k0 + lane + 32 * q;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int64_t e = (int64_t)(p0 + t) * nq + i;
-          const bool ok = i < nq && p0 + t < Np;
-          jj[q * 3 + t] = ok ? amT[e] : -1;
-          ww[q * 3 + t] = ok ? wT[e] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int j = jj[q * 3 + t];
-          if (j < 0) continue;
-          const int64_t r = (int64_t)(p0 + t) * nv + (j < nv ? j : 0);
-          if (r < it.r0 || r >= it.r0 + it.nr) continue;
-          g.pos[q * 3 + t] = (int)(r - it.r0) * 64 + lane + 32 * q;
-          g.w[q * 3 + t] = ww[q * 3 + t];
-        }
+        const int t = (g >> 6) + 2 * q;
+        if (t >= 3 || p0 + t >= Np) continue;
+        const int j = jj[q];
+        const int64_t rr = (int64_t)(p0 + t) * nv + (j >= 0 && j < nv ? j : 0);
+        if (rr < it.r0 || rr >= it.r0 + it.nr) continue;
+        r.pos[q] = (int)(rr - it.r0) * 64 + col;
+        r.w[q] = ww[q];
       }
     }
   }
@@ -195,31 +229,29 @@ struct OneHotPolicy {
     *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
   }
-  __device__ __forceinline__ void gen_store(const Item& it, int kb, int lane, const GenRegs& g, const GenRegs* prev,
+  __device__ __forceinline__ void gen_store(const Item& it, int kb, int g, const GenRegs& r, const GenRegs* prev,
                                             uint8_t* a_hi, uint8_t* a_lo) const {
-    if (fast && prev) {
-      // the tile is zero but for the entries this lane wrote into it last time
-      // (a position belongs to one lane: its row, or its column, is the lane's)
+    if (fast) {
+      // the tile is zero but for the entries this thread wrote into it last time
+      // (a position belongs to one thread: its row, or its column and shape)
+      if (prev) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e)
-        if (prev->pos[e] >= 0) put(a_hi, a_lo, prev->pos[e] >> 6, prev->pos[e] & 63, 0.f);
+        for (int e = 0; e < 2; ++e)
+          if (prev->pos[e] >= 0) put(a_hi, a_lo, prev->pos[e] >> 6, prev->pos[e] & 63, 0.f);
+      }
 #pragma unroll
-      for (int e = 0; e < 6; ++e)
-        if (g.pos[e] >= 0) put(a_hi, a_lo, g.pos[e] >> 6, g.pos[e] & 63, g.w[e]);
+      for (int e = 0; e < 2; ++e)
+        if (r.pos[e] >= 0) put(a_hi, a_lo, r.pos[e] >> 6, r.pos[e] & 63, r.w[e]);
       return;
     }
+    if (g >= 32) return;  // warp 0 writes the general layouts
+    const int lane = g;
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     for (int o = lane * 16; o < tc::kTM * 128; o += 32 * 16) {
       *reinterpret_cast<uint4*>(a_hi + o) = z;
       *reinterpret_cast<uint4*>(a_lo + o) = z;
     }
     __syncwarp();
-    if (fast) {
-#pragma unroll
-      for (int e = 0; e < 6; ++e)
-        if (g.pos[e] >= 0) put(a_hi, a_lo, g.pos[e] >> 6, g.pos[e] & 63, g.w[e]);
-      return;
-    }
     const int64_t k0 = (int64_t)kb * 64;
     if (ROWS_Q) {
       if (k0 >= nr) return;
@@ -233,9 +265,9 @@ struct OneHotPolicy {
         for (int p = p0; p <= p1; ++p) {
           int j = amT[(int64_t)p * nq + i];
           if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; stay inside the shape
-          const int64_t r = (int64_t)p * nv + j;
-          if (r < k0 || r >= k0 + 64) continue;
-          put(a_hi, a_lo, row, (int)(r - k0), gS[(int64_t)b * Np + p] * cb * kinv[r]);
+          const int64_t rr = (int64_t)p * nv + j;
+          if (rr < k0 || rr >= k0 + 64) continue;
+          put(a_hi, a_lo, row, (int)(rr - k0), gS[(int64_t)b * Np + p] * cb * kinv[rr]);
         }
       }
     } else {
@@ -250,9 +282,9 @@ struct OneHotPolicy {
         for (int p = p0; p <= p1; ++p) {
           int j = amT[(int64_t)p * nq + i];
           if (j < 0 || j >= nv) j = 0;
-          const int64_t r = (int64_t)p * nv + j;
-          if (r < it.r0 || r >= it.r0 + it.nr) continue;
-          put(a_hi, a_lo, (int)(r - it.r0), col, gS[(int64_t)b * Np + p] * cu);
+          const int64_t rr = (int64_t)p * nv + j;
+          if (rr < it.r0 || rr >= it.r0 + it.nr) continue;
+          put(a_hi, a_lo, (int)(rr - it.r0), col, gS[(int64_t)b * Np + p] * cu);
         }
       }
     }
@@ -346,11 +378,27 @@ struct Operand {
 
 Operand make_operand(const void* x, int dtype, int64_t rows, int cols, bool force_split, Scratch& sc, cudaStream_t s) {
   Operand o;
+  if (dtype != GIFT_F32 && !force_split && rows >= tc::kTM && reinterpret_cast<uintptr_t>(x) % 16 == 0) {
+    // a BF16 input is its own one-part operand: the tensor map covers its rows
+    o.hi = const_cast<__nv_bfloat16*>(static_cast<const __nv_bfloat16*>(x));
+    o.rows_alloc = rows;
+    return o;
+  }
   o.rows_alloc = rows + 128;
   const int64_t n = rows * cols;
   o.hi = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * cols);
   const bool split = dtype == GIFT_F32 || force_split;
   if (split) o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * cols);
+  const bool vec = dtype == GIFT_F32 && n % 4 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(o.hi) % 8 == 0 && reinterpret_cast<uintptr_t>(o.lo) % 8 == 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(n4, 256), (int64_t)device_sm_count() * 16);
+    k_split4<<<grid, 256, 0, s>>>(static_cast<const float4*>(x), n4, reinterpret_cast<uint2*>(o.hi),
+                                  reinterpret_cast<uint2*>(o.lo));
+    GIFT_LAUNCHED("k_split4");
+    return o;
+  }
   if (dtype == GIFT_F32)
     k_split_any<float><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(static_cast<const float*>(x), n, o.hi, o.lo);
   else
@@ -360,14 +408,15 @@ Operand make_operand(const void* x, int dtype, int64_t rows, int cols, bool forc
   return o;
 }
 
-// transposed two-part operand: out [cols, ld] with ld = rows rounded up to 64
+// transposed operand: out [cols, ld] with ld = rows rounded up to 64; two-part
+// for FP32 input, one-part (lo null) for BF16 input, which BF16 holds exactly
 Operand make_transposed(const void* x, int dtype, int64_t rows, int64_t cols, int64_t& ld, Scratch& sc,
                         cudaStream_t s) {
   Operand o;
   ld = cdiv(rows, 64) * 64;
   o.rows_alloc = cols + 128;
   o.hi = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
-  o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
+  if (dtype == GIFT_F32) o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
   const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(ld, 32)), blk(32, 8);
   if (dtype == GIFT_F32)
     k_transpose_split<float><<<grid, blk, 0, s>>>(static_cast<const float*>(x), rows, cols, o.hi, o.lo, ld);

@@ -12,7 +12,8 @@
 //   warps 2..5    epilogue; thread = TMEM lane = row of the A tile
 //
 // SPLIT = 3 multiplies two-part operands (x = hi + lo, both BF16):
-// hi*hi + hi*lo + lo*hi. Chunking the reduction dimension bounds how many
+// hi*hi + hi*lo + lo*hi. SPLIT = 2 multiplies a two-part A with a B that is
+// exact in BF16 (hi*b + lo*b). Chunking the reduction dimension bounds how many
 // MMA steps feed one accumulator: the tensor-core FP32 accumulation is not
 // round-to-nearest, and the chunk partials are summed in FP32 on the CUDA
 // cores by the epilogue.
@@ -28,12 +29,17 @@
 //   void epi_chunk(const Item&, int c, uint32_t taddr, Ctx&, int m, uint8_t* warp_smem) const;
 //   void epi_end(const Item&, Ctx&, int m, uint8_t* warp_smem) const;
 //   static constexpr int kWarpSmem;                           (bytes per epilogue warp)
-// Optionally (GEN_A = true) the A operand is not loaded by TMA but written by
-// the 32 lanes of warp 0 into the stage (128-byte swizzled, K-major):
-//   struct GenRegs;                                           (per-lane values of one k-block)
-//   void gen_load(const Item&, int kb, int lane, GenRegs&) const;
-//   void gen_store(const Item&, int kb, int lane, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
+// Optionally (GEN_A = true) the A operand is not loaded by TMA but written
+// into the stage (128-byte swizzled, K-major) by GEN_WARPS generator warps:
+// warp 0 and warps 6 .. 4 + GEN_WARPS; generator thread g = 32 * (generator
+// warp) + lane, g < 32 * GEN_WARPS. Each generator warp arrives on a stage's
+// full barrier once its part of the tile is written.
+//   static constexpr int GEN_WARPS;                           (1 .. 4)
+//   struct GenRegs;                                           (per-thread values of one k-block)
+//   void gen_load(const Item&, int kb, int g, GenRegs&) const;
+//   void gen_store(const Item&, int kb, int g, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
 //                  uint8_t* a_lo) const;             (prev: what this stage held last time, null on first use)
+// The engine zeroes every stage's A tiles before the first k-block.
 #pragma once
 #include <type_traits>
 
@@ -51,6 +57,16 @@ struct gen_a_of : std::false_type {};
 template <class P>
 struct gen_a_of<P, std::void_t<decltype(P::GEN_A)>> : std::integral_constant<bool, P::GEN_A> {};
 
+template <class P, class = void>
+struct gen_warps_of : std::integral_constant<int, 1> {};
+template <class P>
+struct gen_warps_of<P, std::void_t<decltype(P::GEN_WARPS)>> : std::integral_constant<int, P::GEN_WARPS> {};
+
+// threads of the engine CTA: producer, MMA, four epilogue warps, extra generator warps
+template <class P>
+struct engine_threads
+    : std::integral_constant<int, kEngineThreads + (gen_a_of<P>::value ? 32 * (gen_warps_of<P>::value - 1) : 0)> {};
+
 template <class P>
 struct EngineLayout {
   // one k-block = one 128-byte swizzle row of K: 64 BF16 or 128 E4M3 elements
@@ -58,8 +74,11 @@ struct EngineLayout {
   static constexpr int kABytes = kTM * 128;
   static constexpr int kBBytes = P::TN * 128;
   static_assert(P::EB == 2 || P::SPLIT == 1, "two-part operands are BF16");
-  static constexpr int kParts = P::SPLIT == 1 ? 1 : 2;
-  static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
+  static_assert(P::SPLIT == 1 || P::SPLIT == 2 || P::SPLIT == 3, "SPLIT is 1, 2 or 3");
+  static constexpr int kPartsA = P::SPLIT == 1 ? 1 : 2;
+  static constexpr int kPartsB = P::SPLIT == 3 ? 2 : 1;
+  // stage: A, B, then (two-part) A lo, then (SPLIT 3) B lo
+  static constexpr int kStageBytes = kPartsA * kABytes + kPartsB * kBBytes;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem;
   static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
@@ -67,7 +86,7 @@ struct EngineLayout {
 };
 
 template <class P>
-__global__ void __launch_bounds__(kEngineThreads, 1)
+__global__ void __launch_bounds__(engine_threads<P>::value, 1)
     tc_engine(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const P p,
               int* err) {
@@ -75,6 +94,9 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   constexpr int S = P::STAGES;
   constexpr int NB = P::NBUF;
   constexpr int TN = P::TN;
+  constexpr bool kGen = gen_a_of<P>::value;
+  constexpr int kGenWarps = kGen ? gen_warps_of<P>::value : 1;
+  static_assert(kGenWarps >= 1 && kGenWarps <= 4, "one to four generator warps");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -92,7 +114,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full0 + 8 * s, 1);
+      mbar_init(full0 + 8 * s, kGenWarps);
       mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < NB; ++b) {
@@ -105,6 +127,17 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
     tmem_alloc(smem_u32(tmem_holder), kCols);
     tmem_relinquish();
   }
+  if constexpr (kGen) {  // generated A tiles start as zeros
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int s = 0; s < S; ++s) {
+      uint8_t* st = tiles + s * L::kStageBytes;
+      for (int o = threadIdx.x * 16; o < L::kABytes; o += engine_threads<P>::value * 16) {
+        *reinterpret_cast<uint4*>(st + o) = z;
+        if (L::kPartsA == 2) *reinterpret_cast<uint4*>(st + L::kABytes + L::kBBytes + o) = z;
+      }
+    }
+    fence_proxy_async_smem();
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -113,11 +146,15 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
   constexpr uint32_t kIdesc = P::EB == 2 ? idesc_bf16(kTM, TN) : idesc_e4m3(kTM, TN);
   constexpr int KE = L::kKElems;
 
-  if (warp == 0) {
-    if constexpr (gen_a_of<P>::value) {
-      // all lanes write the A tile of every k-block, with the loads for the next
-      // two k-blocks in flight; lane 0 loads B by TMA
-      if (lane == 0) prefetch_tmap(&tmB);
+  if (warp == 0 || warp >= 6) {
+    if constexpr (kGen) {
+      // every generator thread writes its part of the A tile of every k-block,
+      // with the loads for the next two k-blocks in flight; lane 0 of warp 0
+      // loads B by TMA
+      const int gw = warp == 0 ? 0 : warp - 5;
+      const int gt = gw * 32 + lane;
+      const bool tma_lane = gw == 0 && lane == 0;
+      if (tma_lane) prefetch_tmap(&tmB);
       struct Cur {
         int64_t item;
         typename P::Item it;
@@ -171,19 +208,19 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       bool used[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
-      if (c0.valid) p.gen_load(c0.it, c0.kb, lane, ga);
-      if (c1.valid) p.gen_load(c1.it, c1.kb, lane, gb);
+      if (c0.valid) p.gen_load(c0.it, c0.kb, gt, ga);
+      if (c1.valid) p.gen_load(c1.it, c1.kb, gt, gb);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       int last_phase[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
-      constexpr uint32_t kBTx = L::kParts * L::kBBytes;
+      constexpr uint32_t kBTx = L::kPartsB * L::kBBytes;
       // one k-block: prefetch into `fill` for c2, write c0's tile from `use`
       auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill) -> bool {
         if (!ok || !c0.valid) return false;
-        if (c2.valid) p.gen_load(c2.it, c2.kb, lane, fill);
+        if (c2.valid) p.gen_load(c2.it, c2.kb, gt, fill);
         int w_ok = 1;
         if (lane == 0) w_ok = mbar_wait(empty0 + 8 * stage, phase ^ 1, err, kErrProducer) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
@@ -192,19 +229,21 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
           return false;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, lane, use, used[stage] ? &held[stage] : nullptr, st,
+        p.gen_store(c0.it, c0.kb, gt, use, used[stage] ? &held[stage] : nullptr, st,
                     st + L::kABytes + L::kBBytes);
         held[stage] = use;
         used[stage] = true;
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
+        if (tma_lane) {
           const uint32_t sa = smem_u32(st);
           mbar_expect_tx(full0 + 8 * stage, kBTx);
           tma_load_2d(sa + L::kABytes, &tmB, c0.kb * KE, c0.br, full0 + 8 * stage);
           if (P::SPLIT == 3)
             tma_load_2d(sa + 2 * L::kABytes + L::kBBytes, &tmB2, c0.kb * KE, c0.br, full0 + 8 * stage);
           last_phase[stage] = (int)phase;
+        } else if (lane == 0) {
+          mbar_arrive(full0 + 8 * stage);
         }
         if (++stage == S) {
           stage = 0;
@@ -220,7 +259,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       };
       while (step(ga, gc) && step(gb, ga) && step(gc, gb)) {
       }
-      if (!ok && lane == 0) {
+      if (!ok && tma_lane) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
           if (last_phase[s2] < 0) continue;
           const long long t0 = clock64();
@@ -255,10 +294,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
               mbar_expect_tx(full0 + 8 * stage, L::kStageBytes);
               tma_load_2d(st, &tmA, kb * KE, ar, full0 + 8 * stage);
               tma_load_2d(st + L::kABytes, &tmB, kb * KE, br, full0 + 8 * stage);
-              if (P::SPLIT == 3) {
-                tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * KE, ar, full0 + 8 * stage);
-                tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
-              }
+              if (P::SPLIT >= 2) tma_load_2d(st + L::kABytes + L::kBBytes, &tmA2, kb * KE, ar, full0 + 8 * stage);
+              if (P::SPLIT == 3) tma_load_2d(st + 2 * L::kABytes + L::kBBytes, &tmB2, kb * KE, br, full0 + 8 * stage);
               last_phase[stage] = (int)phase;
               if (++stage == S) {
                 stage = 0;
@@ -316,10 +353,8 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                 continue;
               }
               mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
-              if (P::SPLIT == 3) {
-                mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
-                mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
-              }
+              if (P::SPLIT == 3) mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
+              if (P::SPLIT >= 2) mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
             }
             mma_commit(empty0 + 8 * stage);
             if (++stage == S) {
@@ -337,7 +372,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp < 6) {
     const int quad = warp & 3;
     const int m = quad * 32 + lane;
     const int ew = warp - 2;
@@ -385,7 +420,7 @@ void launch_engine(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap
                    const P& p, int* err, int grid, cudaStream_t s) {
   using L = EngineLayout<P>;
   GIFT_CUDA(cudaFuncSetAttribute(tc_engine<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem));
-  tc_engine<P><<<grid, kEngineThreads, L::kSmem, s>>>(a, b, a2, b2, p, err);
+  tc_engine<P><<<grid, engine_threads<P>::value, L::kSmem, s>>>(a, b, a2, b2, p, err);
   GIFT_LAUNCHED("tc_engine");
 }
 

@@ -1,10 +1,13 @@
 // Plain GEMM on the tcgen05 engine: C[M, N] (+)= A[M, K] * B[N, K]^T with
-// A, B K-major BF16 (SPLIT = 1) or two-part BF16 (SPLIT = 3: hi*hi + hi*lo +
-// lo*hi, FP32-level), FP32 output. The reduction runs in up to four chunks,
+// A, B K-major BF16 (SPLIT = 1), two-part BF16 (SPLIT = 3: hi*hi + hi*lo +
+// lo*hi, FP32-level), or a two-part A with a B exact in BF16 (SPLIT = 2:
+// hi*b + lo*b), FP32 output. The reduction runs in up to four chunks,
 // each accumulated in its own TMEM buffer and summed in FP32 by the
 // epilogue (bounds the steps that feed one tensor-core accumulator).
-// Work items run column-tile-major so CTAs working at the same time share
-// the B tile.
+// Work items run along the longer side: with more row tiles than column
+// tiles they run row-tile-major, so the CTAs working at the same time share
+// each A tile (read from memory once) and all of B; otherwise column-tile-
+// major, sharing the B tile.
 #pragma once
 #include "tc_engine.cuh"
 
@@ -12,7 +15,7 @@ namespace gift {
 
 template <int SPLIT_>
 struct GemmPolicy {
-  static constexpr int TN = 128, NBUF = 4, STAGES = SPLIT_ == 1 ? 6 : 3, SPLIT = SPLIT_, EB = 2;
+  static constexpr int TN = 128, NBUF = 4, STAGES = SPLIT_ == 1 ? 6 : SPLIT_ == 2 ? 4 : 3, SPLIT = SPLIT_, EB = 2;
   static constexpr int kWarpSmem = 16;
   static constexpr int kChunks = 4;
   int64_t M, N;
@@ -20,6 +23,7 @@ struct GemmPolicy {
   float* C;
   int64_t ldc;
   int accumulate;
+  bool row_major;  // item order: row tile slow (true) or column tile slow
   struct Item {
     int64_t r0, c0;
     int nr, nc;
@@ -31,8 +35,8 @@ struct GemmPolicy {
   __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
   __device__ __forceinline__ Item decode(int64_t item) const {
     Item it;
-    const int64_t mt = n_mt();
-    const int64_t ct = item / mt, rt = item % mt;
+    const int64_t mt = n_mt(), nt = cdiv(N, TN);
+    const int64_t ct = row_major ? item % nt : item / mt, rt = row_major ? item / nt : item % mt;
     it.r0 = rt * tc::kTM;
     it.c0 = ct * TN;
     it.nr = (int)min((int64_t)tc::kTM, M - it.r0);
@@ -92,9 +96,10 @@ struct GemmPolicy {
   }
 };
 
-// Two-part (SPLIT 3) or one-part (SPLIT 1, when a lo part is null) BF16
-// operands, each allocated with at least one TMA box (128 rows) of rows;
-// lda / ldb are row pitches in elements (0 = K): C[M, N] (+)= A * B^T.
+// Two-part (SPLIT 3), two-part A with one-part B (SPLIT 2, b_lo null) or
+// one-part (SPLIT 1, both lo parts null) BF16 operands; a_rows_alloc /
+// b_rows_alloc are the rows the tensor maps cover (rows past M or N read as
+// zeros); lda / ldb are row pitches in elements (0 = K): C[M, N] (+)= A * B^T.
 void gemm_tc(const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo, int64_t M, int64_t a_rows_alloc, int64_t lda,
              const __nv_bfloat16* b_hi, const __nv_bfloat16* b_lo, int64_t N, int64_t b_rows_alloc, int64_t ldb, int K,
              float* C, int64_t ldc, int accumulate, int* err, cudaStream_t s);

@@ -7,10 +7,11 @@ from oracle import gift_oracle as O
 pytestmark = pytest.mark.gpu
 
 
-def _tie_free(seed, B, Np, nv, din, dout, margin=1e-3, vq=None):
+def _tie_free(seed, B, Np, nv, din, dout, margin=1e-3, vq=None, counts=None):
     g = np.random.default_rng(seed)
     while True:
-        counts = np.full(B, nv) if vq is None else g.choice(vq, size=B)
+        if counts is None:
+            counts = np.full(B, nv) if vq is None else g.choice(vq, size=B)
         off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
         Q = g.standard_normal((off[-1], din)).astype(np.float32)
         P = g.standard_normal((Np, nv, din)).astype(np.float32)
@@ -102,3 +103,31 @@ def test_bf16_inputs_forward_backward(gpu_lib):
     S2 = gpu_lib.GiftMatch.apply(q, off, pb, wb)
     (S2 * torch.from_numpy(G).cuda()).sum().backward()
     assert q.grad.dtype == torch.bfloat16
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_wide_shapes_several_tiles(gpu_lib, dtype):
+    """64 views per database shape and ragged query view counts: the forward's
+    short-reduction epilogue (two whole shapes per 128-column tile), the
+    gradient GEMMs with the A tile generated by four warps (one shape per
+    k-block on the query side, up to three shapes per 128-row tile on the
+    database side), BF16 inputs read in place, several row tiles with ragged
+    tails — all against the oracle in full."""
+    import torch
+    Q, off, P, W, G = _tie_free(6, B=4, Np=5, nv=64, din=96, dout=128, margin=1e-5, counts=(40, 100, 64, 57))
+    if dtype == "bf16":
+        qd, pd, wd = (torch.from_numpy(a).to(torch.bfloat16).cuda() for a in (Q, P, W))
+        Q, P, W = (t.float().cpu().numpy() for t in (qd, pd, wd))
+    else:
+        qd, pd, wd = (torch.from_numpy(a).cuda() for a in (Q, P, W))
+    assert off[-1] > 128 and P.shape[0] * P.shape[1] > 256
+    S, am = gpu_lib.match_forward(qd, off, pd, wd)
+    Sr, jr = O.match_forward(Q, off, P, W)
+    assert np.allclose(S.cpu().numpy(), Sr, rtol=1e-5, atol=1e-6)
+    assert np.array_equal(am.cpu().numpy().astype(np.int64), jr)
+    dW, dQ, dP = gpu_lib.match_backward(qd, off, pd, wd, torch.from_numpy(G).cuda(), am)
+    rW, rQ, rP = O.match_backward(Q, off, P, W, G)
+    scale = max(np.abs(rQ).max(), np.abs(rP).max())
+    assert np.allclose(dQ.cpu().numpy(), rQ, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dP.cpu().numpy(), rP, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
