@@ -87,6 +87,34 @@ __global__ void k_transpose_split(const T* __restrict__ in, int64_t rows, int64_
   }
 }
 
+// out[c, r] = in[r, c] for BF16 (one part), 64 x 64 tiles moved in 16-byte
+// pieces (cols % 8 == 0, ld % 64 == 0, 16-byte aligned rows); zero for rows <= r < ld
+__global__ __launch_bounds__(256) void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int64_t rows,
+                                                        int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ld) {
+  __shared__ __nv_bfloat16 t[64][72];
+  const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+  const int tid = threadIdx.x, part = tid & 7;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int row = (tid >> 3) + 32 * i;
+    const int64_t r = r0 + row, c = c0 + part * 8;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < rows && c < cols) v = *reinterpret_cast<const uint4*>(in + r * cols + c);
+    *reinterpret_cast<uint4*>(&t[row][part * 8]) = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int oc = (tid >> 3) + 32 * i;
+    const int64_t c = c0 + oc, r = r0 + part * 8;
+    if (c >= cols || r >= ld) continue;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = t[part * 8 + k][oc];
+    *reinterpret_cast<uint4*>(out + c * ld + r) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
 // ---------------------------------------------------------------- one-hot gradient GEMMs
 // k-blocks per accumulator chunk: 16 x 4 sub-steps x 3 products = 192 MMA steps
 constexpr int kOneHotChunkKB = 16;
@@ -124,9 +152,13 @@ struct OneHotPolicy {
   // thread g owns column g % 64 of shapes 0 and 2 (g < 64) or shape 1); other
   // layouts are written by warp 0 alone inside gen_store
   bool fast;
-  struct GenRegs {
-    int pos[2];   // row * 64 + column in the A tile, -1 = none
+  int kb_per_shape;  // ROWS_Q fast layout: N_v / 64 k-blocks per shape
+  struct GenRegs {  // loaded argmax (-1: none) and weight of the thread's entries
+    int j[2];
     float w[2];
+  };
+  struct GenPos {
+    int pos[2];  // row * 64 + column in the A tile, -1 = none
   };
   __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
   __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
@@ -148,20 +180,22 @@ struct OneHotPolicy {
   }
   __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
   // the argmax and weight lines of k-block kb + kPrefetchKB are pulled into L2
-  // while this k-block's are loaded: their loads, two k-blocks ahead of use,
-  // then hit L2 instead of waiting on DRAM
+  // while this k-block's are loaded
   static constexpr int kPrefetchKB = 8;
+  // issue the loads of k-block kb (their values are first read by gen_store)
   __device__ __forceinline__ void gen_load(const Item& it, int kb, int g, GenRegs& r) const {
-    r.pos[0] = r.pos[1] = -1;
+    r.j[0] = r.j[1] = -1;
+    r.w[0] = r.w[1] = 0.f;
     if (!fast) return;
     const int64_t k0 = (int64_t)kb * 64;
     if (ROWS_Q) {
       if (k0 >= nr) return;
-      const int p = (int)(k0 / nv);
+      const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
       {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 0..5
         const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
         if (kp < nr && g < 6) {
-          const int64_t e = (kp / nv) * nq + it.r0;
+          const int pp = kb_per_shape == 1 ? kb + kPrefetchKB : (kb + kPrefetchKB) / kb_per_shape;
+          const int64_t e = (int64_t)pp * nq + it.r0;
           const int off = g < 2 ? g * 64 : (g - 2) * 32;  // first row of the line
           if (it.r0 + off < nq) {
             if (g < 2)
@@ -171,17 +205,14 @@ struct OneHotPolicy {
           }
         }
       }
-      if (g >= it.nr) return;
-      const int64_t e = (int64_t)p * nq + it.r0 + g;
-      const int j = amT[e];
-      const float w = wT[e];
-      const int64_t rr = (int64_t)p * nv + (j >= 0 && j < nv ? j : 0);
-      if (rr < k0 || rr >= k0 + 64) return;
-      r.pos[0] = g * 64 + (int)(rr - k0);
-      r.w[0] = w;
+      if (g < it.nr) {
+        const int64_t e = (int64_t)p * nq + it.r0 + g;
+        r.j[0] = amT[e];
+        r.w[0] = wT[e];
+      }
     } else {
       if (k0 >= nq) return;
-      const int p0 = (int)(it.r0 / nv);
+      const int p0 = (int)it.r0 / nv;  // rows < 2^31
       {  // three shapes x 64 query views: 128 bytes of argmax and 256 of weights each
         const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
         if (kp < nq && g < 9) {
@@ -196,28 +227,16 @@ struct OneHotPolicy {
           }
         }
       }
-      const int col = g & 63;
-      const int64_t i = k0 + col;
+      const int64_t i = k0 + (g & 63);
       if (i >= nq) return;
-      int jj[2];
-      float ww[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {  // independent loads first
-        const int t = (g >> 6) + 2 * q;
-        const bool ok = t < 3 && p0 + t < Np;
-        const int64_t e = (int64_t)(p0 + t) * nq + i;
-        jj[q] = ok ? amT[e] : -1;
-        ww[q] = ok ? wT[e] : 0.f;
-      }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int t = (g >> 6) + 2 * q;
-        if (t >= 3 || p0 + t >= Np) continue;
-        const int j = jj[q];
-        const int64_t rr = (int64_t)(p0 + t) * nv + (j >= 0 && j < nv ? j : 0);
-        if (rr < it.r0 || rr >= it.r0 + it.nr) continue;
-        r.pos[q] = (int)(rr - it.r0) * 64 + col;
-        r.w[q] = ww[q];
+        if (t < 3 && p0 + t < Np) {
+          const int64_t e = (int64_t)(p0 + t) * nq + i;
+          r.j[q] = amT[e];
+          r.w[q] = wT[e];
+        }
       }
     }
   }
@@ -229,8 +248,9 @@ struct OneHotPolicy {
     *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
   }
-  __device__ __forceinline__ void gen_store(const Item& it, int kb, int g, const GenRegs& r, const GenRegs* prev,
-                                            uint8_t* a_hi, uint8_t* a_lo) const {
+  __device__ __forceinline__ void gen_store(const Item& it, int kb, int g, const GenRegs& r, const GenPos* prev,
+                                            GenPos& now, uint8_t* a_hi, uint8_t* a_lo) const {
+    now.pos[0] = now.pos[1] = -1;
     if (fast) {
       // the tile is zero but for the entries this thread wrote into it last time
       // (a position belongs to one thread: its row, or its column and shape)
@@ -239,9 +259,28 @@ struct OneHotPolicy {
         for (int e = 0; e < 2; ++e)
           if (prev->pos[e] >= 0) put(a_hi, a_lo, prev->pos[e] >> 6, prev->pos[e] & 63, 0.f);
       }
+      const int64_t k0 = (int64_t)kb * 64;
+      if (ROWS_Q) {
+        const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
+        const int j = r.j[0];
+        if (j >= 0) {  // argmax comes from the forward; stay inside the shape
+          const int64_t rr = (int64_t)p * nv + (j < nv ? j : 0);
+          if (rr >= k0 && rr < k0 + 64) now.pos[0] = g * 64 + (int)(rr - k0);
+        }
+      } else {
+        const int p0 = (int)it.r0 / nv;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = r.j[q];
+          if (j < 0) continue;
+          const int t = (g >> 6) + 2 * q;
+          const int64_t rr = (int64_t)(p0 + t) * nv + (j < nv ? j : 0);
+          if (rr >= it.r0 && rr < it.r0 + it.nr) now.pos[q] = (int)(rr - it.r0) * 64 + (g & 63);
+        }
+      }
 #pragma unroll
       for (int e = 0; e < 2; ++e)
-        if (r.pos[e] >= 0) put(a_hi, a_lo, r.pos[e] >> 6, r.pos[e] & 63, r.w[e]);
+        if (now.pos[e] >= 0) put(a_hi, a_lo, now.pos[e] >> 6, now.pos[e] & 63, r.w[e]);
       return;
     }
     if (g >= 32) return;  // warp 0 writes the general layouts
@@ -417,6 +456,13 @@ Operand make_transposed(const void* x, int dtype, int64_t rows, int64_t cols, in
   o.rows_alloc = cols + 128;
   o.hi = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
   if (dtype == GIFT_F32) o.lo = sc.get<__nv_bfloat16>((size_t)o.rows_alloc * ld);
+  if (dtype != GIFT_F32 && cols % 8 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
+      reinterpret_cast<uintptr_t>(o.hi) % 16 == 0) {
+    const dim3 g64((unsigned)cdiv(cols, 64), (unsigned)cdiv(ld, 64));
+    k_transpose_bf16<<<g64, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), rows, cols, o.hi, ld);
+    GIFT_LAUNCHED("k_transpose_bf16");
+    return o;
+  }
   const dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(ld, 32)), blk(32, 8);
   if (dtype == GIFT_F32)
     k_transpose_split<float><<<grid, blk, 0, s>>>(static_cast<const float*>(x), rows, cols, o.hi, o.lo, ld);
@@ -535,7 +581,8 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.kinv = P.vinv;
     pol.wT = wU;
     pol.C = G;
-    pol.fast = nv % 64 == 0;
+    pol.fast = nv % 64 == 0 && nr < ((int64_t)1 << 31);
+    pol.kb_per_shape = nv / 64;
     const CUtensorMap tB = make_tmap_bf16(Vt.hi, Vt.rows_alloc, ldr, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Vt.lo, Vt.rows_alloc, ldr, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nq, tc::kTM) * cdiv(dout, 128)),
@@ -561,7 +608,8 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     pol.kinv = P.uinv;
     pol.wT = wV;
     pol.C = G;
-    pol.fast = nv >= 64;
+    pol.fast = nv >= 64 && nr < ((int64_t)1 << 31);
+    pol.kb_per_shape = 1;
     const CUtensorMap tB = make_tmap_bf16(Ut.hi, Ut.rows_alloc, ldq, 128);
     const CUtensorMap tB2 = make_tmap_bf16(Ut.lo, Ut.rows_alloc, ldq, 128);
     tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nr, tc::kTM) * cdiv(dout, 128)),

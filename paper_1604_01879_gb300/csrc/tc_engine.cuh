@@ -32,12 +32,15 @@
 // Optionally (GEN_A = true) the A operand is not loaded by TMA but written
 // into the stage (128-byte swizzled, K-major) by GEN_WARPS generator warps:
 // warp 0 and warps 6 .. 4 + GEN_WARPS; generator thread g = 32 * (generator
-// warp) + lane, g < 32 * GEN_WARPS. Each generator warp arrives on a stage's
-// full barrier once its part of the tile is written.
+// warp) + lane, g < 32 * GEN_WARPS. Lane 0 of warp 0 starts the B copy as
+// soon as a stage is free; each generator warp arrives on the stage's full
+// barrier once its part of the A tile is written.
 //   static constexpr int GEN_WARPS;                           (1 .. 4)
-//   struct GenRegs;                                           (per-thread values of one k-block)
+//   struct GenRegs;          (per-thread loads of one k-block: gen_load only issues them, and nothing reads
+//                             them before gen_store two k-blocks later, so their latency is hidden)
+//   struct GenPos;           (the tile entries a thread wrote)
 //   void gen_load(const Item&, int kb, int g, GenRegs&) const;
-//   void gen_store(const Item&, int kb, int g, const GenRegs&, const GenRegs* prev, uint8_t* a_hi,
+//   void gen_store(const Item&, int kb, int g, const GenRegs&, const GenPos* prev, GenPos& now, uint8_t* a_hi,
 //                  uint8_t* a_lo) const;             (prev: what this stage held last time, null on first use)
 // The engine zeroes every stage's A tiles before the first k-block.
 #pragma once
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
       // three register sets rotate by name, so the loads for a k-block are
       // issued two k-blocks before their values are used (no copies between)
       typename P::GenRegs ga, gb, gc;
-      typename P::GenRegs held[S];  // what each stage's A tile holds (its previous k-block)
+      typename P::GenPos held[S];  // what each stage's A tile holds (its previous k-block)
       bool used[S];
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
@@ -229,22 +232,22 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
           return false;
         }
         uint8_t* st = tiles + stage * L::kStageBytes;
-        p.gen_store(c0.it, c0.kb, gt, use, used[stage] ? &held[stage] : nullptr, st,
-                    st + L::kABytes + L::kBBytes);
-        held[stage] = use;
-        used[stage] = true;
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (tma_lane) {
+        if (tma_lane) {  // B is in flight while the A tile is written
           const uint32_t sa = smem_u32(st);
-          mbar_expect_tx(full0 + 8 * stage, kBTx);
+          mbar_expect_tx_only(full0 + 8 * stage, kBTx);
           tma_load_2d(sa + L::kABytes, &tmB, c0.kb * KE, c0.br, full0 + 8 * stage);
           if (P::SPLIT == 3)
             tma_load_2d(sa + 2 * L::kABytes + L::kBBytes, &tmB2, c0.kb * KE, c0.br, full0 + 8 * stage);
           last_phase[stage] = (int)phase;
-        } else if (lane == 0) {
-          mbar_arrive(full0 + 8 * stage);
         }
+        typename P::GenPos now;
+        p.gen_store(c0.it, c0.kb, gt, use, used[stage] ? &held[stage] : nullptr, now, st,
+                    st + L::kABytes + L::kBBytes);
+        held[stage] = now;
+        used[stage] = true;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full0 + 8 * stage);
         if (++stage == S) {
           stage = 0;
           phase ^= 1;

@@ -1,8 +1,8 @@
 // Plain GEMM on the tcgen05 engine: C[M, N] (+)= A[M, K] * B[N, K]^T with
 // A, B K-major BF16 (SPLIT = 1), two-part BF16 (SPLIT = 3: hi*hi + hi*lo +
 // lo*hi, FP32-level), or a two-part A with a B exact in BF16 (SPLIT = 2:
-// hi*b + lo*b), FP32 output. The reduction runs in up to four chunks,
-// each accumulated in its own TMEM buffer and summed in FP32 by the
+// hi*b + lo*b), FP32 output. The reduction runs in chunks of at most 16
+// k-blocks, each accumulated in its own TMEM buffer and summed in FP32 by the
 // epilogue (bounds the steps that feed one tensor-core accumulator).
 // Work items run along the longer side: with more row tiles than column
 // tiles they run row-tile-major, so the CTAs working at the same time share
@@ -17,7 +17,6 @@ template <int SPLIT_>
 struct GemmPolicy {
   static constexpr int TN = 128, NBUF = 4, STAGES = SPLIT_ == 1 ? 6 : SPLIT_ == 2 ? 4 : 3, SPLIT = SPLIT_, EB = 2;
   static constexpr int kWarpSmem = 16;
-  static constexpr int kChunks = 4;
   int64_t M, N;
   int nkb;
   float* C;
@@ -44,10 +43,11 @@ struct GemmPolicy {
     return it;
   }
   // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
-  // x 4 sub-steps per k-block); short reductions use one chunk
+  // x 4 sub-steps per k-block), however long the reduction (the weight
+  // gradient reduces over every database view); short reductions use one chunk
   __device__ __forceinline__ int nch() const {
     const int want = (nkb * 12 + 191) / 192;
-    return want < 1 ? 1 : (want > kChunks ? kChunks : want);
+    return want < 1 ? 1 : want;
   }
   __device__ __forceinline__ int nchunks(const Item&) const { return nch(); }
   __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {

@@ -101,6 +101,9 @@ def test_sampled_sif_entries_and_rerank(c2):
         assert abs(O.contextual(Fq, F(int(p))) - v) < 1e-4
 
 
+DIFF_SAMPLED_SHAPES = (5, 3001)
+
+
 @pytest.fixture(scope="module")
 def diff(gpu_lib):
     import torch
@@ -115,9 +118,12 @@ def diff(gpu_lib):
     wb = torch.from_numpy(Wm).cuda().to(torch.bfloat16)
     off = np.arange(0, nq * nv + 1, nv, dtype=np.int32)
     S, am = gpu_lib.match_forward(qb, off, pb, wb)
-    dW, dQ, dP = gpu_lib.match_backward(qb, off, pb, wb, torch.from_numpy(G).cuda(), am, need=(False, True, False))
+    dW, dQ, dP = gpu_lib.match_backward(qb, off, pb, wb, torch.from_numpy(G).cuda(), am, need=(False, True, True))
+    p_rows = {p: dP[p].cpu().numpy() for p in DIFF_SAMPLED_SHAPES}  # [nv, D] of sampled database shapes
+    del dP
     Qf, Pf, Wf = (t.float().cpu().numpy() for t in (qb, pb, wb))
-    yield dict(S=S.cpu().numpy(), am=am.cpu().numpy(), dQ=dQ.cpu().numpy(), Q=Qf, P=Pf, W=Wf, G=G, nv=nv, N=N)
+    yield dict(S=S.cpu().numpy(), am=am.cpu().numpy(), dQ=dQ.cpu().numpy(), dP=p_rows, Q=Qf, P=Pf, W=Wf, G=G,
+               nv=nv, N=N)
 
 
 def test_differentiation_sampled_views(diff):
@@ -146,3 +152,30 @@ def test_differentiation_sampled_views(diff):
         dU = ((c[:, None] * vsel).sum(0) - (c * ssel).sum() * Un[i]) / nu
         dq = dU @ W.astype(np.float64)
         assert np.allclose(diff["dQ"][rows[i]], dq, rtol=1e-4, atol=1e-5 * np.abs(dq).max())
+
+
+def test_differentiation_sampled_database_views(diff):
+    """dP of every view of two database shapes: each view r collects, over all
+    query views i whose argmax in its shape is r, c (u_i/|u_i| - s v_r/|v_r|) / |v_r|
+    (c = dL/dS / |V(x_b)|), mapped back through W."""
+    Q, P, W, G, nv, N = diff["Q"], diff["P"], diff["W"], diff["G"], diff["nv"], diff["N"]
+    W64 = W.astype(np.float64)
+    U = Q.astype(np.float64) @ W64.T
+    Un = U / np.linalg.norm(U, axis=1, keepdims=True)
+    b_of = np.arange(Q.shape[0]) // nv
+    for p in DIFF_SAMPLED_SHAPES:
+        V = P[p].astype(np.float64) @ W64.T
+        nvr = np.linalg.norm(V, axis=1)
+        Vn = V / nvr[:, None]
+        s = Un @ Vn.T                     # [all query views, nv]
+        j = diff["am"][:, p].astype(np.int64)
+        top2 = np.sort(s, axis=1)[:, -2:]
+        assert np.all(s[np.arange(len(j)), j] >= top2[:, 1] - 1e-4)
+        c = G[b_of, p] / nv
+        dV = np.zeros_like(V)
+        for r in range(nv):
+            sel = j == r
+            if sel.any():
+                dV[r] = ((c[sel, None] * Un[sel]).sum(0) - (c[sel] * s[sel, r]).sum() * Vn[r]) / nvr[r]
+        dp = dV @ W64
+        assert np.allclose(diff["dP"][p], dp, rtol=1e-4, atol=1e-5 * np.abs(dp).max())
