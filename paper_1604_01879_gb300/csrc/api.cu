@@ -342,6 +342,12 @@ void build_lists(Index& ix_, Scratch& sc, cudaStream_t s, int32_t* pos = nullptr
 }
 
 // ------------------------------------------------------------------ query core
+// The BF16 store is the hi part of the two-part rescore rows (D > 64: the
+// fused pass splits the hi*hi products over two accumulators)
+bool fused_scan_ok(const Index& ix) {
+  return ix.prm.storage == GIFT_BF16 && ix.list_lo != nullptr && ix.list_hi == nullptr && ix.prm.dim > 64;
+}
+
 struct QueryOut {
   int32_t* ids;
   float* scores;
@@ -390,9 +396,19 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   fif_plan(ix, P, sc, s);
   uint32_t* table = sc.get<uint32_t>(P.table_upper);
   GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
+  // a BF16 store that is the hi part of the rescore rows: one fused pass gives
+  // the BF16 maxima (candidate selection) and the FP32-level maxima (rescore)
+  const bool fused = R > 0 && fused_scan_ok(ix);
+  uint32_t* table32 = nullptr;
+  if (fused) {
+    table32 = sc.get<uint32_t>(P.table_upper);
+    GIFT_CUDA(cudaMemsetAsync(table32, 0, P.table_upper * 4, s));
+  }
 
   tm.mark(ST_SCAN);
-  if (ix.prm.storage != GIFT_F32)
+  if (fused)
+    fif_scan_tc(ix, P, table, false, nullptr, 0, sc, s, table32);
+  else if (ix.prm.storage != GIFT_F32)
     fif_scan_tc(ix, P, table, false, nullptr, 0, sc, s);
   else
     fif_scan(ix, P, table, false, nullptr, 0, s);
@@ -413,13 +429,15 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   sort_ids_rows(cand, B, Rr, cand_sorted, s);
 
   tm.mark(ST_RESCORE);
-  GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
-  if (ix.list_lo)
-    fif_scan_tc(ix, P, table, true, cand_sorted, Rr, sc, s);
-  else
-    fif_scan(ix, P, table, true, cand_sorted, Rr, s);
+  if (!fused) {
+    GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
+    if (ix.list_lo)
+      fif_scan_tc(ix, P, table, true, cand_sorted, Rr, sc, s);
+    else
+      fif_scan(ix, P, table, true, cand_sorted, Rr, s);
+  }
   float* cand_score = sc.get<float>((size_t)B * Rr);
-  fif_combine(ix, P, table, nullptr, cand_sorted, Rr, cand_score, s);
+  fif_combine(ix, P, fused ? table32 : table, nullptr, cand_sorted, Rr, cand_score, s);
   tm.mark(ST_TOPK);
   sort_candidates(cand_sorted, cand_score, B, Rr, topk, out_ids, out_scores, s);
 }

@@ -35,9 +35,11 @@ struct FifPlan {
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s);
 void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
               const int32_t* cand_sorted, int R, cudaStream_t s);
-// tcgen05 scan of a BF16 store (rescore: two-part BF16, candidates only)
+// tcgen05 scan of a BF16 or E4M3 store (rescore: two-part BF16, candidates only;
+// table32 non-null: the fused pass of a BF16 store with its two-part rows, which
+// fills `table` with BF16 maxima and `table32` with FP32-level maxima of every run)
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
-                 int R, Scratch& sc, cudaStream_t s);
+                 int R, Scratch& sc, cudaStream_t s, uint32_t* table32 = nullptr);
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
                  const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s);
 

@@ -255,6 +255,87 @@ struct RescorePolicy : ListSched {
   }
 };
 
+// ---------------------------------------------------------------- fused scan + rescore policy
+// For a BF16 store that is also the hi part of the two-part rescore store:
+// one pass computes, per (slot, entry), hi*hi in two accumulators (first and
+// second half of the k-blocks, 128 MMA steps or fewer each) and hi*lo + lo*hi
+// in a third. The BF16 score (both hi*hi halves) fills the scan table, whose
+// top-R shapes are the rescore candidates; the FP32-level score (all three)
+// fills a second table, from which the candidates' rescored values are read,
+// so the separate scan pass over the BF16 store is not needed.
+struct FusedPolicy : ListSched {
+  // three accumulators leave room for one TMEM buffer, so the epilogue's drain
+  // stalls the next tile's MMAs: eight epilogue warps (two per lane quadrant,
+  // each over half of the columns) halve it; a run split between the halves
+  // is merged by the atomicMax of both partial maxima
+  static constexpr int TN = kRescTN, NBUF = 1, STAGES = 3, SPLIT = 3, EB = 2, ACCS = 3, EPI_SPLIT = 2;
+  static constexpr int kWarpSmem = TN * 12;
+  SlotInfo si;
+  uint32_t* table32;  // per-(slot, run) FP32-level maxima
+  using Item = ListItem;
+  struct Ctx {
+    RowCtx row;
+    int cur_run, half;
+    float cur_bf, cur_fp;
+  };
+  __device__ __forceinline__ static int acc_of(int product, int kb, int n) {
+    return product == 0 ? (kb < n / 2 ? 0 : 1) : 2;
+  }
+  __device__ __forceinline__ int64_t total() const { return total_items(); }
+  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
+  __device__ __forceinline__ int nchunks(const Item&) const { return 1; }
+  __device__ __forceinline__ void chunk(const Item& it, int, int& br, int& kb0, int& kb1) const {
+    br = (int)it.e0;
+    kb0 = 0;
+    kb1 = nkb;
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.s0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int ew, uint8_t* ws) const {
+    load_entry_meta<TN>(si, it, ws);
+    load_row(si, it, m, x.row);
+    x.cur_run = -1;
+    x.half = ew >> 2;
+    x.cur_bf = x.cur_fp = 0.f;
+  }
+  __device__ __forceinline__ void flush(const Ctx& x) const {
+    if (!x.row.valid || x.cur_run < 0) return;
+    if (x.cur_bf > 0.f) atomicMax(si.table + x.row.rb + x.cur_run, __float_as_uint(x.cur_bf));
+    if (x.cur_fp > 0.f) atomicMax(table32 + x.row.rb + x.cur_run, __float_as_uint(x.cur_fp));
+  }
+  __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
+    const int* e_run = reinterpret_cast<const int*>(ws);
+    const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
+    const int npieces = (it.ne + 31) >> 5;
+    const int pc1 = min(npieces, 2 * x.half + 2);
+    for (int pc = 2 * x.half; pc < pc1; ++pc) {
+      uint32_t h0[32], h1[32], cr[32];
+      tc::tmem_ld32(taddr + pc * 32, h0);
+      tc::tmem_ld32(taddr + TN + pc * 32, h1);
+      tc::tmem_ld32(taddr + 2 * TN + pc * 32, cr);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = pc * 32 + j;
+        const int run = e_run[c];
+        const float f = x.row.qi * e_scale[c];
+        const float hh = __uint_as_float(h0[j]) + __uint_as_float(h1[j]);
+        const float u = fmaxf(hh * f, 0.f);
+        const float v = fmaxf((hh + __uint_as_float(cr[j])) * f, 0.f);
+        if (run != x.cur_run) {
+          flush(x);
+          x.cur_run = run;
+          x.cur_bf = u;
+          x.cur_fp = v;
+        } else {
+          x.cur_bf = fmaxf(x.cur_bf, u);
+          x.cur_fp = fmaxf(x.cur_fp, v);
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ void epi_end(const Item&, Ctx& x, int, uint8_t*) const { flush(x); }
+};
+
 // slot-ordered BF16 copies of the query views: hi = bf16(q), lo = bf16(q - hi)
 __global__ void k_slot_split(const float* __restrict__ q, const int32_t* __restrict__ slot_view, int64_t nslots,
                              int D, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
@@ -317,10 +398,14 @@ __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t*
 }  // namespace
 
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
-                 int R, Scratch& sc, cudaStream_t s) {
+                 int R, Scratch& sc, cudaStream_t s, uint32_t* table32) {
   const int K = ix.prm.n_codewords, D = ix.prm.dim;
   const int64_t ns = P.nslots;
   if (ns <= 0) return;
+  const bool fused = table32 != nullptr;
+  GIFT_REQUIRE(!fused || (!rescore && ix.prm.storage == GIFT_BF16 && ix.list_lo && !ix.list_hi && D > 64),
+               "the fused scan needs a BF16 store with its two-part rescore rows");
+  if (fused) rescore = true;  // slot low parts, rescore tile width
   const bool fp8 = !rescore && ix.prm.storage == GIFT_FP8_E4M3;
   const int64_t qrows = ns + tc::kTM;  // one box of padding rows
   __nv_bfloat16* qhi = nullptr;
@@ -387,6 +472,18 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     if (P.kc) P.kc->begin(1);
     tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
     if (P.kc) P.kc->end(1);
+  } else if (fused) {
+    FusedPolicy pol;
+    static_cast<ListSched&>(pol) = ls;
+    pol.si = si;
+    pol.table32 = table32;
+    const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
+    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, FusedPolicy::TN);
+    const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
+    const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, FusedPolicy::TN);
+    if (P.kc) P.kc->begin(2);
+    tc::launch_engine(tA, tB, tA2, tB2, pol, ix.d_err, grid, s);
+    if (P.kc) P.kc->end(2);
   } else {
     GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the two-part BF16 list store");
     // BF16 index: the store itself is the hi part; FP8 index: a separate BF16 hi store

@@ -18,6 +18,12 @@
 // round-to-nearest, and the chunk partials are summed in FP32 on the CUDA
 // cores by the epilogue.
 //
+// Optionally (ACCS > 1) a chunk has several accumulators side by side in TMEM
+// (accumulator a at column a * TN of the chunk's buffer) and the policy routes
+// each product of each k-block to one of them:
+//   static constexpr int ACCS;
+//   static int acc_of(int product, int kb_in_chunk, int kbs_in_chunk);   (product: 0 hi*hi, 1 hi*lo, 2 lo*hi)
+//
 // A policy class P supplies the schedule and the epilogue:
 //   static constexpr int TN, NBUF, STAGES, SPLIT, EB;          (EB: operand bytes, 2 BF16 / 1 E4M3)
 //   struct Item; struct Ctx;                                  (per-thread epilogue state)
@@ -65,10 +71,23 @@ struct gen_warps_of : std::integral_constant<int, 1> {};
 template <class P>
 struct gen_warps_of<P, std::void_t<decltype(P::GEN_WARPS)>> : std::integral_constant<int, P::GEN_WARPS> {};
 
-// threads of the engine CTA: producer, MMA, four epilogue warps, extra generator warps
+template <class P, class = void>
+struct accs_of : std::integral_constant<int, 1> {};
+template <class P>
+struct accs_of<P, std::void_t<decltype(P::ACCS)>> : std::integral_constant<int, P::ACCS> {};
+
+// EPI_SPLIT = 2: eight epilogue warps, two per TMEM lane quadrant, each taking
+// half of the tile's columns (policy argument ew = warp - 2, column half ew / 4)
+template <class P, class = void>
+struct epi_split_of : std::integral_constant<int, 1> {};
+template <class P>
+struct epi_split_of<P, std::void_t<decltype(P::EPI_SPLIT)>> : std::integral_constant<int, P::EPI_SPLIT> {};
+
+// threads of the engine CTA: producer, MMA, epilogue warps, extra generator warps
 template <class P>
 struct engine_threads
-    : std::integral_constant<int, kEngineThreads + (gen_a_of<P>::value ? 32 * (gen_warps_of<P>::value - 1) : 0)> {};
+    : std::integral_constant<int, kEngineThreads + 128 * (epi_split_of<P>::value - 1) +
+                                      (gen_a_of<P>::value ? 32 * (gen_warps_of<P>::value - 1) : 0)> {};
 
 template <class P>
 struct EngineLayout {
@@ -83,8 +102,12 @@ struct EngineLayout {
   // stage: A, B, then (two-part) A lo, then (SPLIT 3) B lo
   static constexpr int kStageBytes = kPartsA * kABytes + kPartsB * kBBytes;
   static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + 4 * P::kWarpSmem;
-  static_assert(P::NBUF * P::TN <= 512, "TMEM holds 512 columns");
+  static constexpr int kEpiWarps = 4 * epi_split_of<P>::value;
+  static_assert(epi_split_of<P>::value == 1 || epi_split_of<P>::value == 2, "EPI_SPLIT is 1 or 2");
+  static_assert(epi_split_of<P>::value == 1 || !gen_a_of<P>::value, "generated A tiles take four epilogue warps");
+  static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + kEpiWarps * P::kWarpSmem;
+  static constexpr int kAccs = accs_of<P>::value;
+  static_assert(P::NBUF * kAccs * P::TN <= 512, "TMEM holds 512 columns");
   static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
@@ -112,8 +135,10 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
   const uint32_t empty0 = full0 + 8 * S;
   const uint32_t tfull0 = empty0 + 8 * S;
   const uint32_t tempty0 = tfull0 + 8 * NB;
-  constexpr uint32_t kCols = (NB * TN <= 32) ? 32 : (NB * TN <= 64) ? 64 : (NB * TN <= 128) ? 128
-                             : (NB * TN <= 256) ? 256 : 512;
+  constexpr int kAccs = L::kAccs;
+  constexpr int kBufCols = kAccs * TN;  // TMEM columns of one chunk buffer
+  constexpr uint32_t kCols = (NB * kBufCols <= 32) ? 32 : (NB * kBufCols <= 64) ? 64 : (NB * kBufCols <= 128) ? 128
+                             : (NB * kBufCols <= 256) ? 256 : 512;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -122,7 +147,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
     }
     for (int b = 0; b < NB; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 4);
+      mbar_init(tempty0 + 8 * b, L::kEpiWarps);
     }
     fence_barrier_init();
   }
@@ -149,7 +174,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
   constexpr uint32_t kIdesc = P::EB == 2 ? idesc_bf16(kTM, TN) : idesc_e4m3(kTM, TN);
   constexpr int KE = L::kKElems;
 
-  if (warp == 0 || warp >= 6) {
+  if (warp == 0 || (kGen && warp >= 6)) {
     if constexpr (kGen) {
       // every generator thread writes its part of the A tile of every k-block,
       // with the loads for the next two k-blocks in flight; lane 0 of warp 0
@@ -336,7 +361,9 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
             break;
           }
           fence_after_sync();
-          const uint32_t d = tmem + buf * TN;
+          const uint32_t d = tmem + buf * kBufCols;
+          uint32_t written = 0;  // accumulators of this chunk written so far (kAccs > 1)
+          (void)written;
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(full0 + 8 * stage, phase, err, kErrMma)) {
               ok = false;
@@ -348,16 +375,39 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
             const uint32_t sa2 = sb + L::kBBytes;
             const uint32_t sb2 = sa2 + L::kABytes;
             // four MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 elements)
+            if constexpr (kAccs == 1) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t acc_in = (kb != kb0 || kk != 0) ? 1u : 0u;
-              if (P::EB == 1) {
-                mma_f8(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
-                continue;
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc_in = (kb != kb0 || kk != 0) ? 1u : 0u;
+                if (P::EB == 1) {
+                  mma_f8(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
+                  continue;
+                }
+                mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
+                if (P::SPLIT == 3) mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
+                if (P::SPLIT >= 2) mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
               }
-              mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
-              if (P::SPLIT == 3) mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
-              if (P::SPLIT >= 2) mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
+            } else {
+              static_assert(P::EB == 2, "routed accumulators take BF16 products");
+              const int a0 = P::acc_of(0, kb - kb0, kb1 - kb0);
+              const int a1 = P::acc_of(1, kb - kb0, kb1 - kb0);
+              const int a2 = P::acc_of(2, kb - kb0, kb1 - kb0);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                mma_f16(d + a0 * TN, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc,
+                        (written >> a0) & 1u);
+                written |= 1u << a0;
+                if (P::SPLIT == 3) {
+                  mma_f16(d + a1 * TN, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc,
+                          (written >> a1) & 1u);
+                  written |= 1u << a1;
+                }
+                if (P::SPLIT >= 2) {
+                  mma_f16(d + a2 * TN, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc,
+                          (written >> a2) & 1u);
+                  written |= 1u << a2;
+                }
+              }
             }
             mma_commit(empty0 + 8 * stage);
             if (++stage == S) {
@@ -375,7 +425,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
       }
     }
     __syncwarp();
-  } else if (warp < 6) {
+  } else if (warp < 2 + L::kEpiWarps) {
     const int quad = warp & 3;
     const int m = quad * 32 + lane;
     const int ew = warp - 2;
@@ -396,7 +446,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
           break;
         }
         fence_after_sync();
-        p.epi_chunk(it, c, tmem + (static_cast<uint32_t>(quad * 32) << 16) + buf * TN, ctx, m, my);
+        p.epi_chunk(it, c, tmem + (static_cast<uint32_t>(quad * 32) << 16) + buf * kBufCols, ctx, m, my);
         fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
