@@ -265,17 +265,17 @@ struct RescorePolicy : ListSched {
 // so the separate scan pass over the BF16 store is not needed.
 struct FusedPolicy : ListSched {
   // three accumulators leave room for one TMEM buffer, so the epilogue's drain
-  // stalls the next tile's MMAs: eight epilogue warps (two per lane quadrant,
-  // each over half of the columns) halve it; a run split between the halves
-  // is merged by the atomicMax of both partial maxima
-  static constexpr int TN = kRescTN, NBUF = 1, STAGES = 3, SPLIT = 3, EB = 2, ACCS = 3, EPI_SPLIT = 2;
+  // stalls the next tile's MMAs: sixteen epilogue warps (four per lane
+  // quadrant, each over a quarter of the columns) shorten it; a run split
+  // between quarters is merged by the atomicMax of the partial maxima
+  static constexpr int TN = kRescTN, NBUF = 1, STAGES = 3, SPLIT = 3, EB = 2, ACCS = 3, EPI_SPLIT = 4;
   static constexpr int kWarpSmem = TN * 12;
   SlotInfo si;
   uint32_t* table32;  // per-(slot, run) FP32-level maxima
   using Item = ListItem;
   struct Ctx {
     RowCtx row;
-    int cur_run, half;
+    int cur_run, part;
     float cur_bf, cur_fp;
   };
   __device__ __forceinline__ static int acc_of(int product, int kb, int n) {
@@ -294,7 +294,7 @@ struct FusedPolicy : ListSched {
     load_entry_meta<TN>(si, it, ws);
     load_row(si, it, m, x.row);
     x.cur_run = -1;
-    x.half = ew >> 2;
+    x.part = ew >> 2;
     x.cur_bf = x.cur_fp = 0.f;
   }
   __device__ __forceinline__ void flush(const Ctx& x) const {
@@ -305,17 +305,18 @@ struct FusedPolicy : ListSched {
   __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
     const int* e_run = reinterpret_cast<const int*>(ws);
     const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
-    const int npieces = (it.ne + 31) >> 5;
-    const int pc1 = min(npieces, 2 * x.half + 2);
-    for (int pc = 2 * x.half; pc < pc1; ++pc) {
-      uint32_t h0[32], h1[32], cr[32];
-      tc::tmem_ld32(taddr + pc * 32, h0);
-      tc::tmem_ld32(taddr + TN + pc * 32, h1);
-      tc::tmem_ld32(taddr + 2 * TN + pc * 32, cr);
+    // this warp's 32 columns, 16 at a time
+    const int npieces = (it.ne + 15) >> 4;
+    const int pc1 = min(npieces, 2 * x.part + 2);
+    for (int pc = 2 * x.part; pc < pc1; ++pc) {
+      uint32_t h0[16], h1[16], cr[16];
+      tc::tmem_ld16(taddr + pc * 16, h0);
+      tc::tmem_ld16(taddr + TN + pc * 16, h1);
+      tc::tmem_ld16(taddr + 2 * TN + pc * 16, cr);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = pc * 32 + j;
+      for (int j = 0; j < 16; ++j) {
+        const int c = pc * 16 + j;
         const int run = e_run[c];
         const float f = x.row.qi * e_scale[c];
         const float hh = __uint_as_float(h0[j]) + __uint_as_float(h1[j]);

@@ -76,8 +76,9 @@ struct accs_of : std::integral_constant<int, 1> {};
 template <class P>
 struct accs_of<P, std::void_t<decltype(P::ACCS)>> : std::integral_constant<int, P::ACCS> {};
 
-// EPI_SPLIT = 2: eight epilogue warps, two per TMEM lane quadrant, each taking
-// half of the tile's columns (policy argument ew = warp - 2, column half ew / 4)
+// EPI_SPLIT = 2 or 4: 4 * EPI_SPLIT epilogue warps, EPI_SPLIT per TMEM lane
+// quadrant, each taking 1 / EPI_SPLIT of the tile's columns (policy argument
+// ew = warp - 2, column part ew / 4)
 template <class P, class = void>
 struct epi_split_of : std::integral_constant<int, 1> {};
 template <class P>
@@ -103,7 +104,8 @@ struct EngineLayout {
   static constexpr int kStageBytes = kPartsA * kABytes + kPartsB * kBBytes;
   static constexpr int kBarBytes = 256;
   static constexpr int kEpiWarps = 4 * epi_split_of<P>::value;
-  static_assert(epi_split_of<P>::value == 1 || epi_split_of<P>::value == 2, "EPI_SPLIT is 1 or 2");
+  static_assert(epi_split_of<P>::value == 1 || epi_split_of<P>::value == 2 || epi_split_of<P>::value == 4,
+                "EPI_SPLIT is 1, 2 or 4");
   static_assert(epi_split_of<P>::value == 1 || !gen_a_of<P>::value, "generated A tiles take four epilogue warps");
   static constexpr int kSmem = 1024 + P::STAGES * kStageBytes + kBarBytes + kEpiWarps * P::kWarpSmem;
   static constexpr int kAccs = accs_of<P>::value;
