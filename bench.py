@@ -289,6 +289,10 @@ def main():
     ap.add_argument("--no-aca", action="store_true", help="skip the two-measure re-rank measurement")
     ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU k-means measurement")
     ap.add_argument("--no-render", action="store_true", help="skip the projection front end measurement")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="only the differentiation workload (forward + backward; for ncu launch lists)")
+    ap.add_argument("--diff-shapes", type=int, default=None, help="override its database shapes (small ncu case)")
+    ap.add_argument("--diff-queries", type=int, default=None, help="override its query shapes (small ncu case)")
     ap.add_argument("--rescore", type=int, default=None, help="override the config's rescore depth R")
     ap.add_argument("--oracle-queries", type=int, default=4, help="sampled queries for recall (large configs)")
     args = ap.parse_args()
@@ -371,6 +375,12 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     gift.load()
+    if args.diff_only:
+        if rank == 0:
+            print(json.dumps({"differentiation": bench_differentiation(
+                gift, torch, dev, torch.cuda.current_stream(), reps=max(1, args.steps), n_shapes=args.diff_shapes,
+                n_queries=args.diff_queries)}))
+        return
 
     t0 = time.time()
     build_s = None
@@ -828,11 +838,13 @@ def bench_kmeans(cfg, gift, torch, dev, stream, data):
             "note": "exact assignment (tensor-core quantiser) + float64 means; the host fixture uses FP32 distances"}
 
 
-def bench_differentiation(gift, torch, dev, stream, reps=3):
+def bench_differentiation(gift, torch, dev, stream, reps=3, n_shapes=None, n_queries=None):
     """Forward + backward of the projected match (Eq. 3 after u = W q) on the
-    differentiation workload; device-timed with CUDA events."""
+    differentiation workload (or a smaller one of the same recipe); device-timed
+    with CUDA events."""
     from synth import DIFF_WORKLOAD as W_, shape_views, projection_matrix, upstream_grad
     nq, N, nv, D, dout = W_["n_queries"], W_["n_shapes"], W_["n_views"], W_["dim"], W_["d_out"]
+    nq, N = n_queries or nq, n_shapes or N
     s = W_["seed"]
     q = torch.from_numpy(shape_views(0, nq, nv, D, W_["n_classes"], 2000 + s, 4000 + s)).to(dev).to(
         torch.bfloat16).reshape(nq * nv, D)
@@ -858,7 +870,8 @@ def bench_differentiation(gift, torch, dev, stream, reps=3):
     proj = 2.0 * (nq * nv + nr) * D * dout
     sim = 2.0 * (nq * nv) * nr * dout
     f_ms, b_ms = statistics.median(fw), statistics.median(bw)
-    out = {"workload": W_["name"], "forward_ms": f_ms, "backward_ms": b_ms,
+    name = W_["name"] if (nq, N) == (W_["n_queries"], W_["n_shapes"]) else f"match{nq}x{N}x{nv}_d{D}_p{dout}_bf16"
+    out = {"workload": name, "forward_ms": f_ms, "backward_ms": b_ms,
            "useful_tflop_fwd": (proj + sim) / 1e12, "useful_tflop_bwd": (proj + 2 * proj) / 1e12,
            "fwd_useful_tflops": (proj + sim) / (f_ms / 1e3) / 1e12,
            "bwd_useful_tflops": 3 * proj / (b_ms / 1e3) / 1e12,
