@@ -191,32 +191,35 @@ struct OneHotPolicy {
     if (ROWS_Q) {
       if (k0 >= nr) return;
       const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
-      {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 0..5
+      {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 32..37
+         // (not warp 0, which also starts the B copies)
         const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
-        if (kp < nr && g < 6) {
+        const int u = g - 32;
+        if (kp < nr && u >= 0 && u < 6) {
           const int pp = kb_per_shape == 1 ? kb + kPrefetchKB : (kb + kPrefetchKB) / kb_per_shape;
           const int64_t e = (int64_t)pp * nq + it.r0;
-          const int off = g < 2 ? g * 64 : (g - 2) * 32;  // first row of the line
+          const int off = u < 2 ? u * 64 : (u - 2) * 32;  // first row of the line
           if (it.r0 + off < nq) {
-            if (g < 2)
+            if (u < 2)
               tc::prefetch_l2(amT + e + off);
             else
               tc::prefetch_l2(wT + e + off);
           }
         }
       }
-      if (g < it.nr) {
+      if (g < it.nr) {  // read-only for the kernel's lifetime
         const int64_t e = (int64_t)p * nq + it.r0 + g;
-        r.j[0] = amT[e];
-        r.w[0] = wT[e];
+        r.j[0] = __ldg(amT + e);
+        r.w[0] = __ldg(wT + e);
       }
     } else {
       if (k0 >= nq) return;
       const int p0 = (int)it.r0 / nv;  // rows < 2^31
-      {  // three shapes x 64 query views: 128 bytes of argmax and 256 of weights each
+      {  // three shapes x 64 query views: 128 bytes of argmax and 256 of weights each,
+         // one line per thread 32..40
         const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
-        if (kp < nq && g < 9) {
-          const int t = g / 3, u = g % 3;
+        if (kp < nq && g >= 32 && g < 41) {
+          const int t = (g - 32) / 3, u = (g - 32) % 3;
           const int off = u == 0 ? 0 : (u - 1) * 32;  // first query view of the line
           if (p0 + t < Np && kp + off < nq) {
             const int64_t e = (int64_t)(p0 + t) * nq + kp + off;
@@ -234,8 +237,8 @@ struct OneHotPolicy {
         const int t = (g >> 6) + 2 * q;
         if (t < 3 && p0 + t < Np) {
           const int64_t e = (int64_t)(p0 + t) * nq + i;
-          r.j[q] = amT[e];
-          r.w[q] = wT[e];
+          r.j[q] = __ldg(amT + e);
+          r.w[q] = __ldg(wT + e);
         }
       }
     }

@@ -234,10 +234,12 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
       // three register sets rotate by name, so the loads for a k-block are
       // issued two k-blocks before their values are used (no copies between)
       typename P::GenRegs ga, gb, gc;
-      typename P::GenPos held[S];  // what each stage's A tile holds (its previous k-block)
-      bool used[S];
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) used[s2] = false;
+      // what each stage's A tile holds (its previous k-block): the loop below
+      // visits stages 0, 1, 2 in its three calls, so each call names its own
+      // record and the records stay in registers
+      static_assert(S == 3, "generated A tiles rotate through three stages");
+      typename P::GenPos held0, held1, held2;
+      bool used0 = false, used1 = false, used2 = false;
       if (c0.valid) p.gen_load(c0.it, c0.kb, gt, ga);
       if (c1.valid) p.gen_load(c1.it, c1.kb, gt, gb);
       int stage = 0;
@@ -248,7 +250,8 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
       for (int s2 = 0; s2 < S; ++s2) last_phase[s2] = -1;
       constexpr uint32_t kBTx = L::kPartsB * L::kBBytes;
       // one k-block: prefetch into `fill` for c2, write c0's tile from `use`
-      auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill) -> bool {
+      auto step = [&](typename P::GenRegs& use, typename P::GenRegs& fill, typename P::GenPos& held,
+                      bool& used) -> bool {
         if (!ok || !c0.valid) return false;
         if (c2.valid) p.gen_load(c2.it, c2.kb, gt, fill);
         int w_ok = 1;
@@ -268,10 +271,9 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
           last_phase[stage] = (int)phase;
         }
         typename P::GenPos now;
-        p.gen_store(c0.it, c0.kb, gt, use, used[stage] ? &held[stage] : nullptr, now, st,
-                    st + L::kABytes + L::kBBytes);
-        held[stage] = now;
-        used[stage] = true;
+        p.gen_store(c0.it, c0.kb, gt, use, used ? &held : nullptr, now, st, st + L::kABytes + L::kBBytes);
+        held = now;
+        used = true;
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(full0 + 8 * stage);
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
         }
         return true;
       };
-      while (step(ga, gc) && step(gb, ga) && step(gc, gb)) {
+      while (step(ga, gc, held0, used0) && step(gb, ga, held1, used1) && step(gc, gb, held2, used2)) {
       }
       if (!ok && tma_lane) {
         for (int s2 = 0; s2 < S; ++s2) {  // let issued copies land before exiting (bounded)
