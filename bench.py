@@ -488,21 +488,22 @@ def main():
     assign_rows = stages[-1][0]["assign_rows"]
 
     # ---- end to end through the C ABI with host buffers: pinned query features in,
-    # ids / scores out, every step; two streams alternate so that the copies of
-    # one batch overlap the kernels of the other
+    # ids / scores out, every step; three streams rotate so that the copies of
+    # one batch overlap the kernels of the others
     if large:  # pinned host copies of a few batches, cycled
         q_host = [(batches[i][0].cpu().pin_memory(), batches[i][1]) for i in range(min(nb, 8))]
     else:
         q_host = [(torch.from_numpy(data["q"][qoff[i * B]:qoff[(i + 1) * B]]).pin_memory(), batches[i][1])
                   for i in range(nb)]
-    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    n_streams = 3
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
     hq = [(torch.empty((B, topk), dtype=torch.int32).pin_memory(), torch.empty((B, topk)).pin_memory())
-          for _ in range(2)]
+          for _ in range(n_streams)]
     hr = [(torch.empty((B, topk), dtype=torch.int32).pin_memory(), torch.empty((B, topk)).pin_memory())
-          for _ in range(2)]
+          for _ in range(n_streams)]
 
     def e2e_step(i):
-        j = i % 2
+        j = i % n_streams
         qh, ob = q_host[i % len(q_host)]
         streams[j].synchronize()  # this stream's host buffers are free again
         ix.query(qh, ob, mode="fif", topk=topk, out=hq[j], stream=streams[j])
