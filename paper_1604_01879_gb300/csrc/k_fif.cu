@@ -351,6 +351,65 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
   }
 }
 
+// Candidate scores with multiple assignment (ma > 1): each warp takes one view
+// at a time; the runs of the view's ma lists fold their maxima into the warp's
+// shared array over the query's candidates (atomicMax on the float bits), so a
+// shape reached through several lists counts once with the largest maximum;
+// the array is then added into the block's fixed-point sums and cleared. The
+// candidates are looked up in a shared copy of the query's sorted list (the
+// dense sums keep k_fif_combine, whose warps look the other lists up directly).
+constexpr int kCombineWarps = kCombineT / 32;
+__global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const CombineArgs a) {
+  extern __shared__ unsigned long long acc[];  // [R] sums, then int32 cand[R], then uint32 [warps][R] view maxima
+  const int q = blockIdx.x, R = a.R;
+  int32_t* cs = reinterpret_cast<int32_t*>(acc + R);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* vmax = reinterpret_cast<uint32_t*>(cs + R) + (size_t)w * R;
+  for (int i = threadIdx.x; i < R; i += kCombineT) {
+    acc[i] = 0ull;
+    cs[i] = a.cand[(int64_t)q * R + i];
+  }
+  for (int i = lane; i < R; i += 32) vmax[i] = 0u;
+  __syncthreads();
+  const int v0 = a.qoff[q], v1 = a.qoff[q + 1];
+  for (int v = v0 + w; v < v1; v += kCombineWarps) {
+    // lane t < ma: the list of assignment t
+    int64_t off = 0, rb = 0;
+    int n = 0;
+    if (lane < a.ma) {
+      const int32_t sl = a.view_slot[(int64_t)v * a.ma + lane];
+      const int k = a.skeys[sl];
+      off = a.run_off[k];
+      rb = a.runbase[sl];
+      n = a.nruns[k];
+    }
+    for (int t = 0; t < a.ma; ++t) {
+      const int64_t o = __shfl_sync(0xffffffffu, off, t);
+      const int64_t b = __shfl_sync(0xffffffffu, rb, t);
+      const int nt = __shfl_sync(0xffffffffu, n, t);
+      for (int r = lane; r < nt; r += 32) {
+        const uint32_t m = a.table[b + r];
+        if (m == 0u) continue;  // non-negative float bits: 0 <=> no positive maximum
+        const int idx = find_sorted(cs, R, a.run_shape[o + r]);
+        if (idx >= 0) atomicMax(&vmax[idx], m);
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < R; i += 32) {
+      const uint32_t m = vmax[i];
+      if (m != 0u) {
+        atomicAdd(&acc[i], fix32(m));
+        vmax[i] = 0u;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const float Vq = (float)(v1 - v0);
+  for (int i = threadIdx.x; i < R; i += kCombineT)
+    a.cand_score[(int64_t)q * R + i] = __fdiv_rn(__ull2float_rn(acc[i]) * 2.3283064365386963e-10f, Vq);
+}
+
 }  // namespace
 
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s) {
@@ -437,6 +496,14 @@ void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float
   a.cand = cand_sorted;
   a.R = R;
   a.cand_score = cand_score;
+  if (P.ma > 1 && cand_sorted) {
+    GIFT_REQUIRE(R <= 1024, "rescore depth must be <= 1024");
+    const size_t smem = (size_t)R * (8 + 4 + 4 * kCombineWarps);
+    GIFT_CUDA(cudaFuncSetAttribute(k_fif_combine_ma_cand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fif_combine_ma_cand<<<(unsigned)P.B, kCombineT, smem, s>>>(a);
+    GIFT_LAUNCHED("k_fif_combine_ma_cand");
+    return;
+  }
   GIFT_CUDA(cudaFuncSetAttribute(k_fif_combine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kCombineChunk * 8));
   if (cand_sorted) {
