@@ -39,3 +39,19 @@ def test_roofline_without_tensor_core_scan():
                        "measured")
     assert r["kernel"] == "tc_engine<AssignPolicy>" and r["scan_hbm"]["achieved_gbs"] is None
     assert bench.roofline(cfg, _st(0.0, 0.0, 0.0), 0, 0, 0, 0, {"hbm_gbs": 1.0, "bf16_tflops": 1.0}, "m") is None
+
+
+def test_roofline_names_the_fused_pass():
+    """A BF16 store with rescore rows runs scan and rescore as one kernel: no scan time of its own,
+    the entry is the fused kernel with the three-product FLOPs over every scanned pair."""
+    cfg = CONFIGS["db12000x64_d4096_k1024"]
+    peaks = {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}
+    pairs = 7.46e8
+    r = bench.roofline(cfg, _st(0.0, 12.35, 0.97), pairs, 6e9, 12.5e9, 64000, peaks, "measured", with_traffic=False)
+    assert r["kernel"] == "tc_engine<FusedPolicy>" and r["bound"] == "tensor"
+    assert abs(r["achieved"] - 6 * pairs * cfg.dim / 12.35e-3 / 1e12) < 1e-6 * r["achieved"]
+    assert "tc_engine<ScanPolicy>" not in r["all"] and "tc_engine<RescorePolicy>" not in r["all"]
+    # an FP8 store keeps the separate scan and rescore
+    r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.1, 32.0, 1.0), pairs, 47e9, 188e9, 32768,
+                       peaks, "measured", with_traffic=False)
+    assert r["kernel"] == "tc_engine<RescorePolicy>" and "tc_engine<ScanPolicy>" in r["all"]
