@@ -355,9 +355,10 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
 // at a time; the runs of the view's ma lists fold their maxima into the warp's
 // shared array over the query's candidates (atomicMax on the float bits), so a
 // shape reached through several lists counts once with the largest maximum;
-// the array is then added into the block's fixed-point sums and cleared. The
-// candidates are looked up in a shared copy of the query's sorted list (the
-// dense sums keep k_fif_combine, whose warps look the other lists up directly).
+// the array is then added into the block's fixed-point sums and cleared. Each
+// list's runs are merged against a shared copy of the query's sorted candidates
+// (the dense sums keep k_fif_combine, whose warps look the other lists up
+// directly).
 constexpr int kCombineWarps = kCombineT / 32;
 __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const CombineArgs a) {
   extern __shared__ unsigned long long acc[];  // [R] sums, then int32 cand[R], then uint32 [warps][R] view maxima
@@ -387,11 +388,21 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
       const int64_t o = __shfl_sync(0xffffffffu, off, t);
       const int64_t b = __shfl_sync(0xffffffffu, rb, t);
       const int nt = __shfl_sync(0xffffffffu, n, t);
-      for (int r = lane; r < nt; r += 32) {
-        const uint32_t m = a.table[b + r];
-        if (m == 0u) continue;  // non-negative float bits: 0 <=> no positive maximum
-        const int idx = find_sorted(cs, R, a.run_shape[o + r]);
-        if (idx >= 0) atomicMax(&vmax[idx], m);
+      // runs (strictly ascending shape ids) and candidates (ascending) are merged:
+      // each lane walks a contiguous segment of the runs with a cursor into the
+      // candidates, and reads the table only for candidate shapes
+      const int seg = (nt + 31) >> 5;
+      const int r0 = min(nt, lane * seg), r1 = min(nt, r0 + seg);
+      if (r0 < r1) {
+        int c = lower_bound_i32(cs, R, a.run_shape[o + r0]);
+        for (int r = r0; r < r1 && c < R; ++r) {
+          const int32_t p = a.run_shape[o + r];
+          while (c < R && cs[c] < p) ++c;
+          if (c < R && cs[c] == p) {
+            const uint32_t m = a.table[b + r];
+            if (m != 0u) atomicMax(&vmax[c], m);  // non-negative float bits: 0 <=> no positive maximum
+          }
+        }
       }
     }
     __syncwarp();
