@@ -44,6 +44,8 @@ Readings where the paper is silent (each also listed in the design notes):
   assignment, queries ``ma``;
 * ranking ties go to the lower shape id; re-ranking orders by
   (S' desc, S desc, id asc); S' = 0 when both F vectors are zero;
+* an Eq. 7 membership is the positive part of the neighbour's score (a
+  negative score, possible only with signed features, gives membership 0);
 * a database shape's neighbour set N_k1 includes the shape itself;
 * rendering: the centroid is the area-weighted surface centroid; cameras use
   orthographic projection along the view axis (the image plane spans the unit
@@ -337,10 +339,13 @@ def membership(scores, k1):
     """Sparse activation F_q of Eq. 7: F[i] = S(x_q, x_i) if x_i in N_k1(x_q) else 0.
 
     N_k1 is the first k1 entries of the ranking of ``scores`` (float64 [N]).
+    F is a fuzzy-set membership (Eq. 8 compares memberships by min and max), so a
+    neighbour whose score is negative -- possible only with signed features --
+    has membership 0.
     """
     ids, vals = rank(scores, k1)
     F = np.zeros(np.asarray(scores).shape[0])
-    F[ids] = vals
+    F[ids] = np.maximum(vals, 0.0)
     return F
 
 

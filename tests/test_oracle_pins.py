@@ -308,6 +308,17 @@ def test_membership_vector_eq7():
     assert F.tolist() == [0.0, 0.8, 0.5, 0.8, 0.0]
 
 
+def test_membership_of_negative_scores_is_zero():
+    """A neighbour with a negative score (signed features) has membership 0: worked by hand,
+    the first four of the ranking are shapes 1, 3, 4, 0 and only 1 and 3 score above 0."""
+    s = np.array([-0.1, 0.9, -0.3, 0.4, -0.05])
+    assert O.membership(s, 4).tolist() == [0.0, 0.9, 0.0, 0.4, 0.0]
+    # Eq. 8 on such activations, scores +-1: the crisp Jaccard index of {1, 3} and {0, 3, 4}
+    Fa = O.membership(np.array([-1.0, 1.0, -1.0, 1.0, -0.5]), 4)
+    assert Fa.tolist() == [0.0, 1.0, 0.0, 1.0, 0.0]
+    assert O.contextual(Fa, np.array([1.0, 0.0, 0.0, 1.0, 1.0])) == pytest.approx(1 / 4, abs=1e-15)
+
+
 def test_contextual_reduces_to_crisp_jaccard():
     """With all memberships 1, Eq. 8 is the set Jaccard index of Eq. 5."""
     g = np.random.default_rng(3)
