@@ -112,6 +112,17 @@ typedef struct {
   float scan_kernel_ms;    /* tensor-core scan kernel alone (BF16 store)      */
   float rescore_kernel_ms; /* tensor-core rescore kernel alone                */
   int64_t assign_rows;     /* rows quantised                                  */
+  /* candidate work of the FP32 rescore (F-IF queries with rescore_r > 0): a
+     work item is (list, tile of 128 entries, tile of 128 query slots)        */
+  int64_t rescore_items;      /* work items of the touched lists                */
+  int64_t rescore_items_kept; /* items holding a run of one of their slots' query's
+                                 candidates: the items the rescore runs (the fused
+                                 pass of a BF16 store runs every item)          */
+  int64_t cand_pairs;         /* (slot, entry) pairs whose entry's shape is a
+                                 candidate of the slot's query                  */
+  int64_t cand_rows;          /* entries whose shape is a candidate of some slot
+                                 of their list: the rows the rescore needs      */
+  int64_t rescore_rows_read;  /* entries of the kept items                      */
 } gift_timing_t;
 
 /*
@@ -169,10 +180,11 @@ GIFT_API void gift_destroy_index(gift_index* index);
  *    then read in list order).
  *    mode GIFT_MATCH_FIF: Eq. 4: each query view is quantised to its query_ma
  *    nearest codewords, only the F-IF lists of those codewords are scanned,
- *    and a shape's view contributes only when its codeword is one of them;
- *    the per-(query view, shape) maximum is floored at 0 (the value Eq. 4
- *    gives a shape that has any non-matching view). With rescore_r > 0 the
- *    top rescore_r shapes are rescored with FP32 features (same Eq. 4).
+ *    and a shape's view contributes its cosine only when one of its codewords
+ *    is among them; every other view contributes 0 to the per-(query view,
+ *    shape) maximum, so a negative maximum (signed features) counts only when
+ *    every view of the shape is matched. With rescore_r > 0 the top rescore_r
+ *    shapes are rescored with FP32 features (same Eq. 4).
  *  - out_ids: device or host int32 [B * topk]; out_scores: device or host
  *    float [B * topk]; each row ordered by (score desc, shape id asc). When
  *    N < topk the tail holds id -1 and score -INFINITY.
@@ -218,9 +230,12 @@ GIFT_API gift_status gift_rerank(gift_index* index, const int32_t* cand_ids, con
  *    process exits. A batch needs about 20 * B * N + 8 * B * (topk + 1) bytes
  *    (N = database shapes; 256-byte alignment per part); a larger batch returns
  *    GIFT_EINVAL with the size it needs -- split it.
+ *  - Call it with the index's device current (GIFT_EINVAL otherwise); an index
+ *    whose streamed build is still open returns GIFT_ESTATE.
  *  - The first call on a device looks up the buffer's device address with that
  *    device current (the runtime loads the library's module there); make that
- *    first call before any stream capture.
+ *    first call before any stream capture. Later calls check the remembered
+ *    address and look it up again after a device reset.
  *  - Every call uses the same buffer and clears what must start at zero; calls
  *    whose work overlaps on the GPU (several streams or host threads at once)
  *    race on it, so the caller must serialise them.
@@ -231,6 +246,39 @@ GIFT_API gift_status gift_rerank_noalloc(gift_index* index, const int32_t* cand_
                                          const float* cand_scores, int32_t B, int32_t n_cand,
                                          int32_t k1, int32_t topk, int32_t* out_ids,
                                          float* out_sprime, cudaStream_t stream);
+
+/*
+ * Second inverted file of a database sharded over several indices (one per
+ * GPU, each holding a contiguous range of the N shapes; Sec. 2.4, Fig. 3):
+ * install on `index` the S-IF of all n_shapes_total shapes from their ranked
+ * neighbour rows, so that gift_rerank on this index re-ranks over the whole
+ * database (the S-IF is replicated on every shard; no exchange is needed).
+ *  - nbr_ids / nbr_scores: device or host [n_shapes_total * k1]; row p is
+ *    N_k1(x_p) over the whole database (global ids, itself included, ranked by
+ *    (score desc, id asc)) with the scores S(x_p, x_i) that become F_p (Eq. 7),
+ *    e.g. the merged sharded query (gift_merge_topk) of every database shape.
+ *  - The index must have been built with sif_k1 == 0 (GIFT_ESTATE otherwise);
+ *    afterwards gift_rerank and gift_export_sif use global ids in
+ *    [0, n_shapes_total). Synchronises `stream`.
+ * Errors: EINVAL (sizes, an id outside [0, n_shapes_total)), ESTATE, ENOMEM,
+ * ECUDA.
+ */
+GIFT_API gift_status gift_sif_from_neighbours(gift_index* index, const int32_t* nbr_ids, const float* nbr_scores,
+                                              int32_t n_shapes_total, int32_t k1, cudaStream_t stream);
+
+/*
+ * Merge of ranked lists (the exchange step of a database-sharded query, where
+ * every shard returns its own top-R): each row of (id, score) pairs, ids
+ * distinct within a row and id < 0 marking an empty entry, is reduced to its
+ * k best pairs by (score desc, id asc) -- the ranking order of gift_query.
+ * Eq. 4 scores of a shape depend on that shape's views only, so merging the
+ * shards' top lists gives the ranking of an unsharded index.
+ *  - ids, scores: device or host [B * n]; out_ids, out_scores: device or host
+ *    [B * k]; rows with fewer than k entries end in id -1, score -INFINITY.
+ * Errors: EINVAL (B, n, k outside range: 1 <= k <= 1024), ENOMEM, ECUDA.
+ */
+GIFT_API gift_status gift_merge_topk(const int32_t* ids, const float* scores, int32_t B, int64_t n, int32_t k,
+                                     int32_t* out_ids, float* out_scores, cudaStream_t stream);
 
 /*
  * Re-ranking with two similarity measures (Sec. 2.4: Eqs. 9, 10, 11; the
@@ -425,6 +473,12 @@ typedef struct {
   float mean_batch;     /* queries per batch                                             */
   float p50_ms, p99_ms, max_ms;  /* latency, submission to completion                     */
   float queries_per_s;  /* completed / (last completion - first submission)              */
+  int64_t admission_waits;      /* dispatcher passes that held a batch back because the
+                                   batches in flight left too little of the budget      */
+  int64_t peak_in_flight_bytes; /* most admitted bytes of batches in flight at once     */
+  int64_t budget_bytes;         /* budget for batches in flight (after slot buffers)    */
+  int64_t max_batch_bytes;      /* admission estimate of a batch of the maximum size    */
+  int64_t slot_bytes;           /* device and pinned buffers of all slots               */
 } gift_server_stats_t;
 
 typedef struct gift_server gift_server;

@@ -61,7 +61,8 @@ class _Timing(ctypes.Structure):
         "total_ms")] + [("scan_bytes", ctypes.c_int64), ("rescore_bytes", ctypes.c_int64),
                         ("scan_pairs", ctypes.c_int64), ("assign_kernel_ms", ctypes.c_float),
                         ("scan_kernel_ms", ctypes.c_float), ("rescore_kernel_ms", ctypes.c_float),
-                        ("assign_rows", ctypes.c_int64)]
+                        ("assign_rows", ctypes.c_int64)] + [(n, ctypes.c_int64) for n in (
+                            "rescore_items", "rescore_items_kept", "cand_pairs", "cand_rows", "rescore_rows_read")]
 
 
 class _ServerParams(ctypes.Structure):
@@ -72,7 +73,9 @@ class _ServerParams(ctypes.Structure):
 
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("completed", "failed", "batches", "queued")] + [
-        (n, ctypes.c_float) for n in ("mean_batch", "p50_ms", "p99_ms", "max_ms", "queries_per_s")]
+        (n, ctypes.c_float) for n in ("mean_batch", "p50_ms", "p99_ms", "max_ms", "queries_per_s")] + [
+        (n, ctypes.c_int64) for n in ("admission_waits", "peak_in_flight_bytes", "budget_bytes", "max_batch_bytes",
+                                      "slot_bytes")]
 
 
 _P = ctypes.c_void_p
@@ -87,6 +90,8 @@ _SIGS = {
     "gift_query": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "gift_rerank_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P]),
+    "gift_sif_from_neighbours": (_I32, [_P, _P, _P, _I32, _I32, _P]),
+    "gift_merge_topk": (_I32, [_P, _P, _I32, _I64, _I32, _P, _P, _P]),
     "gift_assign": (_I32, [_P, _P, _I64, _I32, _P, _P]),
     "gift_render_views": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _I32, _P, _P]),
     "gift_kmeans": (_I32, [_P, _I64, _I32, _I32, _P, _I32, _P, _P]),
@@ -291,6 +296,13 @@ class Index:
         _check(load().gift_index_info(self._h, ctypes.byref(i)))
         return {n: getattr(i, n) for n, _ in _Info._fields_}
 
+    def set_sif(self, nbr_ids, nbr_scores, n_shapes_total: int, k1: int, stream=None):
+        """Install the S-IF of a whole (sharded) database from its ranked neighbour rows
+        [n_shapes_total, k1] (global ids and scores; gift_sif_from_neighbours)."""
+        _check(load().gift_sif_from_neighbours(self._h, _ptr(nbr_ids), _ptr(nbr_scores), int(n_shapes_total),
+                                               int(k1), _stream(stream)))
+        self.sif_k1 = int(k1)
+
     def set_rescore_depth(self, r: int):
         """FP32 rescore depth of later queries (0 = scores of the list store alone)."""
         _check(load().gift_set_rescore_depth(self._h, int(r)))
@@ -314,6 +326,19 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+def merge_topk(ids, scores, k: int, out=None, stream=None):
+    """The k best (id, score) pairs of each row by (score desc, id asc) (gift_merge_topk);
+    ids int32 and scores float32 [B, n], id < 0 = empty. Returns (ids int32, scores float32) [B, k]."""
+    import torch
+    B, n = ids.shape
+    if out is None:
+        dev = ids.device if hasattr(ids, "is_cuda") and ids.is_cuda else torch.device("cuda")
+        out = (torch.empty((B, k), dtype=torch.int32, device=dev), torch.empty((B, k), dtype=torch.float32, device=dev))
+    _check(load().gift_merge_topk(_ptr(ids), _ptr(scores), int(B), int(n), int(k), _ptr(out[0]), _ptr(out[1]),
+                                  _stream(stream)))
+    return out
 
 
 # ---------------------------------------------------------------- differentiation

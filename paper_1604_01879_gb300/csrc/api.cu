@@ -163,6 +163,11 @@ __global__ void k_list_meta(const int32_t* __restrict__ list_row, const int32_t*
   run_flag[e] = start ? 1 : 0;
 }
 
+// Runs of a list: maximal groups of consecutive entries with one shape id. The
+// stable sort by codeword keeps the (row, assignment) item order inside a list,
+// rows are shape * N_v + view and a view enters a list at most once, so list
+// entries are in ascending (shape, view) order and the run shapes of a list
+// are strictly ascending (the candidate merge of the combine relies on it).
 __global__ void k_runs(const int64_t* __restrict__ run_id_excl, const int64_t* __restrict__ run_flag,
                        const int32_t* __restrict__ skeys, const int64_t* __restrict__ list_off,
                        const int32_t* __restrict__ list_shape, int64_t n, int32_t* __restrict__ entry_run,
@@ -429,6 +434,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   sort_ids_rows(cand, B, Rr, cand_sorted, s);
 
   tm.mark(ST_RESCORE);
+  if (fused) fif_rescore_stats(ix, P, cand_sorted, Rr, sc, s);  // timed calls only
   if (!fused) {
     GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
     if (ix.list_lo)
@@ -676,6 +682,7 @@ void build(const gift_index_params* prm, const float* db_feats, const float* cod
   // S-IF: every database shape as a query, first k1 neighbours (self included)
   if (p.sif_k1 > 0) {
     ix->k1 = p.sif_k1;
+    ix->sif_n = N;
     ix->sif_off = ix->alloc<int64_t>(N + 1);
     ix->sif_ids = ix->alloc<int32_t>((size_t)N * p.sif_k1);
     ix->sif_mem = ix->alloc<uint32_t>((size_t)N * p.sif_k1);
@@ -866,6 +873,7 @@ void stream_end(Index& ix, int pass, cudaStream_t s) {
     // the S-IF arrays appear only now, so no call sees a half-built S-IF
     const int64_t n = (int64_t)ix.prm.n_shapes * ix.prm.sif_k1;
     ix.k1 = ix.prm.sif_k1;
+    ix.sif_n = ix.prm.n_shapes;
     ix.sif_off = ix.alloc<int64_t>(ix.prm.n_shapes + 1);
     ix.sif_ids = ix.alloc<int32_t>(n);
     ix.sif_mem = ix.alloc<uint32_t>(n);
@@ -941,8 +949,8 @@ gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q
     std::vector<gift::OutBuf> outs;
     unsigned long long* stats = nullptr;
     if (tm.on) {
-      stats = sc.get<unsigned long long>(3);
-      GIFT_CUDA(cudaMemsetAsync(stats, 0, 24, stream));
+      stats = sc.get<unsigned long long>(8);
+      GIFT_CUDA(cudaMemsetAsync(stats, 0, 64, stream));
     }
     tm.mark(gift::ST_ASSIGN);
     const float* q = gift::stage_in(q_feats, (size_t)nv * D, sc, stream);
@@ -972,8 +980,8 @@ gift_status gift_query(gift_index* index, const float* q_feats, const int32_t* q
     }
     gift::flush_out(outs, stream);
     if (tm.on) {
-      if (!ix.stats_pinned) GIFT_CUDA(cudaMallocHost(&ix.stats_pinned, 4 * sizeof(unsigned long long)));
-      GIFT_CUDA(cudaMemcpyAsync(ix.stats_pinned, stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+      if (!ix.stats_pinned) GIFT_CUDA(cudaMallocHost(&ix.stats_pinned, 8 * sizeof(unsigned long long)));
+      GIFT_CUDA(cudaMemcpyAsync(ix.stats_pinned, stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 stream));
       ix.stats_valid = true;
       tm.finish();
@@ -1053,6 +1061,8 @@ gift_status gift_aca_build(const gift_index* measure1, const gift_index* measure
     if (!a.ready() || !b.ready()) gift::fail(GIFT_ESTATE, "the streamed build of an index is not complete");
     if (!a.sif_off || !b.sif_off || !a.row_ids || !b.row_ids)
       gift::fail(GIFT_EUNSUPPORTED, "both indices need an S-IF (sif_k1 > 0)");
+    if (a.sif_n != a.prm.n_shapes || b.sif_n != b.prm.n_shapes)
+      gift::fail(GIFT_EUNSUPPORTED, "two measures need indices whose S-IF covers their own shapes");
     GIFT_REQUIRE(a.prm.n_shapes == b.prm.n_shapes, "the two indices must hold the same number of shapes");
     GIFT_REQUIRE(a.k1 == b.k1, "the two indices must have the same k1");
     GIFT_REQUIRE(mode >= GIFT_ACA_NONE && mode <= GIFT_ACA_CO_AUGMENT, "unknown mode");
@@ -1156,13 +1166,69 @@ gift_status gift_export_fif(const gift_index* index, int32_t* db_codes, int64_t*
   });
 }
 
+gift_status gift_sif_from_neighbours(gift_index* index, const int32_t* nbr_ids, const float* nbr_scores,
+                                     int32_t n_shapes_total, int32_t k1, cudaStream_t stream) {
+  return gift::guard("gift_sif_from_neighbours", [&] {
+    GIFT_REQUIRE(index && nbr_ids && nbr_scores, "NULL argument");
+    Index& ix = *reinterpret_cast<Index*>(index);
+    if (!ix.ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
+    if (ix.sif_off) gift::fail(GIFT_ESTATE, "the index already has an S-IF");
+    GIFT_REQUIRE(n_shapes_total >= 1, "n_shapes_total must be positive");
+    GIFT_REQUIRE(k1 >= 1 && k1 <= std::min(1024, n_shapes_total), "k1 must be in [1, min(1024, n_shapes_total)]");
+    int dev = 0;
+    GIFT_CUDA(cudaGetDevice(&dev));
+    GIFT_REQUIRE(dev == ix.device, "call with the index's device current");
+    gift::Scratch sc(stream);
+    const int64_t n = (int64_t)n_shapes_total * k1;
+    const int32_t* ids = gift::stage_in(nbr_ids, (size_t)n, sc, stream);
+    const float* scs = gift::stage_in(nbr_scores, (size_t)n, sc, stream);
+    ix.row_ids = ix.alloc<int32_t>(n);
+    ix.row_sc = ix.alloc<float>(n);
+    GIFT_CUDA(cudaMemcpyAsync(ix.row_ids, ids, n * 4, cudaMemcpyDeviceToDevice, stream));
+    GIFT_CUDA(cudaMemcpyAsync(ix.row_sc, scs, n * 4, cudaMemcpyDeviceToDevice, stream));
+    int64_t* off = ix.alloc<int64_t>((size_t)n_shapes_total + 1);
+    int32_t* sids = ix.alloc<int32_t>(n);
+    uint32_t* mem = ix.alloc<uint32_t>(n);
+    uint64_t* card = ix.alloc<uint64_t>(n_shapes_total);
+    ix.k1 = k1;
+    ix.sif_n = n_shapes_total;
+    ix.sif_ids = sids;
+    ix.sif_mem = mem;
+    ix.sif_card = card;
+    ix.sif_off = off;
+    try {
+      gift::sif_build(ix, ix.row_ids, ix.row_sc, sc, stream);
+    } catch (...) {
+      ix.sif_off = nullptr;  // no half-built S-IF is visible to later calls
+      throw;
+    }
+  });
+}
+
+gift_status gift_merge_topk(const int32_t* ids, const float* scores, int32_t B, int64_t n, int32_t k,
+                            int32_t* out_ids, float* out_scores, cudaStream_t stream) {
+  return gift::guard("gift_merge_topk", [&] {
+    GIFT_REQUIRE(ids && scores && out_ids && out_scores, "NULL argument");
+    GIFT_REQUIRE(B > 0 && n > 0 && n < (int64_t)INT32_MAX, "need B > 0 and 0 < n < 2^31");
+    GIFT_REQUIRE(k > 0 && k <= 1024, "k must be in [1, 1024]");
+    gift::Scratch sc(stream);
+    std::vector<gift::OutBuf> outs;
+    const int32_t* ci = gift::stage_in(ids, (size_t)B * n, sc, stream);
+    const float* cs = gift::stage_in(scores, (size_t)B * n, sc, stream);
+    int32_t* oid = gift::stage_out(out_ids, (size_t)B * k, sc, outs);
+    float* osc = gift::stage_out(out_scores, (size_t)B * k, sc, outs);
+    gift::merge_topk_rows(ci, cs, B, n, k, oid, osc, sc, stream);
+    gift::flush_out(outs, stream);
+  });
+}
+
 gift_status gift_export_sif(const gift_index* index, int64_t* entry_offsets, int32_t* entry_ids,
                             uint32_t* entry_members, uint64_t* card, cudaStream_t stream) {
   return gift::guard("gift_export_sif", [&] {
     GIFT_REQUIRE(index, "NULL index");
     const Index& ix = *reinterpret_cast<const Index*>(index);
     if (!ix.sif_off) gift::fail(GIFT_EUNSUPPORTED, "index built without an S-IF");
-    const int64_t N = ix.prm.n_shapes, n = N * ix.k1;
+    const int64_t N = ix.sif_n, n = N * ix.k1;
     if (entry_offsets)
       GIFT_CUDA(cudaMemcpyAsync(entry_offsets, ix.sif_off, (N + 1) * 8, cudaMemcpyDefault, stream));
     if (entry_ids) GIFT_CUDA(cudaMemcpyAsync(entry_ids, ix.sif_ids, n * 4, cudaMemcpyDefault, stream));
@@ -1234,6 +1300,11 @@ gift_status gift_get_timing(gift_index* index, gift_timing_t* out) {
       t.scan_bytes = (int64_t)ix.stats_pinned[0];
       t.scan_pairs = (int64_t)ix.stats_pinned[1];
       t.rescore_bytes = ix.prm.rescore_r > 0 ? (int64_t)ix.stats_pinned[2] : 0;
+      t.rescore_items = (int64_t)ix.stats_pinned[3];
+      t.rescore_items_kept = (int64_t)ix.stats_pinned[4];
+      t.cand_pairs = (int64_t)ix.stats_pinned[5];
+      t.cand_rows = (int64_t)ix.stats_pinned[6];
+      t.rescore_rows_read = (int64_t)ix.stats_pinned[7];
     }
     *out = t;
   });

@@ -14,7 +14,9 @@ struct FifPlan {
   const int32_t* q_code = nullptr;// [nv * ma]
   const int32_t* qoff = nullptr;  // [B+1] device
   const int32_t* vquery = nullptr;// [nv] query of each view
-  unsigned long long* stats = nullptr;  // optional [3]: scanned bytes, pairs, rescore bytes
+  unsigned long long* stats = nullptr;  // optional [8]: scanned bytes, pairs, rescore bytes, then the
+                                        // rescore's items, kept items, candidate pairs, candidate rows,
+                                        // rows of kept items
   KernelClock* kc = nullptr;            // optional kernel timing
   // derived
   int64_t nslots = 0;
@@ -40,6 +42,10 @@ void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
 // fills `table` with BF16 maxima and `table32` with FP32-level maxima of every run)
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
                  int R, Scratch& sc, cudaStream_t s, uint32_t* table32 = nullptr);
+// counts of the candidate work of a batch (stats [3..7]) without running the
+// rescore: for the fused pass, whose FP32-level products cover every touched pair
+void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_sorted, int R, Scratch& sc,
+                       cudaStream_t s);
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
                  const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s);
 

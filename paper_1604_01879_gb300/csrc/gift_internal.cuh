@@ -122,6 +122,8 @@ struct Index {
 
   // S-IF
   int32_t k1 = 0;
+  int32_t sif_n = 0;             // shapes the S-IF covers: n_shapes, or the whole database of which
+                                 // this index holds a shard (gift_sif_from_neighbours)
   int64_t* sif_off = nullptr;    // [N+1]
   int32_t* sif_ids = nullptr;    // [N*k1]
   uint32_t* sif_mem = nullptr;   // [N*k1]
@@ -212,6 +214,10 @@ void sort_candidates(const int32_t* ids, const float* scores, int32_t B, int32_t
                      int32_t* ids_out, float* scores_out, cudaStream_t s);
 // Rows of ids of length r: ascending copy.
 void sort_ids_rows(const int32_t* ids, int32_t B, int32_t r, int32_t* out, cudaStream_t s);
+// Rows of (id, score) pairs of any length n (ids distinct per row, id < 0 =
+// none): the k best by (score desc, id asc); missing entries id -1, -INF.
+void merge_topk_rows(const int32_t* ids, const float* scores, int32_t B, int64_t n, int32_t k, int32_t* ids_out,
+                     float* scores_out, Scratch& sc, cudaStream_t s);
 
 // k_sif.cu
 void sif_build(Index& ix, const int32_t* nbr_ids, const float* nbr_scores, Scratch& sc,
@@ -270,5 +276,38 @@ __device__ __forceinline__ float key2f(uint32_t k) {
   uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
   return __uint_as_float(u);
 }
+
+// Two-float (compensated) FP32 accumulation, in place of FP64 on the GPU:
+// value = hi + lo. two_sum gives s + e == a + b exactly (Knuth's TwoSum, six
+// FP32 additions, no products, so no contraction into FMA can change it);
+// the rounding errors of the running sum collect in lo, whose own rounding
+// is ~2^-24 |lo|, so n terms sum with ~n 2^-48 relative error before the
+// final rounding of hi + lo.
+struct F2 {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ void f2_add(F2& x, float v) {
+  float s, e;
+  two_sum(x.hi, v, s, e);
+  x.hi = s;
+  x.lo += e;
+}
+__device__ __forceinline__ F2 f2_merge(F2 a, const F2& b) {
+  f2_add(a, b.hi);
+  a.lo += b.lo;
+  return a;
+}
+__device__ __forceinline__ F2 f2_shfl_xor(const F2& x, int o) {
+  F2 y;
+  y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+  y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+  return y;
+}
+__device__ __forceinline__ float f2_value(const F2& x) { return x.hi + x.lo; }
 
 }  // namespace gift

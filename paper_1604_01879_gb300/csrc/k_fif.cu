@@ -6,13 +6,17 @@
 //            contiguous (M_k of them).
 //  scan    : for every list k touched by the batch, the L_k list entries are
 //            multiplied with the M_k slots of bucket k (a grouped contraction);
-//            cosines are floored at 0, reduced by max over each run of equal
-//            shape id inside the list, and folded into a per-(slot, run)
-//            table with atomicMax on the float bits (values >= 0).
+//            cosines are reduced by max over each run of equal shape id inside
+//            the list and folded into a per-(slot, run) table with atomicMax
+//            on an order-preserving key of the float (f2key; 0 = no value).
 //  combine : per query, per view, the max over its query_ma slots of each
-//            shape's run value (the lists of one view are disjoint), summed
-//            over the views in uint64 fixed point (exact, order-free) and
-//            divided by |V(x_q)| -> S(x_q, .) (Eq. 4, normaliser of Eq. 3).
+//            shape's run value, summed over the views in signed 64-bit fixed
+//            point (exact, order-free) and divided by |V(x_q)| -> S(x_q, .)
+//            (Eq. 4, normaliser of Eq. 3). Eq. 4's max runs over every view
+//            of the shape, so 0 joins it whenever some view of the shape
+//            shares no codeword with the query view: a negative maximum
+//            counts only when every view of the shape is matched (checked
+//            from the database codes; never needed for non-negative features).
 //  rescore : the same scan over the FP32 feature master for the top-R
 //            candidate shapes only, combined into FP32 candidate scores.
 #include <algorithm>
@@ -252,7 +256,7 @@ __global__ __launch_bounds__(256) void k_fif_scan(const ScanArgs a) {
     for (int j = 0; j < 4; ++j) {
       const int el = tx * 4 + j;
       float v = 0.f;
-      if (sl < ns && el < ne) v = fmaxf(acc[i][j] * s_inv[sl] * e_scale[el], 0.f);
+      if (sl < ns && el < ne) v = acc[i][j] * s_inv[sl] * e_scale[el];
       Ts[sl][el] = v;
     }
   }
@@ -264,17 +268,19 @@ __global__ __launch_bounds__(256) void k_fif_scan(const ScanArgs a) {
     if (el > 0 && e_run[el - 1] == run) continue;  // not the first entry of its run here
     float m = Ts[sl][el];
     for (int e2 = el + 1; e2 < ne && e_run[e2] == run; ++e2) m = fmaxf(m, Ts[sl][e2]);
-    if (!(m > 0.f)) continue;
     if (RESCORE) {
       if (find_sorted(a.cand + (int64_t)s_q[sl] * a.R, a.R, e_shape[el]) < 0) continue;
     }
-    atomicMax(a.table + s_rb[sl] + run, __float_as_uint(m));
+    atomicMax(a.table + s_rb[sl] + run, f2key(m));
   }
 }
 
 struct CombineArgs {
   const int32_t* qoff;       // [B+1] device
   int ma;
+  const int32_t* q_code;     // [nv*ma] codewords of each query view
+  const int32_t* db_codes;   // [N*Nv*db_ma] codewords of each database view
+  int db_ma, Nv;
   const int32_t* view_slot;  // [nv*ma]
   const int32_t* skeys;      // [nslots] codeword of each slot
   const int64_t* runbase;    // [nslots]
@@ -289,8 +295,36 @@ struct CombineArgs {
   float* cand_score;         // [B, R] (CAND)
 };
 
-__device__ __forceinline__ unsigned long long fix32(uint32_t bits) {
-  return __float2ull_rn(__uint_as_float(bits) * 4294967296.0f);
+// a shape's term in signed 2^-32 fixed point; two's complement sums in uint64
+// are exact and order-free for |sum| < 2^31
+__device__ __forceinline__ unsigned long long fix32(float f) {
+  return (unsigned long long)__float2ll_rn(f * 4294967296.0f);
+}
+__device__ __forceinline__ float unfix32(unsigned long long acc, float Vq) {
+  return __fdiv_rn(__ll2float_rn((long long)acc) * 2.3283064365386963e-10f, Vq);
+}
+
+// Eq. 4's delta is 1 for every view of shape p: each of p's views shares a
+// codeword with query view v (the max then has no 0 candidate)
+__device__ __noinline__ bool all_views_matched(const CombineArgs& a, int64_t v, int32_t p) {
+  const int32_t* qc = a.q_code + v * a.ma;
+  const int32_t* dc = a.db_codes + (int64_t)p * a.Nv * a.db_ma;
+  for (int j = 0; j < a.Nv; ++j) {
+    bool hit = false;
+    for (int t = 0; t < a.db_ma; ++t)
+      for (int u = 0; u < a.ma; ++u) hit |= dc[j * a.db_ma + t] == qc[u];
+    if (!hit) return false;
+  }
+  return true;
+}
+
+// term of (view v, shape p) from its table key (0 = shape not reached): the
+// run maximum, or nothing (Eq. 4's 0) when it is negative and a view of p is
+// outside v's lists
+__device__ __forceinline__ bool view_term(const CombineArgs& a, int64_t v, int32_t p, uint32_t key, float& t) {
+  if (key == 0u) return false;
+  t = key2f(key);
+  return !(t < 0.f) || all_views_matched(a, v, p);
 }
 
 template <bool CAND>
@@ -319,7 +353,7 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
       }
       for (int r = lo + lane; r < hi; r += 32) {
         const int32_t p = rs[r];
-        float m = __uint_as_float(a.table[rb + r]);
+        uint32_t m = a.table[rb + r];
         bool skip = false;
         for (int s_b = 0; s_b < a.ma && !skip; ++s_b) {
           if (s_b == s_a) continue;
@@ -328,9 +362,10 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
           const int r2 = find_sorted(a.run_shape + a.run_off[k2], a.nruns[k2], p);
           if (r2 < 0) continue;
           if (s_b < s_a) skip = true;  // the lower assignment owns this shape
-          else m = fmaxf(m, __uint_as_float(a.table[a.runbase[s2] + r2]));
+          else m = max(m, a.table[a.runbase[s2] + r2]);
         }
-        if (skip || !(m > 0.f)) continue;
+        float t;
+        if (skip || !view_term(a, v, p, m, t)) continue;
         int idx;
         if (CAND) {
           idx = find_sorted(cand, a.R, p);
@@ -338,14 +373,14 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
         } else {
           idx = p - c0;
         }
-        atomicAdd(&acc[idx], fix32(__float_as_uint(m)));
+        atomicAdd(&acc[idx], fix32(t));
       }
     }
   }
   __syncthreads();
   const float Vq = (float)(v1 - v0);
   for (int i = threadIdx.x; i < width; i += kCombineT) {
-    const float val = __fdiv_rn(__ull2float_rn(acc[i]) * 2.3283064365386963e-10f, Vq);
+    const float val = unfix32(acc[i], Vq);
     if (CAND) a.cand_score[(int64_t)q * a.R + i] = val;
     else a.S[(int64_t)q * a.N + c0 + i] = val;
   }
@@ -353,7 +388,7 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
 
 // Candidate scores with multiple assignment (ma > 1): each warp takes one view
 // at a time; the runs of the view's ma lists fold their maxima into the warp's
-// shared array over the query's candidates (atomicMax on the float bits), so a
+// shared array over the query's candidates (atomicMax on the keys), so a
 // shape reached through several lists counts once with the largest maximum;
 // the array is then added into the block's fixed-point sums and cleared. Each
 // list's runs are merged against a shared copy of the query's sorted candidates
@@ -394,13 +429,15 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
       const int seg = (nt + 31) >> 5;
       const int r0 = min(nt, lane * seg), r1 = min(nt, r0 + seg);
       if (r0 < r1) {
+        // run shapes are strictly ascending within a list (entries are in
+        // (shape, view) order and a run is a maximal group of one shape)
         int c = lower_bound_i32(cs, R, a.run_shape[o + r0]);
         for (int r = r0; r < r1 && c < R; ++r) {
           const int32_t p = a.run_shape[o + r];
           while (c < R && cs[c] < p) ++c;
           if (c < R && cs[c] == p) {
             const uint32_t m = a.table[b + r];
-            if (m != 0u) atomicMax(&vmax[c], m);  // non-negative float bits: 0 <=> no positive maximum
+            if (m != 0u) atomicMax(&vmax[c], m);  // key 0: run not written
           }
         }
       }
@@ -409,7 +446,8 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
     for (int i = lane; i < R; i += 32) {
       const uint32_t m = vmax[i];
       if (m != 0u) {
-        atomicAdd(&acc[i], fix32(m));
+        float t;
+        if (view_term(a, v, cs[i], m, t)) atomicAdd(&acc[i], fix32(t));
         vmax[i] = 0u;
       }
     }
@@ -417,8 +455,7 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
   }
   __syncthreads();
   const float Vq = (float)(v1 - v0);
-  for (int i = threadIdx.x; i < R; i += kCombineT)
-    a.cand_score[(int64_t)q * R + i] = __fdiv_rn(__ull2float_rn(acc[i]) * 2.3283064365386963e-10f, Vq);
+  for (int i = threadIdx.x; i < R; i += kCombineT) a.cand_score[(int64_t)q * R + i] = unfix32(acc[i], Vq);
 }
 
 }  // namespace
@@ -495,6 +532,10 @@ void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float
   CombineArgs a;
   a.qoff = P.qoff;
   a.ma = P.ma;
+  a.q_code = P.q_code;
+  a.db_codes = ix.db_codes;
+  a.db_ma = ix.db_ma;
+  a.Nv = ix.prm.views_per_shape;
   a.view_slot = P.view_slot;
   a.skeys = P.skeys;
   a.runbase = P.runbase;

@@ -4,8 +4,9 @@
 // Iteration: every row goes to its nearest centre through the exact
 // quantiser (tensor-core coarse scores + two-float refine, ties to the lowest
 // index); rows are grouped by centre with a stable sort, and each centre
-// becomes the mean of its rows, summed in float64 in ascending row order (so
-// the result does not depend on scheduling). A centre left without rows takes
+// becomes the mean of its rows, summed in two-float (compensated FP32)
+// arithmetic in ascending row order (so the result does not depend on
+// scheduling; no FP64 on the GPU). A centre left without rows takes
 // the row farthest from the centre it was assigned to (distance desc, index
 // asc), the empty centres served in ascending order.
 #include "gift_internal.cuh"
@@ -14,7 +15,7 @@ namespace gift {
 
 namespace {
 
-// one block per centre: mean of its rows (perm[off[c] .. off[c+1]) ascending), float64 sums
+// one block per centre: mean of its rows (perm[off[c] .. off[c+1]) ascending), two-float sums
 __global__ void k_km_mean(const float* __restrict__ X, int D, const int32_t* __restrict__ perm,
                           const int64_t* __restrict__ off, const float* __restrict__ C_old,
                           float* __restrict__ C_new) {
@@ -25,13 +26,19 @@ __global__ void k_km_mean(const float* __restrict__ X, int D, const int32_t* __r
       C_new[(int64_t)c * D + d] = C_old[(int64_t)c * D + d];
       continue;
     }
-    double s = 0.0;
-    for (int64_t e = r0; e < r1; ++e) s += (double)X[(int64_t)perm[e] * D + d];
-    C_new[(int64_t)c * D + d] = (float)(s / (double)(r1 - r0));
+    F2 s;
+    for (int64_t e = r0; e < r1; ++e) f2_add(s, X[(int64_t)perm[e] * D + d]);
+    // (hi + lo) / n: the quotient of the two-float sum, rounded once more
+    const float n = (float)(r1 - r0);
+    const float q = __fdiv_rn(s.hi, n);
+    const float rem = __fmaf_rn(-q, n, s.hi);  // s.hi - q n exactly (n < 2^24)
+    C_new[(int64_t)c * D + d] = q + __fdiv_rn(rem + s.lo, n);
   }
 }
 
-// squared distance of every row to its assigned centre (warp per row, float64)
+// squared distance of every row to its assigned centre (warp per row, two-float):
+// t = x - c exactly as th + tl (TwoSum), t^2 = th^2 + 2 th tl + tl^2 with the
+// rounding error of th^2 recovered by an FMA
 __global__ void k_km_dist(const float* __restrict__ X, int64_t n, int D, const float* __restrict__ C,
                           const int32_t* __restrict__ lab, float* __restrict__ dist) {
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -39,14 +46,18 @@ __global__ void k_km_dist(const float* __restrict__ X, int64_t n, int D, const f
   if (r >= n) return;
   const float* x = X + r * D;
   const float* c = C + (int64_t)lab[r] * D;
-  double s = 0.0;
+  F2 s;
   for (int d = lane; d < D; d += 32) {
-    const double t = (double)x[d] - (double)c[d];
-    s += t * t;
+    float th, tl;
+    two_sum(x[d], -c[d], th, tl);
+    const float p = th * th;
+    const float pe = __fmaf_rn(th, th, -p);
+    f2_add(s, p);
+    s.lo += pe + tl * (2.f * th + tl);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) dist[r] = (float)s;
+  for (int o = 16; o > 0; o >>= 1) s = f2_merge(s, f2_shfl_xor(s, o));
+  if (lane == 0) dist[r] = f2_value(s);
 }
 
 __global__ void k_km_rows(const float* __restrict__ X, int D, const int32_t* __restrict__ rows,

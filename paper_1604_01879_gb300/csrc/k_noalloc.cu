@@ -12,7 +12,10 @@
 //
 // Host code cannot use the name of a __device__ variable as an address; the
 // first call on each device asks the runtime for the variable's device
-// address (with that device current) and remembers it.
+// address (with that device current) and remembers it. Later calls check that
+// the remembered address is still a device allocation of that device (after a
+// cudaDeviceReset the module, and with it the buffer, is loaded anew) and look
+// it up again when it is not.
 #include <mutex>
 
 #include "gift_internal.cuh"
@@ -28,12 +31,19 @@ static __device__ __align__(256) unsigned char g_rerank_scratch[kScratchBytes];
 std::mutex g_mu;
 std::vector<void*> g_addr;  // device address of g_rerank_scratch per device ordinal
 
-void* scratch_address() {
-  int dev = 0;
-  GIFT_CUDA(cudaGetDevice(&dev));
+bool still_valid(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+void* scratch_address(int dev) {
   std::lock_guard<std::mutex> lock(g_mu);
   if ((int)g_addr.size() <= dev) g_addr.resize(dev + 1, nullptr);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || !still_valid(g_addr[dev], dev)) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_rerank_scratch);
     if (e != cudaSuccess || !p) {
@@ -64,18 +74,22 @@ extern "C" gift_status gift_rerank_noalloc(gift_index* index, const int32_t* can
   return gift::guarded("gift_rerank_noalloc", [&] {
     GIFT_REQUIRE(index && cand_ids && cand_scores && out_ids && out_sprime, "NULL argument");
     const gift::Index& ix = *reinterpret_cast<const gift::Index*>(index);
+    if (!ix.ready()) gift::fail(GIFT_ESTATE, "the streamed build of this index is not complete");
     if (!ix.sif_off) gift::fail(GIFT_EUNSUPPORTED, "index built without an S-IF (sif_k1 == 0)");
+    int dev = 0;
+    GIFT_CUDA(cudaGetDevice(&dev));
+    GIFT_REQUIRE(dev == ix.device, "gift_rerank_noalloc must be called with the index's device current");
     GIFT_REQUIRE(B > 0 && n_cand > 0 && k1 > 0 && k1 <= n_cand, "need 0 < k1 <= n_cand and B > 0");
     GIFT_REQUIRE(topk > 0 && topk <= 1024, "topk must be in [1, 1024]");
     GIFT_REQUIRE(gift::on_device(cand_ids) && gift::on_device(cand_scores) && gift::on_device(out_ids) &&
                      gift::on_device(out_sprime),
                  "gift_rerank_noalloc takes device buffers only (host buffers would need staging memory)");
-    const size_t need = gift::sif_rerank_scratch_bytes(B, ix.prm.n_shapes, topk);
+    const size_t need = gift::sif_rerank_scratch_bytes(B, ix.sif_n, topk);
     if (need > gift::kScratchBytes)
       gift::fail(GIFT_EINVAL, "gift_rerank_noalloc needs " + std::to_string(need) +
                                   " bytes of scratch for this batch; its fixed buffer holds " +
                                   std::to_string(gift::kScratchBytes) + " bytes: split the batch");
-    void* scratch = gift::scratch_address();
+    void* scratch = gift::scratch_address(dev);
     gift::sif_rerank_into(ix, cand_ids, cand_scores, B, n_cand, k1, topk, out_ids, out_sprime, scratch,
                           gift::kScratchBytes, stream);
   });

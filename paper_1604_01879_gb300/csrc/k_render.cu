@@ -3,8 +3,8 @@
 // unit sphere, each looking at the origin.
 //
 // Normalisation: the area-weighted centroid of the surface goes to the origin
-// (float64 sums, one block per mesh) and the largest vertex distance from it
-// becomes 1. Views: orthographic along the camera's forward axis f, image axes
+// (two-float FP32 sums, one block per mesh) and the largest vertex distance
+// from it becomes 1. Views: orthographic along the camera's forward axis f, image axes
 // r = f x z / |f x z| and u = r x f, the image spanning [-1, 1]^2 (the unit
 // sphere's silhouette); depth = p . f + 1 in [0, 2], 2 where nothing is seen.
 // One thread per (triangle, view) projects the triangle, walks the pixel
@@ -31,44 +31,46 @@ __device__ __forceinline__ int find_mesh(const int64_t* __restrict__ off, int M,
   return lo;
 }
 
-// per mesh: (cx, cy, cz) = sum(area * centroid) / sum(area), float64
+// per mesh: (cx, cy, cz) = sum(area * centroid) / sum(area); per-triangle terms
+// in FP32, sums in two-float arithmetic (no FP64 on the GPU)
 __global__ __launch_bounds__(kRenderT) void k_mesh_centre(const float* __restrict__ V, const int32_t* __restrict__ T,
                                                           const int64_t* __restrict__ voff,
                                                           const int64_t* __restrict__ toff, float* __restrict__ centre) {
   const int m = blockIdx.x;
   const float* Vm = V + voff[m] * 3;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  F2 acc[4];
   for (int64_t t = toff[m] + threadIdx.x; t < toff[m + 1]; t += blockDim.x) {
     const int32_t* tr = T + t * 3;
-    double a[3], b[3], c[3];
+    float a[3], b[3], c[3];
     for (int d = 0; d < 3; ++d) {
       a[d] = Vm[(int64_t)tr[0] * 3 + d];
       b[d] = Vm[(int64_t)tr[1] * 3 + d];
       c[d] = Vm[(int64_t)tr[2] * 3 + d];
     }
-    const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-    const double cx = e1[1] * e2[2] - e1[2] * e2[1];
-    const double cy = e1[2] * e2[0] - e1[0] * e2[2];
-    const double cz = e1[0] * e2[1] - e1[1] * e2[0];
-    const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-    for (int d = 0; d < 3; ++d) acc[d] += area * (a[d] + b[d] + c[d]) / 3.0;
-    acc[3] += area;
+    const float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const float e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const float cx = e1[1] * e2[2] - e1[2] * e2[1];
+    const float cy = e1[2] * e2[0] - e1[0] * e2[2];
+    const float cz = e1[0] * e2[1] - e1[1] * e2[0];
+    const float area = 0.5f * sqrtf(cx * cx + cy * cy + cz * cz);
+    for (int d = 0; d < 3; ++d) f2_add(acc[d], area * ((a[d] + b[d] + c[d]) * (1.f / 3.f)));
+    f2_add(acc[3], area);
   }
-  __shared__ double red[4][kRenderT / 32];
+  __shared__ F2 red[4][kRenderT / 32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k < 4; ++k) {
-    double x = acc[k];
+    F2 x = acc[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) x = f2_merge(x, f2_shfl_xor(x, o));
     if (lane == 0) red[k][w] = x;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    F2 tot[4];
     for (int k = 0; k < 4; ++k)
-      for (int i = 0; i < kRenderT / 32; ++i) tot[k] += red[k][i];
-    for (int d = 0; d < 3; ++d) centre[m * 4 + d] = tot[3] > 0.0 ? (float)(tot[d] / tot[3]) : 0.f;
+      for (int i = 0; i < kRenderT / 32; ++i) tot[k] = f2_merge(tot[k], red[k][i]);
+    const float A = f2_value(tot[3]);
+    for (int d = 0; d < 3; ++d) centre[m * 4 + d] = A > 0.f ? __fdiv_rn(f2_value(tot[d]), A) : 0.f;
   }
 }
 

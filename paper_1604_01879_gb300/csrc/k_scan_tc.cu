@@ -5,15 +5,17 @@
 // consecutive query slots of bucket k). Rows of the MMA (TMEM lanes) are
 // query slots, columns are list entries; list entries of one shape are
 // consecutive, so each epilogue thread walks its row of columns in order,
-// keeps the max cosine of the current shape run (floored at 0) and folds
-// every run maximum into the per-(slot, run) table with atomicMax on the
-// float bits.
+// keeps the max cosine of the current shape run and folds every run maximum
+// into the per-(slot, run) table with atomicMax on its order-preserving key
+// (f2key, so negative cosines keep their order; 0 = not written).
 //
 // Scan: BF16 store, one product per k-block, 256 entries per tile.
 // Rescore: two-part BF16 operands (x = hi + lo) and three products, the
 // reduction split in four chunks accumulated in separate TMEM buffers and
 // summed in FP32 by the epilogue; only runs of the query's top-R candidate
-// shapes are kept.
+// shapes are kept, and only work items that hold such a run are run (a
+// pre-pass lists them): the FP32-level rescore needs the rows of its
+// candidates' runs, not every row of a touched list.
 #include "fif_plan.cuh"
 #include "gift_internal.cuh"
 #include "tc_engine.cuh"
@@ -28,7 +30,7 @@ constexpr int kRescChunks = 4;
 
 struct ListItem {
   int64_t e0, s0;
-  int ne, ns;
+  int ne, ns, k;
 };
 
 struct ListSched {
@@ -52,6 +54,7 @@ struct ListSched {
     const int64_t local = item - woff[k];
     const int64_t te = local / nts, ts = local % nts;
     ListItem it;
+    it.k = k;
     it.e0 = list_off[k] + te * TN;
     it.ne = (int)min((int64_t)TN, L - te * TN);
     it.s0 = boff[k] + ts * tc::kTM;
@@ -152,8 +155,7 @@ struct ScanPolicy : ListSched {
     x.cur_max = 0.f;
   }
   __device__ __forceinline__ void flush(const Ctx& x) const {
-    if (x.row.valid && x.cur_run >= 0 && x.cur_max > 0.f)
-      atomicMax(si.table + x.row.rb + x.cur_run, __float_as_uint(x.cur_max));
+    if (x.row.valid && x.cur_run >= 0) atomicMax(si.table + x.row.rb + x.cur_run, f2key(x.cur_max));
   }
   __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
     const int* e_run = reinterpret_cast<const int*>(ws);
@@ -167,7 +169,7 @@ struct ScanPolicy : ListSched {
       for (int j = 0; j < 32; ++j) {
         const int c = pc * 32 + j;
         const int run = e_run[c];
-        const float v = fmaxf(__uint_as_float(r[j]) * x.row.qi * e_scale[c], 0.f);
+        const float v = __uint_as_float(r[j]) * x.row.qi * e_scale[c];
         if (run != x.cur_run) {
           flush(x);
           x.cur_run = run;
@@ -186,15 +188,17 @@ struct RescorePolicy : ListSched {
   static constexpr int TN = kRescTN, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
   static constexpr int kWarpSmem = TN * 12;
   SlotInfo si;
-  const int32_t* cand;  // [B, R] candidate ids sorted ascending
+  const int32_t* cand;      // [B, R] candidate ids sorted ascending
   int R;
+  const int64_t* item_map;  // [n_items] the work items holding a candidate run (ascending)
+  const int64_t* n_items;
   using Item = ListItem;
   struct Ctx {
     RowCtx row;
     float sum[TN];
   };
-  __device__ __forceinline__ int64_t total() const { return total_items(); }
-  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
+  __device__ __forceinline__ int64_t total() const { return *n_items; }
+  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item_map[item]); }
   // never an empty chunk: each chunk must write its own accumulator
   // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
   // x 4 sub-steps per k-block); short reductions use one chunk
@@ -238,10 +242,10 @@ struct RescorePolicy : ListSched {
 #pragma unroll
     for (int c = 0; c < TN; ++c) {
       const int run = e_run[c];
-      const float v = fmaxf(x.sum[c] * x.row.qi * e_scale[c], 0.f);
+      const float v = x.sum[c] * x.row.qi * e_scale[c];
       if (run != cur_run) {
-        if (cur_run >= 0 && cur_max > 0.f && is_candidate(cq, R, cur_shape))
-          atomicMax(si.table + x.row.rb + cur_run, __float_as_uint(cur_max));
+        if (cur_run >= 0 && is_candidate(cq, R, cur_shape))
+          atomicMax(si.table + x.row.rb + cur_run, f2key(cur_max));
         cur_run = run;
         cur_max = v;
         cur_shape = e_shape[c];
@@ -249,8 +253,7 @@ struct RescorePolicy : ListSched {
         cur_max = fmaxf(cur_max, v);
       }
     }
-    if (cur_run >= 0 && cur_max > 0.f && is_candidate(cq, R, cur_shape))
-      atomicMax(si.table + x.row.rb + cur_run, __float_as_uint(cur_max));
+    if (cur_run >= 0 && is_candidate(cq, R, cur_shape)) atomicMax(si.table + x.row.rb + cur_run, f2key(cur_max));
     (void)it;
   }
 };
@@ -299,8 +302,8 @@ struct FusedPolicy : ListSched {
   }
   __device__ __forceinline__ void flush(const Ctx& x) const {
     if (!x.row.valid || x.cur_run < 0) return;
-    if (x.cur_bf > 0.f) atomicMax(si.table + x.row.rb + x.cur_run, __float_as_uint(x.cur_bf));
-    if (x.cur_fp > 0.f) atomicMax(table32 + x.row.rb + x.cur_run, __float_as_uint(x.cur_fp));
+    atomicMax(si.table + x.row.rb + x.cur_run, f2key(x.cur_bf));
+    atomicMax(table32 + x.row.rb + x.cur_run, f2key(x.cur_fp));
   }
   __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
     const int* e_run = reinterpret_cast<const int*>(ws);
@@ -320,8 +323,8 @@ struct FusedPolicy : ListSched {
         const int run = e_run[c];
         const float f = x.row.qi * e_scale[c];
         const float hh = __uint_as_float(h0[j]) + __uint_as_float(h1[j]);
-        const float u = fmaxf(hh * f, 0.f);
-        const float v = fmaxf((hh + __uint_as_float(cr[j])) * f, 0.f);
+        const float u = hh * f;
+        const float v = (hh + __uint_as_float(cr[j])) * f;
         if (run != x.cur_run) {
           flush(x);
           x.cur_run = run;
@@ -383,6 +386,77 @@ __global__ __launch_bounds__(256) void k_slot_fp8(const float* __restrict__ q, c
   if (threadIdx.x == 0) scale[s] = sc;
 }
 
+// Rescore work items that hold a candidate run: item (list k, entry tile,
+// slot tile) is kept when some slot of the tile has, among the tile's
+// entries, a run whose shape is one of its query's top-R candidates. One warp
+// per item tests every (slot, run start) pair; items past the real total (the
+// grid covers an upper bound) are not kept. With stats (timed calls only):
+//   [3] items, [4] kept items, [5] candidate (slot, entry) pairs, [6] candidate
+//   rows (entries whose shape is a candidate of some slot of their list, each
+//   list's entries counted once, by its first slot tile), [7] rows of kept items.
+__global__ __launch_bounds__(256) void k_resc_flags(const ListSched ls, const int32_t* __restrict__ slot_view,
+                                                    const int32_t* __restrict__ vquery,
+                                                    const int32_t* __restrict__ entry_run,
+                                                    const int32_t* __restrict__ list_shape,
+                                                    const int32_t* __restrict__ cand, int R, int64_t upper,
+                                                    int64_t* __restrict__ flags,
+                                                    unsigned long long* __restrict__ stats) {
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (item >= upper) return;
+  if (item >= ls.total_items()) {
+    if (lane == 0) flags[item] = 0;
+    return;
+  }
+  const ListItem it = ls.decode_list<kRescTN>(item);
+  bool hit = false;
+  for (int m = 0; m < it.ns && !hit; ++m) {
+    const int32_t* cq = cand + (int64_t)vquery[slot_view[it.s0 + m]] * R;
+    for (int c = lane; c < it.ne && !hit; c += 32) {
+      const int64_t e = it.e0 + c;
+      if ((c == 0 || entry_run[e] != entry_run[e - 1]) && is_candidate(cq, R, list_shape[e])) hit = true;
+    }
+    hit = __any_sync(0xffffffffu, hit);
+  }
+  if (lane == 0) flags[item] = hit ? 1 : 0;
+  if (!stats) return;
+  unsigned long long pairs = 0, rows = 0;
+  for (int m = 0; m < it.ns; ++m) {
+    const int32_t* cq = cand + (int64_t)vquery[slot_view[it.s0 + m]] * R;
+    for (int c = lane; c < it.ne; c += 32) pairs += is_candidate(cq, R, list_shape[it.e0 + c]) ? 1 : 0;
+  }
+  if (it.s0 == ls.boff[it.k]) {  // the list's first slot tile counts its candidate rows
+    const int64_t b0 = ls.boff[it.k], b1 = ls.boff[it.k + 1];
+    for (int c = lane; c < it.ne; c += 32) {
+      const int32_t shape = list_shape[it.e0 + c];
+      bool any = false;
+      for (int64_t s = b0; s < b1 && !any; ++s) any = is_candidate(cand + (int64_t)vquery[slot_view[s]] * R, R, shape);
+      rows += any ? 1 : 0;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    rows += __shfl_xor_sync(0xffffffffu, rows, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&stats[3], 1ull);
+    atomicAdd(&stats[4], hit ? 1ull : 0ull);
+    atomicAdd(&stats[5], pairs);
+    atomicAdd(&stats[6], rows);
+    atomicAdd(&stats[7], hit ? (unsigned long long)it.ne : 0ull);
+  }
+}
+
+// item_map[pos[i]] = i for every kept item i < upper; *n_items = the count
+__global__ void k_compact_items(const int64_t* __restrict__ flags, const int64_t* __restrict__ pos, int64_t upper,
+                                int64_t* __restrict__ item_map, int64_t* __restrict__ n_items) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= upper) return;
+  if (flags[i]) item_map[pos[i]] = i;
+  if (i == upper - 1) *n_items = pos[i] + flags[i];
+}
+
 __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t* __restrict__ list_off, int K,
                                 int tn, int64_t* __restrict__ wcnt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -396,7 +470,35 @@ __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t*
   wcnt[k] = (M > 0 && L > 0) ? cdiv(L, tn) * cdiv(M, tc::kTM) : 0;
 }
 
+// work items (list, entry tile of tn entries, slot tile) of the batch's touched lists
+ListSched list_sched(const Index& ix, const FifPlan& P, int tn, Scratch& sc, cudaStream_t s) {
+  const int K = ix.prm.n_codewords;
+  int64_t* wcnt = sc.get<int64_t>(K + 1);
+  int64_t* woff = sc.get<int64_t>(K + 1);
+  k_work_count_tc<<<(unsigned)cdiv(K + 1, 256), 256, 0, s>>>(P.boff, ix.list_off, K, tn, wcnt);
+  GIFT_LAUNCHED("k_work_count_tc");
+  scan_exclusive_i64(wcnt, woff, K + 1, sc, s);
+  ListSched ls;
+  ls.woff = woff;
+  ls.K = K;
+  ls.boff = P.boff;
+  ls.list_off = ix.list_off;
+  ls.nkb = 0;
+  return ls;
+}
+
 }  // namespace
+
+void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_sorted, int R, Scratch& sc,
+                       cudaStream_t s) {
+  if (!P.stats || P.nslots <= 0) return;
+  const ListSched ls = list_sched(ix, P, kRescTN, sc, s);
+  const int64_t upper = std::max<int64_t>(P.upper_items, 1);
+  int64_t* flags = sc.get<int64_t>(upper);
+  k_resc_flags<<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run, ix.list_shape,
+                                                        cand_sorted, R, upper, flags, P.stats);
+  GIFT_LAUNCHED("k_resc_flags");
+}
 
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
                  int R, Scratch& sc, cudaStream_t s, uint32_t* table32) {
@@ -432,17 +534,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     P.slot_lo = qlo;
   }
   const int tn = rescore ? kRescTN : kScanTN;
-  int64_t* wcnt = sc.get<int64_t>(K + 1);
-  int64_t* woff = sc.get<int64_t>(K + 1);
-  k_work_count_tc<<<(unsigned)cdiv(K + 1, 256), 256, 0, s>>>(P.boff, ix.list_off, K, tn, wcnt);
-  GIFT_LAUNCHED("k_work_count_tc");
-  scan_exclusive_i64(wcnt, woff, K + 1, sc, s);
-
-  ListSched ls;
-  ls.woff = woff;
-  ls.K = K;
-  ls.boff = P.boff;
-  ls.list_off = ix.list_off;
+  ListSched ls = list_sched(ix, P, tn, sc, s);
   ls.nkb = (int)cdiv(D, fp8 ? 128 : 64);
   SlotInfo si;
   si.runbase = P.runbase;
@@ -495,6 +587,20 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     pol.si.scale = ix.list_hi ? ix.list_scale_hi : ix.list_scale;
     pol.cand = cand_sorted;
     pol.R = R;
+    // the work items that hold a candidate run, in their original order
+    const int64_t upper = std::max<int64_t>(P.upper_items, 1);
+    int64_t* flags = sc.get<int64_t>(upper);
+    int64_t* pos = sc.get<int64_t>(upper);
+    int64_t* item_map = sc.get<int64_t>(upper);
+    int64_t* n_items = sc.get<int64_t>(1);
+    k_resc_flags<<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run, ix.list_shape,
+                                                          cand_sorted, R, upper, flags, P.stats);
+    GIFT_LAUNCHED("k_resc_flags");
+    scan_exclusive_i64(flags, pos, upper, sc, s);
+    k_compact_items<<<(unsigned)cdiv(upper, 256), 256, 0, s>>>(flags, pos, upper, item_map, n_items);
+    GIFT_LAUNCHED("k_compact_items");
+    pol.item_map = item_map;
+    pol.n_items = n_items;
     const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
     const CUtensorMap tB = make_tmap_bf16(bhi, ix.list_rows_alloc, D, RescorePolicy::TN);
     const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);

@@ -434,7 +434,7 @@ void aca_rerank(const Aca& a, const int32_t* cand1, const float* sc1, const int3
 }
 
 void sif_build(Index& ix, const int32_t* nbr_ids, const float* nbr_scores, Scratch& sc, cudaStream_t s) {
-  const int32_t N = ix.prm.n_shapes;
+  const int32_t N = ix.sif_n;
   const int k1 = ix.k1;
   const int64_t n = (int64_t)N * k1;
   int32_t* keys = sc.get<int32_t>(n);
@@ -465,7 +465,7 @@ void sif_build(Index& ix, const int32_t* nbr_ids, const float* nbr_scores, Scrat
 
 void sif_rerank(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B, int32_t n_cand,
                 int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, Scratch& sc, cudaStream_t s) {
-  const int32_t N = ix.prm.n_shapes;
+  const int32_t N = ix.sif_n;
   const int64_t BN = (int64_t)B * N;
   unsigned long long* num = sc.get<unsigned long long>(BN);
   GIFT_CUDA(cudaMemsetAsync(num, 0, BN * 8, s));
@@ -506,7 +506,7 @@ size_t sif_rerank_scratch_bytes(int32_t B, int32_t N, int32_t topk) {
 void sif_rerank_into(const Index& ix, const int32_t* cand_ids, const float* cand_scores, int32_t B, int32_t n_cand,
                      int32_t k1, int32_t topk, int32_t* out_ids, float* out_sprime, void* scratch,
                      size_t scratch_bytes, cudaStream_t s) {
-  const int32_t N = ix.prm.n_shapes;
+  const int32_t N = ix.sif_n;
   const int64_t BN = (int64_t)B * N;
   GIFT_REQUIRE(sif_rerank_scratch_bytes(B, N, topk) <= scratch_bytes, "re-rank scratch too small");
   uint8_t* p = static_cast<uint8_t*>(scratch);

@@ -217,7 +217,41 @@ __global__ __launch_bounds__(kT) void k_sort_candidates(const int32_t* __restric
   }
 }
 
+// key of an (id, score) pair: larger = better by (score desc, id asc); 0 = none
+__global__ void k_merge_keys(const int32_t* __restrict__ ids, const float* __restrict__ scores, int64_t n,
+                             unsigned long long* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t id = ids[i];
+  keys[i] = id < 0 ? 0ull
+                   : ((unsigned long long)f2key(scores[i]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)id);
+}
+
+__global__ void k_merge_decode(const unsigned long long* __restrict__ keys, int64_t n, int32_t* __restrict__ ids,
+                               float* __restrict__ scores) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long key = keys[i];
+  ids[i] = key == 0ull ? -1 : (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+  scores[i] = key == 0ull ? -INFINITY : key2f((uint32_t)(key >> 32));
+}
+
 }  // namespace
+
+void merge_topk_rows(const int32_t* ids, const float* scores, int32_t B, int64_t n, int32_t k, int32_t* ids_out,
+                     float* scores_out, Scratch& sc, cudaStream_t s) {
+  if (B <= 0 || k <= 0) return;
+  const int64_t total = (int64_t)B * n;
+  unsigned long long* keys = sc.get<unsigned long long>(total);
+  k_merge_keys<<<(unsigned)cdiv(total, 256), 256, 0, s>>>(ids, scores, total, keys);
+  GIFT_LAUNCHED("k_merge_keys");
+  int32_t* pos = sc.get<int32_t>((size_t)B * k);
+  uint64_t* kout = sc.get<uint64_t>((size_t)B * k);
+  topk_rows_u64(reinterpret_cast<const uint64_t*>(keys), B, n, k, pos, kout, sc, s);
+  k_merge_decode<<<(unsigned)cdiv((int64_t)B * k, 256), 256, 0, s>>>(reinterpret_cast<unsigned long long*>(kout),
+                                                                     (int64_t)B * k, ids_out, scores_out);
+  GIFT_LAUNCHED("k_merge_decode");
+}
 
 void topk_rows_f32(const float* scores, int32_t B, int64_t n, int32_t k, int32_t* ids_out, float* val_out,
                    Scratch&, cudaStream_t s) {

@@ -76,6 +76,9 @@ struct Server {
   bool paused = false;
   std::vector<float> lat_ms;
   int64_t batches = 0, batched_queries = 0, completed = 0, failed = 0;
+  int64_t admission_waits = 0;  // dispatcher passes that held a batch back for memory
+  size_t peak_in_flight = 0;    // largest admitted bytes of the batches in flight at once
+  size_t max_batch_bytes = 0;   // estimate for a batch of the configured maximum size
   Clock::time_point t_first, t_last;
   bool any = false;
   std::string fatal;
@@ -208,12 +211,14 @@ struct Server {
         const size_t need = call_bytes((int64_t)take.size(), views);
         if (in_flight > 0 && in_flight + need > budget) {  // wait for memory to free up
           for (auto it = take.rbegin(); it != take.rend(); ++it) queue.push_front(*it);
+          ++admission_waits;
           break;
         }
         s.reqs = std::move(take);
         s.busy = true;
         s.reserved = need;
         in_flight += need;
+        peak_in_flight = std::max(peak_in_flight, in_flight);
         ++batches;
         batched_queries += (int64_t)s.reqs.size();
         lk.unlock();
@@ -258,7 +263,8 @@ gift_status gift_server_create(gift_index* index, const gift_server_params* para
     sv->slot_bytes = V * D * 4 + Bq * K * 16;
     size_t free_b = 0, total_b = 0;
     GIFT_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const size_t per_batch = sv->slot_bytes + sv->call_bytes((int64_t)Bq, (int64_t)V);
+    sv->max_batch_bytes = sv->call_bytes((int64_t)Bq, (int64_t)V);
+    const size_t per_batch = sv->slot_bytes + sv->max_batch_bytes;
     sv->budget = p.memory_budget > 0 ? (size_t)p.memory_budget : (size_t)(0.8 * (double)free_b);
     GIFT_REQUIRE(sv->slot_bytes * p.slots + per_batch <= sv->budget,
                  "memory budget too small for one batch of the configured size");
@@ -345,6 +351,11 @@ gift_status gift_server_stats(gift_server* server, gift_server_stats_t* out) {
     t.batches = sv.batches;
     t.mean_batch = sv.batches ? (float)sv.batched_queries / (float)sv.batches : 0.f;
     t.queued = (int64_t)sv.queue.size();
+    t.admission_waits = sv.admission_waits;
+    t.peak_in_flight_bytes = (int64_t)sv.peak_in_flight;
+    t.budget_bytes = (int64_t)sv.budget;
+    t.max_batch_bytes = (int64_t)sv.max_batch_bytes;
+    t.slot_bytes = (int64_t)(sv.slot_bytes * sv.slots.size());
     if (!sv.lat_ms.empty()) {
       std::vector<float> v = sv.lat_ms;
       auto pct = [&](double q) {

@@ -9,6 +9,7 @@ from .workload import (  # noqa: F401
     Config,
     class_centres,
     shape_views,
+    signed_views,
     query_views,
     kmeans_codebook,
     kmeans_init_rows,

@@ -171,6 +171,21 @@ def shape_views(first_shape: int, n_shapes: int, n_views: int, dim: int,
     return out
 
 
+def signed_views(n_shapes: int, n_views: int, dim: int, n_classes: int, seed: int, centre_seed: int,
+                 weight: float = 0.5) -> np.ndarray:
+    """Signed view features for edge cases the ReLU recipe never reaches: float32 [n, N_v, D].
+
+    v = weight * mu_c + eps with mu_c, eps ~ N(0, I_D) and no ReLU, L2-normalised in
+    float64 and rounded to float32; shape s has class s mod n_classes. Cosines of
+    such views take both signs.
+    """
+    centres = class_centres(n_classes, dim, centre_seed)
+    eps = _gen(seed, 1).standard_normal((n_shapes, n_views, dim))
+    v = weight * centres[np.arange(n_shapes) % n_classes][:, None, :] + eps
+    v /= np.sqrt((v * v).sum(axis=2, keepdims=True))
+    return v.astype(np.float32)
+
+
 def config_views(cfg: Config, first: int, n: int, device=None, query: bool = False):
     """Views of shapes [first, first + n) of a config's database (or query set).
 

@@ -55,3 +55,24 @@ def test_roofline_names_the_fused_pass():
     r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.1, 32.0, 1.0), pairs, 47e9, 188e9, 32768,
                        peaks, "measured", with_traffic=False)
     assert r["kernel"] == "tc_engine<RescorePolicy>" and "tc_engine<ScanPolicy>" in r["all"]
+
+
+def test_roofline_counts_the_rescore_candidates():
+    """With the candidate counters the separate rescore's work is its candidate pairs and rows;
+    the fused pass keeps its three-product accounting and reports the method's work beside it."""
+    peaks = {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}
+    cfg = CONFIGS["db200000x64_d4096_k4096_fp8"]
+    cand = {"rescore_items": 1000, "rescore_items_kept": 400, "cand_pairs": 2e8, "cand_rows": 5e6,
+            "rescore_rows_read": 5.1e6}
+    r = bench.roofline(cfg, _st(8.0, 14.0, 1.0), 7.3e8, 47e9, 188e9, 32768, peaks, "measured", with_traffic=False,
+                       cand=cand)
+    assert r["kernel"] == "tc_engine<RescorePolicy>" and r["bound"] == "hbm"
+    assert abs(r["achieved"] - 5e6 * (4 * cfg.dim + 12) / 14e-3 / 1e9) < 1e-6 * r["achieved"]
+    assert r["candidate_work"]["items_kept_fraction"] == 0.4
+    c2 = CONFIGS["db12000x64_d4096_k1024"]
+    r = bench.roofline(c2, _st(0.0, 12.0, 1.0), 7.3e8, 6e9, 12e9, 64000, peaks, "measured", with_traffic=False,
+                       cand=dict(cand, cand_pairs=1e8))
+    assert r["kernel"] == "tc_engine<FusedPolicy>"
+    assert abs(r["achieved"] - 6 * 7.3e8 * c2.dim / 12e-3 / 1e12) < 1e-6 * r["achieved"]
+    m = (2 * 7.3e8 + 6 * 1e8) * c2.dim / 12e-3 / 1e12 / 2000.0
+    assert abs(r["candidate_work"]["method_work_frac"] - m) < 1e-9

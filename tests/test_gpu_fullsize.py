@@ -13,7 +13,8 @@ import pytest
 
 from oracle import gift_oracle as O
 from synth import CONFIGS, make_config_inputs, DIFF_WORKLOAD, shape_views, projection_matrix, upstream_grad
-from tests.parity import assert_codes, assert_topk, code_margins, recall
+from tests.parity import (FIX, RTOL, ErrorBand, assert_codes, assert_topk, close, code_margins, recall,
+                          reference_memberships)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,37 +69,57 @@ def test_sampled_queries_top100_and_recall(c2):
 
 
 def test_sampled_sif_entries_and_rerank(c2):
+    """S-IF entries of sampled shapes and S' of one query's re-ranked top-5 against the oracle:
+    memberships within the score tolerance (plus half a fixed-point step), S' within the bound
+    propagated from the memberships' FP32 error (tests/parity.py); the oracle's memberships are
+    taken on the GPU's neighbour sets once those are checked to be correct first-k1 sets."""
     import torch
     d, cfg = c2["d"], c2["cfg"]
     N, Nv, k1 = cfg.n_shapes, cfg.n_views, cfg.sif_k1
     off, ids, mem, card = c2["ix"].export_sif()
     X = d["db"]
+    rows = {}
 
-    def F(p):  # oracle activation row of database shape p (Eq. 7, p as a query)
-        return O.membership(_oracle_row(c2, X[p]), k1)
+    def gpu_row(p):  # N_k1(p) and F_p from the exported entries
+        if p not in rows:
+            F, members = np.zeros(N), []
+            for i in range(N):
+                seg = ids[off[i]:off[i + 1]]
+                j = np.searchsorted(seg, p)
+                if j < len(seg) and seg[j] == p:
+                    members.append(i)
+                    F[i] = mem[off[i] + j] * FIX
+            rows[p] = (np.asarray(members), F)
+        return rows[p]
 
+    def ref_row(p):  # oracle memberships of database shape p on the GPU's neighbour set
+        return reference_memberships(_oracle_row(c2, X[p]), gpu_row(p)[0], k1)
+
+    band = ErrorBand()
     for p in (5, 6789):
-        Fp = F(p)
-        srt = -np.sort(-_oracle_row(c2, X[p]))
-        if srt[k1 - 1] - srt[k1] <= 2e-5:
-            continue  # near tie at the k1 boundary: several sets are correct
-        # entries that list p are exactly p's neighbours
-        nb = np.nonzero(Fp)[0]
-        for i in nb:
-            seg = ids[off[i]:off[i + 1]]
-            j = np.searchsorted(seg, p)
-            assert j < len(seg) and seg[j] == p
-            assert abs(mem[off[i] + j] / 2.0 ** 31 - Fp[i]) < 2e-5
-        assert abs(card[p] / 2.0 ** 31 - Fp.sum()) < 1e-3
-    # S' of the re-ranked top-5 of one query against the oracle's Eq. 8
+        F_ref, (members, F) = ref_row(p), gpu_row(p)
+        assert close(F, F_ref, RTOL, FIX / 2).all()
+        assert abs(card[p] * FIX - F_ref.sum()) <= RTOL * F_ref.sum() + k1 * FIX / 2
+        band.add(F, F_ref)
+    # S' of the re-ranked top-5 of one query
     b = 0
     qoff = d["q_off"]
     rid, rsp = c2["ix"].rerank(torch.from_numpy(c2["ids"][:1]).cuda(), torch.from_numpy(c2["sc"][:1]).cuda(),
                                k1=k1, topk=5)
     rid, rsp = rid.cpu().numpy()[0], rsp.cpu().numpy()[0]
-    Fq = O.membership(_oracle_row(c2, d["q"][qoff[b]:qoff[b + 1]]), k1)
+    Fq = reference_memberships(_oracle_row(c2, d["q"][qoff[b]:qoff[b + 1]]), c2["ids"][b, :k1], k1)
+    gq = np.zeros(N)
+    gq[c2["ids"][b, :k1]] = c2["sc"][b, :k1]
+    band.add(gq, Fq)
+    refs = {}
+    for p in rid:
+        refs[int(p)] = ref_row(int(p))
+        band.add(gpu_row(int(p))[1], refs[int(p)])
+    rtol, atol = band.sprime_tolerance(k1, Fq.sum())
+    assert rtol <= 1e-5, (band.lo, band.hi)
     for p, v in zip(rid, rsp):
-        assert abs(O.contextual(Fq, F(int(p))) - v) < 1e-4
+        ref = O.contextual(Fq, refs[int(p)])
+        assert abs(v - ref) <= rtol * ref + atol, (p, v, ref)
 
 
 DIFF_SAMPLED_SHAPES = (5, 3001)

@@ -94,3 +94,33 @@ def test_bounded_wait_times_out_and_recovers(served):
             sv.submit(np.zeros((4 * 64 + 1, ix.dim), np.float32))  # more views than a batch holds
     finally:
         sv.close()
+
+
+def test_memory_admission_holds_batches_back(served):
+    """A memory budget that fits one full batch in flight: the dispatcher must hold later
+    batches back until memory frees up (admission_waits > 0, the admitted bytes never above
+    the budget while more than one batch is in flight), and every result still equals the
+    request's result alone."""
+    gift, ix, queries = served
+    kw = dict(slots=3, max_batch_queries=16, max_batch_views=16 * 64, topk=20, rerank=True)
+    probe = gift.Server(ix, **kw)
+    st0 = probe.stats()
+    alone = [probe.wait(probe.submit(q)) for q in queries]
+    probe.close()
+    budget = st0["slot_bytes"] + st0["max_batch_bytes"] * 3 // 2  # one full batch, not two
+    sv = gift.Server(ix, memory_budget=budget, start_paused=True, **kw)
+    try:
+        tickets = [sv.submit(q) for q in queries * 3]  # queued while paused: full batches from the start
+        sv.resume()
+        mixed = [sv.wait(t) for t in tickets]
+        st = sv.stats()
+        assert st["budget_bytes"] == budget - st0["slot_bytes"]
+        assert st["admission_waits"] > 0, st
+        assert st["peak_in_flight_bytes"] <= max(st["budget_bytes"], st["max_batch_bytes"]), st
+        assert st["completed"] == 3 * len(queries) and st["failed"] == 0
+        for k, (ib, sb) in enumerate(mixed):
+            ia, sa = alone[k % len(queries)]
+            assert np.array_equal(ia, ib)
+            assert np.allclose(sa, sb, rtol=1e-5, atol=1e-6)
+    finally:
+        sv.close()
