@@ -119,16 +119,18 @@ def kernel_source_hash(files):
 
 
 def recorded_traffic(kernel: str, src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    """DRAM bytes per unit of work from the committed ncu summary (captured on a reduced
+    case of the same kernel), while the kernel's source is unchanged since the capture:
+    (bytes per unit, unit, capture workload), or (None, None, None)."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     try:
         for line in open(path):
             c = [x.strip() for x in line.strip().strip("|").split("|")]
-            if len(c) >= 4 and c[0] == kernel and c[1] == src_hash:
-                return float(c[2]), c[3]
-    except OSError:
+            if len(c) >= 5 and c[0] == kernel and c[1] == src_hash:
+                return float(c[3]), c[4], c[2]
+    except (OSError, ValueError):
         pass
-    return None, None
+    return None, None, None
 
 
 # ---------------------------------------------------------------- reference arm
@@ -254,7 +256,14 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
         return None
     dom = max(table, key=lambda k: table[k]["ms"])
     src_hash = kernel_source_hash(kernels[dom][3] + ["tc_engine.cuh", "tc_common.cuh"])
-    traffic, _ = recorded_traffic(dom, src_hash) if with_traffic else (None, None)
+    per_unit, unit, capture = recorded_traffic(dom, src_hash) if with_traffic else (None, None, None)
+    # units of this launch: rows of the touched lists (scan, fused pass), rows the rescore reads,
+    # rows quantised
+    eb = 1 if cfg.storage == "fp8" else (2 if cfg.storage == "bf16" else 4)
+    units = {"touched row": scan_bytes / (D * eb + 12.0),
+             "rescore row read": (cand or {}).get("rescore_rows_read"),
+             "row quantised": assign_rows}.get(unit)
+    traffic = per_unit * units if per_unit is not None and units else None
     dt = table[dom]
     if dt["bound"] == "hbm":
         psrc = f"{peak_src} hbm_gbs"
@@ -266,7 +275,10 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
     if dom == "tc_engine<RescorePolicy>" and cand:
         work = "algorithmic bytes: the candidate rows (two-part BF16 row + id + scale) of the touched lists, read once"
     out = {"kernel": dom, "bound": dt["bound"], "achieved": dt["achieved"], "peak": dt["peak"],
-           "unit": dt["unit"], "frac": dt["frac"], "traffic": traffic, "peak_source": psrc,
+           "unit": dt["unit"], "frac": dt["frac"], "traffic": traffic,
+           "traffic_source": (f"ncu dram__bytes_read + write on {capture}: {per_unit:.4g} B per {unit}, x {units:.4g}"
+                              if traffic is not None else None),
+           "peak_source": psrc,
            "kernel_ms": dt["ms"], "work": work, "src_hash": src_hash, "all": table,
            "scan_hbm": {"algorithmic_bytes": scan_bytes,
                         "achieved_gbs": (scan_bytes / (st["scan_kernel_ms"] / 1e3) / 1e9
@@ -504,6 +516,25 @@ def measure_workload(cfg, args, gift, torch, dev, rank, world, codebook=None, se
     cand = {k: stages[-1][0][k] for k in ("rescore_items", "rescore_items_kept", "cand_pairs", "cand_rows",
                                           "rescore_rows_read")}
 
+    # ---- device time per step at other rescore depths (recall at each depth comes from the oracle)
+    depth_sweep = None
+    if large and R > 0:
+        depth_sweep = {}
+        for r_ in (0, 200, 400, 600, 800, R):
+            if r_ > R or (0 < r_ < topk):
+                continue
+            ix.set_rescore_depth(r_)
+            step(0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(5):
+                step(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            depth_sweep[r_] = {"ms_per_step": e0.elapsed_time(e1) / 5,
+                               "queries_per_s": 5 * B / (e0.elapsed_time(e1) / 1e3)}
+        ix.set_rescore_depth(R)
+
     # ---- end to end through the C ABI with host buffers: pinned query features in,
     # ids / scores out, every step; three streams rotate so that the copies of
     # one batch overlap the kernels of the others
@@ -593,10 +624,10 @@ def measure_workload(cfg, args, gift, torch, dev, rank, world, codebook=None, se
            "e2e": {"value": B / (e2e_ms / 1e3) * world, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "streams": n_streams},
            "clocks": clocks, "gpu_launches": n_launches, "gpu_launches_per_step": n_launches / args.steps,
-           "build_s": build_s, "serving": serving}
+           "build_s": build_s, "serving": serving, "rescore_depth_sweep": depth_sweep}
     peaks, peak_src = measured_peaks()
     res["roofline"] = roofline(cfg, st, work["scan_pairs"], work["scan_bytes"], work["rescore_bytes"],
-                               work["assign_rows"], peaks, peak_src, with_traffic=not large, cand=cand)
+                               work["assign_rows"], peaks, peak_src, cand=cand)
     res["_recall_gpu"] = recall_gpu
     res["_batches"] = batches
     return res, data, ix
@@ -770,7 +801,8 @@ def main():
             "dtype": "e4m3" if cfg.storage == "fp8" else "bf16", "data": "synthetic", "config": res["config"],
             "exact": res["exact"], "stages_ms": res["stages_ms"], "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": res["gpu_launches"], "gpu_launches_per_step": res["gpu_launches_per_step"],
-            "build_s": res["build_s"], "serving": res["serving"], "roofline": res["roofline"]}
+            "build_s": res["build_s"], "serving": res["serving"], "roofline": res["roofline"],
+            "rescore_depth_sweep": res["rescore_depth_sweep"]}
     db_codes = None
     if not large and not args.no_recall and rank == 0:
         line["recall_at_100"], db_codes = dense_recall(cfg, data, ix, res, cfg.topk)

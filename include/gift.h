@@ -91,6 +91,9 @@ typedef struct {
   int32_t max_runs;         /* most runs in one list                       */
   int32_t max_sif_entry;    /* longest S-IF entry                          */
   int64_t n_entries;        /* F-IF entries: n_rows * db_ma                */
+  int32_t sif_shapes;       /* shapes the S-IF covers (0 = no S-IF): N, or the
+                               whole database for gift_sif_from_neighbours  */
+  int32_t sif_k1;           /* k1 of the S-IF                              */
 } gift_index_info_t;
 
 /* Per-stage device times of the last timed gift_query / gift_rerank call
@@ -384,7 +387,8 @@ GIFT_API gift_status gift_export_fif(const gift_index* index, int32_t* db_codes,
  * Copy the S-IF of a built index (device or host): entry_offsets int64 [N + 1],
  * entry_ids int32 [N * k1] (shape p of each pair), entry_members uint32
  * [N * k1] (F_p[i] in fixed point 2^31), card uint64 [N] (||F_i||_1 in the same
- * fixed point). Any pointer may be NULL. Synchronises `stream`.
+ * fixed point), N and k1 as gift_index_info reports them (sif_shapes, sif_k1).
+ * Any pointer may be NULL. Synchronises `stream`.
  * Errors: EUNSUPPORTED when the index has no S-IF.
  */
 GIFT_API gift_status gift_export_sif(const gift_index* index, int64_t* entry_offsets, int32_t* entry_ids,

@@ -52,7 +52,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("n_rows", ctypes.c_int64),
                 ("n_lists_nonempty", ctypes.c_int32), ("max_list_len", ctypes.c_int32),
                 ("n_runs", ctypes.c_int64), ("max_runs", ctypes.c_int32),
-                ("max_sif_entry", ctypes.c_int32), ("n_entries", ctypes.c_int64)]
+                ("max_sif_entry", ctypes.c_int32), ("n_entries", ctypes.c_int64),
+                ("sif_shapes", ctypes.c_int32), ("sif_k1", ctypes.c_int32)]
 
 
 class _Timing(ctypes.Structure):
@@ -282,11 +283,15 @@ class Index:
         return codes, off, rows
 
     def export_sif(self):
-        """(entry_offsets [N+1], entry_ids, entry_members uint32, card uint64 [N]) as numpy arrays."""
-        N = self.n_shapes
+        """(entry_offsets [N+1], entry_ids, entry_members uint32, card uint64 [N]) as numpy arrays;
+        N and k1 are the S-IF's own (gift_index_info)."""
+        info = self.info()
+        N, k1 = info["sif_shapes"], info["sif_k1"]
+        if N <= 0:
+            raise GiftError(5, "index built without an S-IF")
         off = np.empty(N + 1, np.int64)
-        ids = np.empty(N * self.sif_k1, np.int32)
-        mem = np.empty(N * self.sif_k1, np.uint32)
+        ids = np.empty(N * k1, np.int32)
+        mem = np.empty(N * k1, np.uint32)
         card = np.empty(N, np.uint64)
         _check(load().gift_export_sif(self._h, _ptr(off), _ptr(ids), _ptr(mem), _ptr(card), _stream()))
         return off, ids, mem, card

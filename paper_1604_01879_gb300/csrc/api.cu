@@ -1250,6 +1250,8 @@ gift_status gift_index_info(const gift_index* index, gift_index_info_t* out) {
     out->n_runs = ix.n_runs;
     out->max_runs = ix.max_runs;
     out->max_sif_entry = ix.max_sif_entry;
+    out->sif_shapes = ix.sif_off ? ix.sif_n : 0;
+    out->sif_k1 = ix.sif_off ? ix.k1 : 0;
   });
 }
 

@@ -29,7 +29,7 @@ def test_roofline_picks_dominant_kernel_and_its_roof():
 
 
 def test_recorded_traffic_ignores_other_sources(tmp_path, monkeypatch):
-    assert bench.recorded_traffic("no-such-kernel", "0" * 12) == (None, None)
+    assert bench.recorded_traffic("no-such-kernel", "0" * 12) == (None, None, None)
 
 
 def test_roofline_without_tensor_core_scan():
@@ -76,3 +76,25 @@ def test_roofline_counts_the_rescore_candidates():
     assert abs(r["achieved"] - 6 * 7.3e8 * c2.dim / 12e-3 / 1e12) < 1e-6 * r["achieved"]
     m = (2 * 7.3e8 + 6 * 1e8) * c2.dim / 12e-3 / 1e12 / 2000.0
     assert abs(r["candidate_work"]["method_work_frac"] - m) < 1e-9
+
+
+def test_traffic_is_scaled_by_the_launch_units(tmp_path, monkeypatch):
+    """A capture on a reduced case gives bytes per unit; the entry's traffic is that times the
+    units the timed launch processed (here rows the rescore read)."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.md").write_text(
+        "| kernel | source hash | capture | bytes per unit | unit | note |\n"
+        "|---|---|---|---|---|---|\n"
+        "| tc_engine<RescorePolicy> | abc123 | reduced | 16500 | rescore row read | x |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda files: "abc123")
+    cand = {"rescore_items": 10, "rescore_items_kept": 9, "cand_pairs": 1e8, "cand_rows": 9e6,
+            "rescore_rows_read": 1.1e7}
+    r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.0, 31.0, 1.0), 7e8, 47e9, 188e9, 32768,
+                       {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}, "measured", cand=cand)
+    assert r["kernel"] == "tc_engine<RescorePolicy>"
+    assert r["traffic"] == 16500 * 1.1e7 and "reduced" in r["traffic_source"]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda files: "changed")
+    r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.0, 31.0, 1.0), 7e8, 47e9, 188e9, 32768,
+                       {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}, "measured", cand=cand)
+    assert r["traffic"] is None
