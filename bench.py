@@ -497,8 +497,17 @@ def measure_workload(cfg, args, gift, torch, dev, rank, world, codebook=None, se
         torch.distributed.barrier()
     total_ms = float(t_tensor.item())
     if args.profile:
-        log(f"[bench] profile run: {total_ms / args.steps:.3f} ms/step")
-        return {"ms_per_step": total_ms / args.steps}, data, ix
+        # one more step, timed by the library, outside the captured range: the work
+        # counters that scale an ncu capture of these launches to other workloads
+        ix.set_timing(True)
+        st_q, _ = step(0, timing=True)
+        ix.set_timing(False)
+        eb = 1 if cfg.storage == "fp8" else (2 if cfg.storage == "bf16" else 4)
+        counters = {k: st_q[k] for k in ("scan_bytes", "rescore_bytes", "scan_pairs", "assign_rows", "rescore_items",
+                                         "rescore_items_kept", "cand_pairs", "cand_rows", "rescore_rows_read")}
+        counters["touched_rows"] = st_q["scan_bytes"] / (cfg.dim * eb + 12)
+        log(f"[bench] profile run: {total_ms / args.steps:.3f} ms/step; work per step {json.dumps(counters)}")
+        return {"ms_per_step": total_ms / args.steps, "work": counters}, data, ix
 
     # ---- per-stage device times (CUDA events recorded by the library on this stream)
     ix.set_timing(True)

@@ -381,93 +381,6 @@ __global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, in
   }
 }
 
-// ---------------------------------------------------------------- gathered G
-// G[i] = sum_p wU[p, i] V[p * nv + amT[p, i]]: every (query view, shape) block of
-// the one-hot matrix has a single non-zero, so the row it selects is gathered
-// and added on the CUDA cores instead of multiplying the whole block on the
-// tensor cores (1/nv of whose products are useful). CTA: 128 query views x 128
-// columns; warp w: views 16w .. 16w+15, lane: columns 4 lane .. 4 lane+3, a
-// float4 accumulator per view. Shape p's nv rows (this CTA's columns) and each
-// view's (argmax, weight) are staged in shared memory by cp.async one shape
-// ahead; shapes are added in ascending order (deterministic).
-constexpr int kGQ = 128, kGD = 128, kGatherMaxNv = 64;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__global__ __launch_bounds__(256) void k_gather_views(const float* __restrict__ V, const int16_t* __restrict__ amT,
-                                                      const float* __restrict__ wU, int64_t nq, int Np, int nv,
-                                                      int dout, float* __restrict__ G) {
-  extern __shared__ __align__(16) float g_smem[];  // [2][nv][kGD] rows, then [2][kGQ] (argmax, weight)
-  float* rows = g_smem;
-  int2* jw = reinterpret_cast<int2*>(g_smem + 2 * nv * kGD);
-  const int64_t i0 = (int64_t)blockIdx.x * kGQ;
-  const int c0 = blockIdx.y * kGD;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int pieces = min(kGD, dout - c0) >> 2;  // 16-byte pieces per row (dout % 16 == 0)
-  auto stage = [&](int p, int buf) {
-    for (int t = tid; t < nv * pieces; t += 256) {
-      const int r = t / pieces, q4 = t - r * pieces;
-      cp_async16(rows + ((size_t)buf * nv + r) * kGD + q4 * 4, V + ((int64_t)p * nv + r) * dout + c0 + q4 * 4);
-    }
-    if (tid < kGQ) {
-      const int64_t i = i0 + tid;
-      int j = 0;
-      float wt = 0.f;
-      if (i < nq) {
-        j = amT[(int64_t)p * nq + i];
-        wt = wU[(int64_t)p * nq + i];
-        if (j < 0 || j >= nv) j = 0;  // the weight was taken for row 0 as well
-      }
-      jw[buf * kGQ + tid] = make_int2(j, __float_as_int(wt));
-    }
-    cp_async_commit();
-  };
-  float4 acc[16];
-#pragma unroll
-  for (int v = 0; v < 16; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const bool active = lane < pieces;
-  stage(0, 0);
-  for (int p = 0; p < Np; ++p) {
-    const int buf = p & 1;
-    if (p + 1 < Np) {
-      stage(p + 1, buf ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    if (active) {
-      const int2* J = jw + buf * kGQ + warp * 16;
-      const float* R = rows + (size_t)buf * nv * kGD + lane * 4;
-#pragma unroll
-      for (int v = 0; v < 16; ++v) {
-        const int2 e = J[v];
-        const float4 x = *reinterpret_cast<const float4*>(R + e.x * kGD);
-        const float wt = __int_as_float(e.y);
-        acc[v].x = fmaf(wt, x.x, acc[v].x);
-        acc[v].y = fmaf(wt, x.y, acc[v].y);
-        acc[v].z = fmaf(wt, x.z, acc[v].z);
-        acc[v].w = fmaf(wt, x.w, acc[v].w);
-      }
-    }
-    __syncthreads();  // buffer buf is restaged at the next iteration
-  }
-  if (!active) return;
-#pragma unroll
-  for (int v = 0; v < 16; ++v) {
-    const int64_t i = i0 + warp * 16 + v;
-    if (i < nq) *reinterpret_cast<float4*>(G + i * dout + c0 + lane * 4) = acc[v];
-  }
-}
-
 __global__ void k_view_coef(const int32_t* __restrict__ vquery, const int32_t* __restrict__ qoff, int64_t nq,
                             float* __restrict__ coef) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -653,16 +566,7 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   GIFT_LAUNCHED("k_onehot_prep");
   float* G = sc.get<float>((size_t)std::max(nq, nr) * dout);  // G = A V, then H = A^T U
   const int sms = device_sm_count();
-  const bool gather = nv <= kGatherMaxNv && ((uintptr_t)P.V & 15) == 0 && Np > 0;
-  if (gather) {
-    const size_t smem = (size_t)2 * nv * kGD * 4 + 2 * kGQ * 8;
-    GIFT_CUDA(cudaFuncSetAttribute(k_gather_views, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gather_views<<<dim3((unsigned)cdiv(nq, kGQ), (unsigned)cdiv(dout, kGD)), 256, smem, s>>>(P.V, amT, wU, nq, Np,
-                                                                                              nv, dout, G);
-    GIFT_LAUNCHED("k_gather_views");
-    k_tangent<<<(unsigned)cdiv(nq, 8), 256, 0, s>>>(P.U, P.uinv, G, nq, dout, dU);
-    GIFT_LAUNCHED("k_tangent");
-  } else {
+  {
     int64_t ldr = 0;
     const Operand Vt = make_transposed(P.V, GIFT_F32, nr, dout, ldr, sc, s);  // [dout, ldr], K = database views
     OneHotPolicy<true> pol;
