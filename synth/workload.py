@@ -91,10 +91,11 @@ CONFIGS = {
         rescore_r=200, topk=100, sif_k1=50, kmeans_shapes=256, kmeans_iters=10,
         seed=5),
     # reduced case of the FP8 / MA = 2 configuration for kernel profiles (~4 GB on the device,
-    # list stores larger than L2): 50 shapes per class, 8 codewords per class
+    # list stores larger than L2) with the large one's list structure: 8 codewords per class,
+    # ~8 query slots per list (32-query batches), candidates of about two classes per query
     "db3200x64_d4096_k512_fp8": Config(
         name="db3200x64_d4096_k512_fp8", n_shapes=3200, n_views=64, dim=4096, n_classes=64, n_codewords=512,
-        n_queries=512, query_ma=2, storage="fp8", rescore_r=200, topk=100, sif_k1=50, batch=256,
+        n_queries=256, query_ma=2, storage="fp8", rescore_r=100, topk=100, sif_k1=50, batch=32,
         kmeans_shapes=128, kmeans_iters=6, seed=6, generator="counter"),
     # 16x scale-up of ModelNet40 with FP8 store and query-side MA = 2
     "db200000x64_d4096_k4096_fp8": Config(
