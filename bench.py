@@ -755,7 +755,7 @@ def main():
         codebook = config_codebook(cfg)
         log(f"[bench] codebook fixture in {time.time() - t0:.1f}s")
         q_sample = sorted({int(round(x)) for x in np.linspace(0, cfg.n_queries - 1, max(1, args.oracle_queries))})
-        if not args.no_recall and not args.profile and rank == 0:
+        if not args.no_recall and not args.profile and rank == 0 and world == 1:  # recall: the N = 1 run
             import multiprocessing as mp
             ctx = mp.get_context("spawn")  # before the first CUDA call
             oracle_conn, child = ctx.Pipe(duplex=False)
@@ -795,6 +795,8 @@ def main():
         return
 
     serve_s = (15.0 if large else 5.0) if args.serve_seconds is None else args.serve_seconds
+    if world > 1:
+        serve_s = 0.0  # serving is measured on one GPU
     res, data, ix = measure_workload(cfg, args, gift, torch, dev, rank, world, codebook=codebook,
                                      serve_seconds=serve_s,
                                      recall_queries=q_sample if oracle_conn is not None else None)
