@@ -420,7 +420,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
 
   tm.mark(ST_COMBINE);
   float* S = sc.get<float>((size_t)B * N);
-  fif_combine(ix, P, table, S, nullptr, 0, nullptr, s);
+  fif_combine(ix, P, table, S, nullptr, 0, nullptr, sc, s);
 
   tm.mark(ST_TOPK);
   if (R <= 0) {
@@ -443,7 +443,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
       fif_scan(ix, P, table, true, cand_sorted, Rr, s);
   }
   float* cand_score = sc.get<float>((size_t)B * Rr);
-  fif_combine(ix, P, fused ? table32 : table, nullptr, cand_sorted, Rr, cand_score, s);
+  fif_combine(ix, P, fused ? table32 : table, nullptr, cand_sorted, Rr, cand_score, sc, s);
   tm.mark(ST_TOPK);
   sort_candidates(cand_sorted, cand_score, B, Rr, topk, out_ids, out_scores, s);
 }

@@ -47,6 +47,6 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
 void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_sorted, int R, Scratch& sc,
                        cudaStream_t s);
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
-                 const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s);
+                 const int32_t* cand_sorted, int R, float* cand_score, Scratch& sc, cudaStream_t s);
 
 }  // namespace gift

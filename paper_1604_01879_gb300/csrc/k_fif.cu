@@ -29,7 +29,6 @@ namespace gift {
 namespace {
 
 constexpr int kCombineT = 256;
-constexpr int kCombineChunk = 12288;  // shapes per combine block (96 KiB of uint64)
 
 __global__ void k_slot_setup(const int32_t* __restrict__ perm, int64_t nslots, int ma,
                              const int32_t* __restrict__ skeys, const int32_t* __restrict__ nruns,
@@ -293,6 +292,10 @@ struct CombineArgs {
   const int32_t* cand;       // [B, R] sorted ids (CAND)
   int R;
   float* cand_score;         // [B, R] (CAND)
+  const int32_t* vquery;     // [nv] query of each view
+  unsigned long long* acc;   // [B, N] (dense) or [B, R] (candidates, ma > 1) fixed-point sums, zeroed
+  int64_t nv;
+  int groups;                // blocks per query of k_fif_combine_ma_cand
 };
 
 // a shape's term in signed 2^-32 fixed point; two's complement sums in uint64
@@ -327,63 +330,79 @@ __device__ __forceinline__ bool view_term(const CombineArgs& a, int64_t v, int32
   return !(t < 0.f) || all_views_matched(a, v, p);
 }
 
-template <bool CAND>
-__global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) {
+// Dense shape scores: one warp per (query view, assignment) walks the runs of
+// that list and adds each shape's term into the query's row of fixed-point
+// sums (global atomics; the runs of one list are distinct shapes). A shape
+// reached through several of the view's lists counts once, with the largest
+// maximum, added by the lowest assignment that reaches it.
+__global__ __launch_bounds__(kCombineT) void k_fif_combine_views(const CombineArgs a) {
+  const int64_t item = ((int64_t)blockIdx.x * kCombineT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= a.nv * a.ma) return;
+  const int64_t v = item / a.ma;
+  const int s_a = (int)(item % a.ma);
+  const int32_t s = a.view_slot[item];
+  const int k = a.skeys[s];
+  const int32_t* rs = a.run_shape + a.run_off[k];
+  const int nr = a.nruns[k];
+  const int64_t rb = a.runbase[s];
+  unsigned long long* row = a.acc + (int64_t)a.vquery[v] * a.N;
+  for (int r = lane; r < nr; r += 32) {
+    const int32_t p = rs[r];
+    uint32_t m = a.table[rb + r];
+    bool skip = false;
+    for (int s_b = 0; s_b < a.ma && !skip; ++s_b) {
+      if (s_b == s_a) continue;
+      const int32_t s2 = a.view_slot[v * a.ma + s_b];
+      const int k2 = a.skeys[s2];
+      const int r2 = find_sorted(a.run_shape + a.run_off[k2], a.nruns[k2], p);
+      if (r2 < 0) continue;
+      if (s_b < s_a) skip = true;  // the lower assignment owns this shape
+      else m = max(m, a.table[a.runbase[s2] + r2]);
+    }
+    float t;
+    if (skip || !view_term(a, v, p, m, t)) continue;
+    atomicAdd(row + p, fix32(t));
+  }
+}
+
+// fixed-point sums -> scores (1/|V(x_q)|) sum (Eq. 4), n = row width
+__global__ void k_unfix_rows(const unsigned long long* __restrict__ acc, const int32_t* __restrict__ qoff, int B,
+                             int64_t n, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * n) return;
+  const int q = (int)(i / n);
+  out[i] = unfix32(acc[i], (float)(qoff[q + 1] - qoff[q]));
+}
+
+// Candidate scores (ma = 1): one block per query, its warps over the query's
+// views; a run's term is added at its shape's position among the query's
+// sorted candidates (shared fixed-point sums).
+__global__ __launch_bounds__(kCombineT) void k_fif_combine_cand(const CombineArgs a) {
   extern __shared__ unsigned long long acc[];
   const int q = blockIdx.x;
-  const int c0 = CAND ? 0 : blockIdx.y * kCombineChunk;
-  const int c1 = CAND ? 0 : min(a.N, c0 + kCombineChunk);
-  const int width = CAND ? a.R : (c1 - c0);
-  for (int i = threadIdx.x; i < width; i += kCombineT) acc[i] = 0ull;
+  for (int i = threadIdx.x; i < a.R; i += kCombineT) acc[i] = 0ull;
   __syncthreads();
   const int v0 = a.qoff[q], v1 = a.qoff[q + 1];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t* cand = CAND ? a.cand + (int64_t)q * a.R : nullptr;
+  const int32_t* cand = a.cand + (int64_t)q * a.R;
   for (int v = v0 + w; v < v1; v += kCombineT / 32) {
-    for (int s_a = 0; s_a < a.ma; ++s_a) {
-      const int32_t s = a.view_slot[(int64_t)v * a.ma + s_a];
-      const int k = a.skeys[s];
-      const int32_t* rs = a.run_shape + a.run_off[k];
-      const int nr = a.nruns[k];
-      const int64_t rb = a.runbase[s];
-      int lo = 0, hi = nr;
-      if (!CAND) {
-        lo = lower_bound_i32(rs, nr, c0);
-        hi = lower_bound_i32(rs, nr, c1);
-      }
-      for (int r = lo + lane; r < hi; r += 32) {
-        const int32_t p = rs[r];
-        uint32_t m = a.table[rb + r];
-        bool skip = false;
-        for (int s_b = 0; s_b < a.ma && !skip; ++s_b) {
-          if (s_b == s_a) continue;
-          const int32_t s2 = a.view_slot[(int64_t)v * a.ma + s_b];
-          const int k2 = a.skeys[s2];
-          const int r2 = find_sorted(a.run_shape + a.run_off[k2], a.nruns[k2], p);
-          if (r2 < 0) continue;
-          if (s_b < s_a) skip = true;  // the lower assignment owns this shape
-          else m = max(m, a.table[a.runbase[s2] + r2]);
-        }
-        float t;
-        if (skip || !view_term(a, v, p, m, t)) continue;
-        int idx;
-        if (CAND) {
-          idx = find_sorted(cand, a.R, p);
-          if (idx < 0) continue;
-        } else {
-          idx = p - c0;
-        }
-        atomicAdd(&acc[idx], fix32(t));
-      }
+    const int32_t s = a.view_slot[v];
+    const int k = a.skeys[s];
+    const int32_t* rs = a.run_shape + a.run_off[k];
+    const int nr = a.nruns[k];
+    const int64_t rb = a.runbase[s];
+    for (int r = lane; r < nr; r += 32) {
+      const int32_t p = rs[r];
+      float t;
+      if (!view_term(a, v, p, a.table[rb + r], t)) continue;
+      const int idx = find_sorted(cand, a.R, p);
+      if (idx >= 0) atomicAdd(&acc[idx], fix32(t));
     }
   }
   __syncthreads();
   const float Vq = (float)(v1 - v0);
-  for (int i = threadIdx.x; i < width; i += kCombineT) {
-    const float val = unfix32(acc[i], Vq);
-    if (CAND) a.cand_score[(int64_t)q * a.R + i] = val;
-    else a.S[(int64_t)q * a.N + c0 + i] = val;
-  }
+  for (int i = threadIdx.x; i < a.R; i += kCombineT) a.cand_score[(int64_t)q * a.R + i] = unfix32(acc[i], Vq);
 }
 
 // Candidate scores with multiple assignment (ma > 1): each warp takes one view
@@ -397,7 +416,7 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine(const CombineArgs a) 
 constexpr int kCombineWarps = kCombineT / 32;
 __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const CombineArgs a) {
   extern __shared__ unsigned long long acc[];  // [R] sums, then int32 cand[R], then uint32 [warps][R] view maxima
-  const int q = blockIdx.x, R = a.R;
+  const int q = blockIdx.x / a.groups, g = blockIdx.x % a.groups, R = a.R;
   int32_t* cs = reinterpret_cast<int32_t*>(acc + R);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* vmax = reinterpret_cast<uint32_t*>(cs + R) + (size_t)w * R;
@@ -408,7 +427,7 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
   for (int i = lane; i < R; i += 32) vmax[i] = 0u;
   __syncthreads();
   const int v0 = a.qoff[q], v1 = a.qoff[q + 1];
-  for (int v = v0 + w; v < v1; v += kCombineWarps) {
+  for (int v = v0 + g * kCombineWarps + w; v < v1; v += a.groups * kCombineWarps) {
     // lane t < ma: the list of assignment t
     int64_t off = 0, rb = 0;
     int n = 0;
@@ -454,8 +473,9 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
     __syncwarp();
   }
   __syncthreads();
-  const float Vq = (float)(v1 - v0);
-  for (int i = threadIdx.x; i < R; i += kCombineT) a.cand_score[(int64_t)q * R + i] = unfix32(acc[i], Vq);
+  // this block's views' part of the sums (the query's groups add up in a.acc)
+  for (int i = threadIdx.x; i < R; i += kCombineT)
+    if (acc[i] != 0ull) atomicAdd(a.acc + (int64_t)q * R + i, acc[i]);
 }
 
 }  // namespace
@@ -528,7 +548,7 @@ void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
 }
 
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,
-                 const int32_t* cand_sorted, int R, float* cand_score, cudaStream_t s) {
+                 const int32_t* cand_sorted, int R, float* cand_score, Scratch& sc, cudaStream_t s) {
   CombineArgs a;
   a.qoff = P.qoff;
   a.ma = P.ma;
@@ -548,25 +568,43 @@ void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float
   a.cand = cand_sorted;
   a.R = R;
   a.cand_score = cand_score;
+  a.vquery = P.vquery;
+  a.nv = P.nv;
+  a.acc = nullptr;
+  a.groups = 1;
+  if (P.B <= 0) return;
   if (P.ma > 1 && cand_sorted) {
     GIFT_REQUIRE(R <= 1024, "rescore depth must be <= 1024");
+    // a query's views spread over several blocks (about one view per warp), so
+    // that a batch of a few hundred queries fills every SM
+    const int64_t per_query = cdiv(P.nv, (int64_t)P.B);
+    a.groups = (int)std::min<int64_t>(16, std::max<int64_t>(1, cdiv(per_query, (int64_t)kCombineWarps)));
+    a.acc = sc.get<unsigned long long>((size_t)P.B * R);
+    GIFT_CUDA(cudaMemsetAsync(a.acc, 0, (size_t)P.B * R * 8, s));
     const size_t smem = (size_t)R * (8 + 4 + 4 * kCombineWarps);
     GIFT_CUDA(cudaFuncSetAttribute(k_fif_combine_ma_cand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fif_combine_ma_cand<<<(unsigned)P.B, kCombineT, smem, s>>>(a);
+    k_fif_combine_ma_cand<<<(unsigned)(P.B * a.groups), kCombineT, smem, s>>>(a);
     GIFT_LAUNCHED("k_fif_combine_ma_cand");
+    k_unfix_rows<<<(unsigned)cdiv((int64_t)P.B * R, 256), 256, 0, s>>>(a.acc, P.qoff, P.B, R, cand_score);
+    GIFT_LAUNCHED("k_unfix_rows");
     return;
   }
-  GIFT_CUDA(cudaFuncSetAttribute(k_fif_combine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kCombineChunk * 8));
   if (cand_sorted) {
     GIFT_REQUIRE(R <= 1024, "rescore depth must be <= 1024");
-    k_fif_combine<true><<<dim3((unsigned)P.B, 1), kCombineT, (size_t)R * 8, s>>>(a);
-  } else {
-    const unsigned chunks = (unsigned)cdiv(a.N, kCombineChunk);
-    const size_t smem = (size_t)std::min(a.N, kCombineChunk) * 8;
-    k_fif_combine<false><<<dim3((unsigned)P.B, chunks), kCombineT, smem, s>>>(a);
+    k_fif_combine_cand<<<(unsigned)P.B, kCombineT, (size_t)R * 8, s>>>(a);
+    GIFT_LAUNCHED("k_fif_combine_cand");
+    return;
   }
-  GIFT_LAUNCHED("k_fif_combine");
+  const int64_t n = (int64_t)P.B * a.N;
+  a.acc = sc.get<unsigned long long>((size_t)n);
+  GIFT_CUDA(cudaMemsetAsync(a.acc, 0, (size_t)n * 8, s));
+  const int64_t warps = P.nv * P.ma;
+  if (warps > 0) {
+    k_fif_combine_views<<<(unsigned)cdiv(warps * 32, (int64_t)kCombineT), kCombineT, 0, s>>>(a);
+    GIFT_LAUNCHED("k_fif_combine_views");
+  }
+  k_unfix_rows<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(a.acc, P.qoff, P.B, a.N, S_dense);
+  GIFT_LAUNCHED("k_unfix_rows");
 }
 
 }  // namespace gift

@@ -9,13 +9,18 @@
 // into the per-(slot, run) table with atomicMax on its order-preserving key
 // (f2key, so negative cosines keep their order; 0 = not written).
 //
-// Scan: BF16 store, one product per k-block, 256 entries per tile.
+// (Lists touched by at most 64 slots of a batch swap the roles: entries are the
+// MMA rows and slots the columns, see the slot-column policies below.)
+//
+// Scan: BF16 or E4M3 store, one product per k-block, 256 entries per tile.
 // Rescore: two-part BF16 operands (x = hi + lo) and three products, the
 // reduction split in four chunks accumulated in separate TMEM buffers and
 // summed in FP32 by the epilogue; only runs of the query's top-R candidate
 // shapes are kept, and only work items that hold such a run are run (a
 // pre-pass lists them): the FP32-level rescore needs the rows of its
 // candidates' runs, not every row of a touched list.
+#include <type_traits>
+
 #include "fif_plan.cuh"
 #include "gift_internal.cuh"
 #include "tc_engine.cuh"
@@ -40,7 +45,8 @@ struct ListSched {
   const int64_t* list_off;  // [K+1]
   int nkb;
   __device__ __forceinline__ int64_t total_items() const { return woff[K]; }
-  template <int TN>
+  // TN entries x TS slots per item
+  template <int TN, int TS = tc::kTM>
   __device__ __forceinline__ ListItem decode_list(int64_t item) const {
     int lo = 0, hi = K;
     while (hi - lo > 1) {
@@ -50,15 +56,15 @@ struct ListSched {
     const int k = lo;
     const int64_t L = list_off[k + 1] - list_off[k];
     const int64_t M = boff[k + 1] - boff[k];
-    const int64_t nts = cdiv(M, tc::kTM);
+    const int64_t nts = cdiv(M, (int64_t)TS);
     const int64_t local = item - woff[k];
     const int64_t te = local / nts, ts = local % nts;
     ListItem it;
     it.k = k;
     it.e0 = list_off[k] + te * TN;
     it.ne = (int)min((int64_t)TN, L - te * TN);
-    it.s0 = boff[k] + ts * tc::kTM;
-    it.ns = (int)min((int64_t)tc::kTM, M - ts * tc::kTM);
+    it.s0 = boff[k] + ts * TS;
+    it.ns = (int)min((int64_t)TS, M - ts * TS);
     return it;
   }
 };
@@ -258,6 +264,140 @@ struct RescorePolicy : ListSched {
   }
 };
 
+// ---------------------------------------------------------------- slot-column policies
+// Most lists are touched by few query slots of a batch (a few to a few dozen,
+// from the queries whose views share its codeword). For lists of up to 64
+// slots these policies make the list entries the 128 MMA rows (A, TMEM lanes)
+// and the slots the N columns (B), N = TS in {16, 32, 64}, the smallest that
+// holds the list's slots. The small slot tile leaves most of shared memory to
+// the entry tiles, so more of them are in flight from DRAM (5 to 11 stages
+// instead of 3 or 4), and the MMAs shrink with N. Each launch runs the lists
+// of one slot class; lists of more slots keep the slot-row policies above.
+//
+// Epilogue: thread = entry row; it accumulates its TS slot columns, then per
+// slot the warp takes the segmented max over its lanes by run (entries of one
+// shape are consecutive, so a run is a contiguous group of lanes) with five
+// shuffles, and the first lane of each run folds it into the per-(slot, run)
+// table with atomicMax on the order-preserving key. A run split between warps
+// or tiles is merged by the atomics. The rescore writes every run of its
+// items: the candidate sums read the table only at candidate shapes.
+//
+// EB = 1, SPLIT = 1: E4M3 scan (per-slot and per-entry scales, one chunk).
+// EB = 2, SPLIT = 3: FP32-level rescore with two-part BF16 operands, the
+// reduction in kRescChunks chunks summed in FP32 (as RescorePolicy).
+__host__ __device__ constexpr int slot_class(int64_t M) { return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 : 128; }
+
+template <int EB_, int SPLIT_, int TS_>
+struct SlotsPolicy : ListSched {
+  static constexpr int TN = TS_, EB = EB_, SPLIT = SPLIT_;
+  static constexpr bool kResc = SPLIT_ == 3;
+  // the slot-row policies' product order (slot hi x entry lo before slot lo x
+  // entry hi), so a (slot, entry) value does not depend on the list's class
+  static constexpr bool SWAP_CROSS = true;
+  static constexpr int NBUF = kResc ? kRescChunks : (TS_ <= 64 ? 4 : 2);
+  // stage bytes: entries (A) 16 KB per part, slots (B) TS x 128 bytes per part
+  static constexpr int kStage = (kResc ? 2 : 1) * (16384 + TS_ * 128);
+  static constexpr int STAGES = (200 * 1024) / kStage > 12 ? 12 : (200 * 1024) / kStage;
+  static constexpr int kWarpSmem = TS_ * 12;
+  static_assert(TS_ == 16 || TS_ == 32 || TS_ == 64, "slot tile of 16, 32 or 64");
+  static_assert(kResc ? EB_ == 2 : (EB_ == 1 && SPLIT_ == 1), "E4M3 scan or two-part BF16 rescore");
+  SlotInfo si;
+  const int64_t* item_map;  // rescore: [n_items] the kept work items (ascending); scan: null
+  const int64_t* n_items;
+  using Item = ListItem;
+  struct Ctx {
+    int run;
+    float esc;
+    bool valid;
+    float sum[TS_];
+  };
+  __device__ __forceinline__ int64_t total() const { return kResc ? *n_items : total_items(); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    return decode_list<tc::kTM, TS_>(kResc ? item_map[item] : item);
+  }
+  __device__ __forceinline__ int nch() const {
+    if (!kResc) return 1;
+    const int want = (nkb * 12 + 191) / 192;
+    return want < 1 ? 1 : (want > kRescChunks ? kRescChunks : want);
+  }
+  __device__ __forceinline__ int nchunks(const Item&) const { return nch(); }
+  __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
+    br = (int)it.s0;
+    const int n = nch();
+    kb0 = (int)((int64_t)nkb * c / n);
+    kb1 = (int)((int64_t)nkb * (c + 1) / n);
+  }
+  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.e0; }
+  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int, uint8_t* ws) const {
+    int64_t* s_rb = reinterpret_cast<int64_t*>(ws);
+    float* s_qi = reinterpret_cast<float*>(s_rb + TS_);
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < TS_; j += 32) {
+      int64_t rb = 0;
+      float qi = 0.f;
+      if (j < it.ns) {
+        const int64_t s = it.s0 + j;
+        rb = si.runbase[s];
+        qi = si.q_inv[si.slot_view[s]] * (si.slot_scale ? si.slot_scale[s] : 1.f);
+      }
+      s_rb[j] = rb;
+      s_qi[j] = qi;
+    }
+    x.valid = m < it.ne;
+    const int64_t e = it.e0 + m;
+    x.run = x.valid ? si.entry_run[e] : -1 - m;  // rows past the list: a group of their own
+    x.esc = x.valid ? si.scale[e] : 0.f;
+#pragma unroll
+    for (int j = 0; j < TS_; ++j) x.sum[j] = 0.f;
+  }
+  __device__ __forceinline__ void epi_chunk(const Item&, int, uint32_t taddr, Ctx& x, int, uint8_t*) const {
+    if constexpr (TS_ == 16) {
+      uint32_t r[16];
+      tc::tmem_ld16(taddr, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x.sum[j] += __uint_as_float(r[j]);
+    } else {
+#pragma unroll
+      for (int pc = 0; pc < TS_ / 32; ++pc) {
+        uint32_t r[32];
+        tc::tmem_ld32(taddr + pc * 32, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
+      }
+    }
+  }
+  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int, uint8_t* ws) const {
+    const int64_t* s_rb = reinterpret_cast<const int64_t*>(ws);
+    const float* s_qi = reinterpret_cast<const float*>(s_rb + TS_);
+    const int lane = threadIdx.x & 31;
+    // lane + o holds the same run (the lanes between do too): offsets 1, 2, 4, 8, 16
+    unsigned same = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int o = 1 << b;
+      const int r2 = __shfl_down_sync(0xffffffffu, x.run, o);
+      if (lane + o < 32 && r2 == x.run) same |= 1u << b;
+    }
+    const int up = __shfl_up_sync(0xffffffffu, x.run, 1);
+    const bool head = x.valid && (lane == 0 || up != x.run);
+    const int64_t tb = head ? (int64_t)x.run : 0;
+#pragma unroll
+    for (int j = 0; j < TS_; ++j) {
+      if (j < it.ns) {  // warp-uniform
+        float v = x.sum[j] * s_qi[j] * x.esc;  // the slot-row policies' rounding order
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const float y = __shfl_down_sync(0xffffffffu, v, 1 << b);
+          if (same & (1u << b)) v = fmaxf(v, y);
+        }
+        if (head) atomicMax(si.table + s_rb[j] + tb, f2key(v));
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------- fused scan + rescore policy
 // For a BF16 store that is also the hi part of the two-part rescore store:
 // one pass computes, per (slot, entry), hi*hi in two accumulators (first and
@@ -394,6 +534,7 @@ __global__ __launch_bounds__(256) void k_slot_fp8(const float* __restrict__ q, c
 //   [3] items, [4] kept items, [5] candidate (slot, entry) pairs, [6] candidate
 //   rows (entries whose shape is a candidate of some slot of their list, each
 //   list's entries counted once, by its first slot tile), [7] rows of kept items.
+template <int TS>
 __global__ __launch_bounds__(256) void k_resc_flags(const ListSched ls, const int32_t* __restrict__ slot_view,
                                                     const int32_t* __restrict__ vquery,
                                                     const int32_t* __restrict__ entry_run,
@@ -408,7 +549,7 @@ __global__ __launch_bounds__(256) void k_resc_flags(const ListSched ls, const in
     if (lane == 0) flags[item] = 0;
     return;
   }
-  const ListItem it = ls.decode_list<kRescTN>(item);
+  const ListItem it = ls.decode_list<kRescTN, TS>(item);
   bool hit = false;
   for (int m = 0; m < it.ns && !hit; ++m) {
     const int32_t* cq = cand + (int64_t)vquery[slot_view[it.s0 + m]] * R;
@@ -457,8 +598,10 @@ __global__ void k_compact_items(const int64_t* __restrict__ flags, const int64_t
   if (i == upper - 1) *n_items = pos[i] + flags[i];
 }
 
+// ts_class > 0: only the lists of that slot class (slot tiles of ts_class slots);
+// otherwise every touched list, slot tiles of 128
 __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t* __restrict__ list_off, int K,
-                                int tn, int64_t* __restrict__ wcnt) {
+                                int tn, int ts_class, int64_t* __restrict__ wcnt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > K) return;
   if (k == K) {
@@ -467,15 +610,17 @@ __global__ void k_work_count_tc(const int64_t* __restrict__ boff, const int64_t*
   }
   const int64_t M = boff[k + 1] - boff[k];
   const int64_t L = list_off[k + 1] - list_off[k];
-  wcnt[k] = (M > 0 && L > 0) ? cdiv(L, tn) * cdiv(M, tc::kTM) : 0;
+  const int ts = ts_class > 0 ? ts_class : tc::kTM;
+  const bool mine = ts_class <= 0 || slot_class(M) == ts_class;
+  wcnt[k] = (M > 0 && L > 0 && mine) ? cdiv(L, (int64_t)tn) * cdiv(M, (int64_t)ts) : 0;
 }
 
 // work items (list, entry tile of tn entries, slot tile) of the batch's touched lists
-ListSched list_sched(const Index& ix, const FifPlan& P, int tn, Scratch& sc, cudaStream_t s) {
+ListSched list_sched(const Index& ix, const FifPlan& P, int tn, Scratch& sc, cudaStream_t s, int ts_class = 0) {
   const int K = ix.prm.n_codewords;
   int64_t* wcnt = sc.get<int64_t>(K + 1);
   int64_t* woff = sc.get<int64_t>(K + 1);
-  k_work_count_tc<<<(unsigned)cdiv(K + 1, 256), 256, 0, s>>>(P.boff, ix.list_off, K, tn, wcnt);
+  k_work_count_tc<<<(unsigned)cdiv(K + 1, 256), 256, 0, s>>>(P.boff, ix.list_off, K, tn, ts_class, wcnt);
   GIFT_LAUNCHED("k_work_count_tc");
   scan_exclusive_i64(wcnt, woff, K + 1, sc, s);
   ListSched ls;
@@ -487,6 +632,59 @@ ListSched list_sched(const Index& ix, const FifPlan& P, int tn, Scratch& sc, cud
   return ls;
 }
 
+// E4M3 scan of the lists of one slot class
+template <int TS>
+void scan_fp8_class(const Index& ix, const FifPlan& P, const SlotInfo& si, const CUtensorMap& tA, const void* q8,
+                    int64_t qrows, Scratch& sc, cudaStream_t s, int grid) {
+  SlotsPolicy<1, 1, TS> pol;
+  static_cast<ListSched&>(pol) = list_sched(ix, P, tc::kTM, sc, s, TS);
+  pol.nkb = (int)cdiv((int64_t)ix.prm.dim, (int64_t)128);
+  pol.si = si;
+  pol.item_map = nullptr;
+  pol.n_items = nullptr;
+  const CUtensorMap tB = make_tmap_u8(q8, qrows, ix.prm.dim, TS);
+  tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
+}
+
+// the rescore work of one slot class: its items that hold a candidate run
+// (slot classes of up to 64 slots: slot columns; 128: slot rows, RescorePolicy)
+template <int TS>
+struct RescoreClass {
+  using Pol = std::conditional_t<TS == 128, RescorePolicy, SlotsPolicy<2, 3, (TS < 128 ? TS : 64)>>;
+  Pol pol;
+  void plan(const Index& ix, const FifPlan& P, const SlotInfo& si, const int32_t* cand_sorted, int R,
+            int64_t upper, int64_t* flags, int64_t* pos, Scratch& sc, cudaStream_t s) {
+    ListSched ls = list_sched(ix, P, kRescTN, sc, s, TS);
+    ls.nkb = (int)cdiv((int64_t)ix.prm.dim, (int64_t)64);
+    static_cast<ListSched&>(pol) = ls;
+    pol.si = si;
+    if constexpr (TS == 128) {
+      pol.cand = cand_sorted;
+      pol.R = R;
+    }
+    int64_t* item_map = sc.get<int64_t>(upper);
+    int64_t* n_items = sc.get<int64_t>(1);
+    k_resc_flags<TS><<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run,
+                                                             ix.list_shape, cand_sorted, R, upper, flags, P.stats);
+    GIFT_LAUNCHED("k_resc_flags");
+    scan_exclusive_i64(flags, pos, upper, sc, s);
+    k_compact_items<<<(unsigned)cdiv(upper, 256), 256, 0, s>>>(flags, pos, upper, item_map, n_items);
+    GIFT_LAUNCHED("k_compact_items");
+    pol.item_map = item_map;
+    pol.n_items = n_items;
+  }
+  // tE, tE2: the entry rows (hi, lo), 128-row boxes
+  void run(const Index& ix, const CUtensorMap& tE, const CUtensorMap& tE2, const void* qhi, const void* qlo,
+           int64_t qrows, int grid, cudaStream_t s) {
+    const CUtensorMap tS = make_tmap_bf16(qhi, qrows, ix.prm.dim, TS);
+    const CUtensorMap tS2 = make_tmap_bf16(qlo, qrows, ix.prm.dim, TS);
+    if constexpr (TS == 128)
+      tc::launch_engine(tS, tE, tS2, tE2, pol, ix.d_err, grid, s);  // slots are the MMA rows
+    else
+      tc::launch_engine(tE, tS, tE2, tS2, pol, ix.d_err, grid, s);
+  }
+};
+
 }  // namespace
 
 void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_sorted, int R, Scratch& sc,
@@ -495,14 +693,14 @@ void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_so
   const ListSched ls = list_sched(ix, P, kRescTN, sc, s);
   const int64_t upper = std::max<int64_t>(P.upper_items, 1);
   int64_t* flags = sc.get<int64_t>(upper);
-  k_resc_flags<<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run, ix.list_shape,
+  k_resc_flags<tc::kTM><<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run, ix.list_shape,
                                                         cand_sorted, R, upper, flags, P.stats);
   GIFT_LAUNCHED("k_resc_flags");
 }
 
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
                  int R, Scratch& sc, cudaStream_t s, uint32_t* table32) {
-  const int K = ix.prm.n_codewords, D = ix.prm.dim;
+  const int D = ix.prm.dim;
   const int64_t ns = P.nslots;
   if (ns <= 0) return;
   const bool fused = table32 != nullptr;
@@ -533,9 +731,12 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     P.slot_hi = qhi;
     P.slot_lo = qlo;
   }
-  const int tn = rescore ? kRescTN : kScanTN;
-  ListSched ls = list_sched(ix, P, tn, sc, s);
-  ls.nkb = (int)cdiv(D, fp8 ? 128 : 64);
+  // the BF16 scan and the fused pass schedule 128 slots x tn entries per item
+  auto sched = [&](int tn) {
+    ListSched ls = list_sched(ix, P, tn, sc, s);
+    ls.nkb = (int)cdiv(D, 64);
+    return ls;
+  };
   SlotInfo si;
   si.runbase = P.runbase;
   si.slot_view = P.slot_view;
@@ -548,17 +749,26 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   si.table = table;
   const int grid = device_sm_count();
   if (fp8) {
-    ScanPolicy<1> pol;
-    static_cast<ListSched&>(pol) = ls;
-    pol.si = si;
-    const CUtensorMap tA = make_tmap_u8(q8, qrows, D, tc::kTM);
-    const CUtensorMap tB = make_tmap_u8(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy<1>::TN);
+    // lists of up to 64 slots: list entries are the MMA rows, query slots the columns,
+    // one launch per slot class
+    const CUtensorMap tA = make_tmap_u8(ix.list_feat, ix.list_rows_alloc, D, tc::kTM);
     if (P.kc) P.kc->begin(1);
-    tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
+    scan_fp8_class<16>(ix, P, si, tA, q8, qrows, sc, s, grid);
+    scan_fp8_class<32>(ix, P, si, tA, q8, qrows, sc, s, grid);
+    scan_fp8_class<64>(ix, P, si, tA, q8, qrows, sc, s, grid);
+    {  // lists of more than 64 slots: slots are the MMA rows, 256 entries per item
+      ScanPolicy<1> pol;
+      static_cast<ListSched&>(pol) = list_sched(ix, P, kScanTN, sc, s, 128);
+      pol.nkb = (int)cdiv(D, 128);
+      pol.si = si;
+      const CUtensorMap tS = make_tmap_u8(q8, qrows, D, tc::kTM);
+      const CUtensorMap tE = make_tmap_u8(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy<1>::TN);
+      tc::launch_engine(tS, tE, tS, tE, pol, ix.d_err, grid, s);
+    }
     if (P.kc) P.kc->end(1);
   } else if (!rescore) {
     ScanPolicy<2> pol;
-    static_cast<ListSched&>(pol) = ls;
+    static_cast<ListSched&>(pol) = sched(kScanTN);
     pol.si = si;
     const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
     const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, ScanPolicy<2>::TN);
@@ -567,7 +777,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     if (P.kc) P.kc->end(1);
   } else if (fused) {
     FusedPolicy pol;
-    static_cast<ListSched&>(pol) = ls;
+    static_cast<ListSched&>(pol) = sched(kRescTN);
     pol.si = si;
     pol.table32 = table32;
     const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
@@ -581,32 +791,27 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     GIFT_REQUIRE(ix.list_lo != nullptr, "rescore needs the two-part BF16 list store");
     // BF16 index: the store itself is the hi part; FP8 index: a separate BF16 hi store
     const void* bhi = ix.list_hi ? ix.list_hi : ix.list_feat;
-    RescorePolicy pol;
-    static_cast<ListSched&>(pol) = ls;
-    pol.si = si;
-    pol.si.scale = ix.list_hi ? ix.list_scale_hi : ix.list_scale;
-    pol.cand = cand_sorted;
-    pol.R = R;
-    // the work items that hold a candidate run, in their original order
+    SlotInfo sr = si;
+    sr.scale = ix.list_hi ? ix.list_scale_hi : ix.list_scale;
+    // the work items that hold a candidate run, per slot class, in their original order
     const int64_t upper = std::max<int64_t>(P.upper_items, 1);
     int64_t* flags = sc.get<int64_t>(upper);
     int64_t* pos = sc.get<int64_t>(upper);
-    int64_t* item_map = sc.get<int64_t>(upper);
-    int64_t* n_items = sc.get<int64_t>(1);
-    k_resc_flags<<<(unsigned)cdiv(upper, 8), 256, 0, s>>>(ls, P.slot_view, P.vquery, ix.entry_run, ix.list_shape,
-                                                          cand_sorted, R, upper, flags, P.stats);
-    GIFT_LAUNCHED("k_resc_flags");
-    scan_exclusive_i64(flags, pos, upper, sc, s);
-    k_compact_items<<<(unsigned)cdiv(upper, 256), 256, 0, s>>>(flags, pos, upper, item_map, n_items);
-    GIFT_LAUNCHED("k_compact_items");
-    pol.item_map = item_map;
-    pol.n_items = n_items;
-    const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
-    const CUtensorMap tB = make_tmap_bf16(bhi, ix.list_rows_alloc, D, RescorePolicy::TN);
-    const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
-    const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, RescorePolicy::TN);
+    RescoreClass<16> c16;
+    RescoreClass<32> c32;
+    RescoreClass<64> c64;
+    RescoreClass<128> c128;
+    c16.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
+    c32.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
+    c64.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
+    c128.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
+    const CUtensorMap tA = make_tmap_bf16(bhi, ix.list_rows_alloc, D, tc::kTM);
+    const CUtensorMap tA2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, tc::kTM);
     if (P.kc) P.kc->begin(2);
-    tc::launch_engine(tA, tB, tA2, tB2, pol, ix.d_err, grid, s);
+    c16.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
+    c32.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
+    c64.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
+    c128.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
     if (P.kc) P.kc->end(2);
   }
 }

@@ -107,17 +107,20 @@ __global__ __launch_bounds__(kT) void k_topk(const float* __restrict__ scores,
     for (int byte = nbytes - 1; byte >= 0; --byte) {
       if (tid < 256) hist[tid] = 0;
       __syncthreads();
-      // keys of close scores share their high bytes, so most of a warp's keys fall in one
-      // bin: one atomic per distinct bin per warp (lanes grouped by __match_any_sync)
-      for (int64_t c0 = 0; c0 < n; c0 += kT) {
-        const int64_t i = c0 + tid;
-        int bin = -1;
-        if (i < n) {
-          const unsigned long long key = get_key<F32>(sr, kr, i);
-          if ((key & mask) == prefix) bin = (int)((key >> (8 * byte)) & 255);
+      if (byte == nbytes - 1) {
+        // the top byte (sign and high exponent bits) is the same for nearly every key: one
+        // atomic per distinct bin per warp (lanes grouped by __match_any_sync)
+        for (int64_t c0 = 0; c0 < n; c0 += kT) {
+          const int64_t i = c0 + tid;
+          const int bin = i < n ? (int)((get_key<F32>(sr, kr, i) >> (8 * byte)) & 255) : -1;
+          const unsigned peers = __match_any_sync(kFull, bin);
+          if (bin >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
         }
-        const unsigned peers = __match_any_sync(kFull, bin);
-        if (bin >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+      } else {
+        for (int64_t i = tid; i < n; i += kT) {
+          const unsigned long long key = get_key<F32>(sr, kr, i);
+          if ((key & mask) == prefix) atomicAdd(&hist[(key >> (8 * byte)) & 255], 1);
+        }
       }
       __syncthreads();
       if (tid == 0) {

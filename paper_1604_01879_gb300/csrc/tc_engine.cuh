@@ -71,6 +71,14 @@ struct gen_warps_of : std::integral_constant<int, 1> {};
 template <class P>
 struct gen_warps_of<P, std::void_t<decltype(P::GEN_WARPS)>> : std::integral_constant<int, P::GEN_WARPS> {};
 
+// SWAP_CROSS = true: with SPLIT = 3 the two cross products of a k-block are
+// issued as lo(A) * hi(B) before hi(A) * lo(B), so that an engine run with the
+// operand roles exchanged accumulates the same products in the same order
+template <class P, class = void>
+struct swap_cross_of : std::false_type {};
+template <class P>
+struct swap_cross_of<P, std::void_t<decltype(P::SWAP_CROSS)>> : std::integral_constant<bool, P::SWAP_CROSS> {};
+
 template <class P, class = void>
 struct accs_of : std::integral_constant<int, 1> {};
 template <class P>
@@ -388,6 +396,11 @@ __global__ void __launch_bounds__(engine_threads<P>::value, 1)
                   continue;
                 }
                 mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, acc_in);
+                if (swap_cross_of<P>::value && P::SPLIT == 3) {
+                  mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
+                  mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
+                  continue;
+                }
                 if (P::SPLIT == 3) mma_f16(d, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb2 + kk * 32), kIdesc, 1u);
                 if (P::SPLIT >= 2) mma_f16(d, sdesc_sw128(sa2 + kk * 32), sdesc_sw128(sb + kk * 32), kIdesc, 1u);
               }

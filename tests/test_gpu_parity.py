@@ -198,6 +198,37 @@ def test_reduced_precision_store_without_rescore(gpu_lib, storage, tol):
     ix.close()
 
 
+def test_fp8_lists_of_every_slot_class(gpu_lib):
+    """E4M3 scan and FP32-level rescore with query MA = 2 where the touched lists hold from 16 to
+    386 query slots: lists of up to 64 slots run with entries as the MMA rows (slot tiles of 16,
+    32, 64), larger ones with slots as the rows, in one or several slot tiles of 128."""
+    import torch
+    N, Nv, D, C, K = 96, 16, 128, 4, 12
+    X, cb, _, _, dbc, _ = _case(N, Nv, D, C, K, 1, (16,), 151)
+    picks = [c + C * i for c, n in enumerate((24, 12, 5, 1)) for i in range(n)]  # queries per class
+    Q = np.concatenate([X[p] for p in picks])
+    qoff = np.arange(len(picks) + 1, dtype=np.int32) * Nv
+    qc = O.quantize(Q, cb, 2)
+    M = np.bincount(qc.ravel(), minlength=K)
+    M = M[M > 0]
+    assert (M <= 16).any() and ((M > 16) & (M <= 32)).any() and ((M > 32) & (M <= 64)).any()
+    assert ((M > 64) & (M <= 128)).any() and (M > 256).any()
+    ref = O.fif_scores(Q, qoff, qc, X, dbc)
+    Qd = torch.from_numpy(Q).cuda()
+    plain = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="fp8", query_ma=2, keep_exact=False)
+    ids, sc = plain.query(Qd, qoff, mode="fif", topk=N)
+    for b in range(len(picks)):
+        i = ids[b].cpu().numpy()
+        assert sorted(i.tolist()) == list(range(N))
+        assert np.abs(sc[b].cpu().numpy() - ref[b, i]).max() < 6e-2
+    plain.close()
+    ix = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="fp8", query_ma=2, rescore_r=64, keep_exact=False)
+    ids, sc = ix.query(Qd, qoff, mode="fif", topk=20)
+    for b in range(len(picks)):
+        assert_topk(ids[b].cpu().numpy(), sc[b].cpu().numpy(), ref[b], 20)
+    ix.close()
+
+
 def test_database_smaller_than_k(gpu_lib):
     import torch
     N, Nv, D, C, K = 5, 8, 16, 2, 3
@@ -292,6 +323,30 @@ def test_rerank_matches_oracle(c1):
         assert rtol <= 1e-5, (band.lo, band.hi)
         ref = np.array([O.contextual(Fq, F_db[p]) for p in range(N)])
         assert_topk(rid[b], rsp[b], ref, 10, rtol=rtol, atol=atol)
+
+
+def test_rerank_whole_database_order(c1):
+    """topk = N: every shape once, by S' (Eq. 8) desc, then the F-IF score S desc for candidates,
+    then ascending id for the shapes neither the S-IF walk nor the candidate list reaches."""
+    import torch
+    Q, qoff = c1["Q"], c1["qoff"]
+    k1, N = c1["cfg"].sif_k1, c1["X"].shape[0]
+    ids, sc = c1["ix"].query(torch.from_numpy(Q).cuda(), qoff, mode="fif", topk=30)
+    rid, rsp = c1["ix"].rerank(ids, sc, k1=k1, topk=N)
+    ids, sc, rid, rsp = (t.cpu().numpy() for t in (ids, sc, rid, rsp))
+    for b in range(len(qoff) - 1):
+        assert sorted(rid[b].tolist()) == list(range(N))
+        assert np.all(np.diff(rsp[b]) <= 0)
+        zero = rsp[b] == 0
+        assert zero.any() and np.all(zero[np.argmax(zero):])  # the S' = 0 shapes close the row
+        z = rid[b][zero]
+        cand = dict(zip(ids[b].tolist(), sc[b].tolist()))
+        is_c = np.array([p in cand for p in z])
+        n_c = int(is_c.sum())
+        assert is_c[:n_c].all() and not is_c[n_c:].any()  # candidates before unreached shapes
+        s_c = np.array([cand[p] for p in z[:n_c]])
+        assert np.all(np.diff(s_c) <= 0)
+        assert np.all(np.diff(z[n_c:]) > 0)
 
 
 @pytest.mark.parametrize("D", [256, 80])
