@@ -400,14 +400,14 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   P.kc = &tm.kc;
   fif_plan(ix, P, sc, s);
   uint32_t* table = sc.get<uint32_t>(P.table_upper);
-  GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
+  fif_zero_table(P, table, s);
   // a BF16 store that is the hi part of the rescore rows: one fused pass gives
   // the BF16 maxima (candidate selection) and the FP32-level maxima (rescore)
   const bool fused = R > 0 && fused_scan_ok(ix);
   uint32_t* table32 = nullptr;
   if (fused) {
     table32 = sc.get<uint32_t>(P.table_upper);
-    GIFT_CUDA(cudaMemsetAsync(table32, 0, P.table_upper * 4, s));
+    fif_zero_table(P, table32, s);
   }
 
   tm.mark(ST_SCAN);
@@ -436,7 +436,7 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   tm.mark(ST_RESCORE);
   if (fused) fif_rescore_stats(ix, P, cand_sorted, Rr, sc, s);  // timed calls only
   if (!fused) {
-    GIFT_CUDA(cudaMemsetAsync(table, 0, P.table_upper * 4, s));
+    fif_zero_table(P, table, s);
     if (ix.list_lo)
       fif_scan_tc(ix, P, table, true, cand_sorted, Rr, sc, s);
     else

@@ -24,7 +24,7 @@ struct FifPlan {
   int64_t* boff = nullptr;        // [K+1] slots of codeword k
   int32_t* slot_view = nullptr;   // [nslots]
   int32_t* view_slot = nullptr;   // [nv * ma]
-  int64_t* runbase = nullptr;     // [nslots] first table cell of each slot
+  int64_t* runbase = nullptr;     // [nslots + 1] first table cell of each slot; [nslots] = cells in use
   int64_t* woff = nullptr;        // [K+1] scan work items per codeword (exclusive)
   int64_t upper_items = 0;        // bound on the number of scan work items
   int64_t table_upper = 0;        // bound on the table cells
@@ -35,6 +35,9 @@ struct FifPlan {
 };
 
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s);
+// clear the table cells the batch uses (runbase[nslots] of them; the table is
+// allocated for table_upper)
+void fif_zero_table(const FifPlan& P, uint32_t* table, cudaStream_t s);
 void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
               const int32_t* cand_sorted, int R, cudaStream_t s);
 // tcgen05 scan of a BF16 or E4M3 store (rescore: two-part BF16, candidates only;

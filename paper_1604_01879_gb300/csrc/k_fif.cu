@@ -35,6 +35,7 @@ __global__ void k_slot_setup(const int32_t* __restrict__ perm, int64_t nslots, i
                              int32_t* __restrict__ slot_view, int32_t* __restrict__ view_slot,
                              int64_t* __restrict__ run_cnt) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == nslots) run_cnt[s] = 0;  // so that the scan's last element is the table size
   if (s >= nslots) return;
   const int32_t item = perm[s];
   slot_view[s] = item / ma;
@@ -478,7 +479,24 @@ __global__ __launch_bounds__(kCombineT) void k_fif_combine_ma_cand(const Combine
     if (acc[i] != 0ull) atomicAdd(a.acc + (int64_t)q * R + i, acc[i]);
 }
 
+// zero the first *n cells (n read on the device)
+__global__ void k_zero_cells(uint32_t* __restrict__ t, const int64_t* __restrict__ n_dev) {
+  const int64_t n = *n_dev;
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint4* t4 = reinterpret_cast<uint4*>(t);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+    t4[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) t[i] = 0u;
+}
+
 }  // namespace
+
+void fif_zero_table(const FifPlan& P, uint32_t* table, cudaStream_t s) {
+  if (P.nslots <= 0) return;
+  k_zero_cells<<<1216, 256, 0, s>>>(table, P.runbase + P.nslots);  // 8 blocks per SM of a GB300
+  GIFT_LAUNCHED("k_zero_cells");
+}
 
 void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s) {
   const int K = ix.prm.n_codewords;
@@ -492,11 +510,11 @@ void fif_plan(const Index& ix, FifPlan& P, Scratch& sc, cudaStream_t s) {
   P.slot_view = sc.get<int32_t>(n);
   P.view_slot = sc.get<int32_t>(n);
   int64_t* run_cnt = sc.get<int64_t>(n + 1);
-  k_slot_setup<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(perm, n, P.ma, P.skeys, ix.nruns, P.slot_view,
-                                                        P.view_slot, run_cnt);
+  k_slot_setup<<<(unsigned)cdiv(n + 1, 256), 256, 0, s>>>(perm, n, P.ma, P.skeys, ix.nruns, P.slot_view,
+                                                            P.view_slot, run_cnt);
   GIFT_LAUNCHED("k_slot_setup");
   P.runbase = sc.get<int64_t>(n + 1);
-  scan_exclusive_i64(run_cnt, P.runbase, n, sc, s);
+  scan_exclusive_i64(run_cnt, P.runbase, n + 1, sc, s);  // runbase[n] = table cells in use
   P.table_upper = n * (int64_t)std::max(1, ix.max_runs);
   int64_t* wcnt = sc.get<int64_t>(K + 1);
   P.woff = sc.get<int64_t>(K + 1);

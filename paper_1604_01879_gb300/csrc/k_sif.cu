@@ -127,6 +127,93 @@ __global__ void k_rerank_keys(const unsigned long long* __restrict__ num,
   keys[idx] = ((unsigned long long)f2key(sp) << 32) | (unsigned long long)f2key(Srow[idx]);
 }
 
+// The shapes a query reaches -- through the S-IF walk (numerator > 0) or as a
+// candidate (finite S) -- in ascending id order, with their ranking keys (as
+// k_rerank_keys); every other shape has the same key, S' = 0 and S = -inf,
+// below all of these, so the top-k of the dense row is the top-k of this
+// compact row, followed (when fewer than min(topk, N) shapes are reached) by the
+// unreached shapes in ascending id order. One block per query, rows of `cap`
+// (padding: key 0, id -1).
+constexpr int kCompactT = 1024;
+__global__ __launch_bounds__(kCompactT) void k_rerank_compact(
+    const unsigned long long* __restrict__ num, const unsigned long long* __restrict__ fq_norm,
+    const unsigned long long* __restrict__ card, const float* __restrict__ Srow, int32_t N, int64_t cap, int need,
+    int32_t* __restrict__ ids, unsigned long long* __restrict__ keys) {
+  __shared__ int wtot[kCompactT / 32];
+  __shared__ int s_count;
+  const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const unsigned long long* nr = num + (int64_t)b * N;
+  const float* sr = Srow + (int64_t)b * N;
+  int32_t* oid = ids + (int64_t)b * cap;
+  unsigned long long* okey = keys + (int64_t)b * cap;
+  const unsigned long long fq = fq_norm[b];
+  if (t == 0) s_count = 0;
+  __syncthreads();
+  // pass 0: the reached shapes; pass 1 (only when too few): the first unreached ones
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && s_count >= need) break;  // block-uniform (read after a barrier)
+    for (int c0 = 0; c0 < N; c0 += kCompactT) {
+      const int p = c0 + t;
+      bool in = false;
+      unsigned long long key = 0;
+      if (p < N) {
+        const unsigned long long nm = nr[p];
+        const float sv = sr[p];
+        const bool reached = nm != 0ull || sv != -INFINITY;
+        in = pass == 0 ? reached : !reached;
+        if (in) {
+          float sp = 0.f;
+          if (nm > 0) sp = __fdiv_rn(__ull2float_rn(nm), __ull2float_rn(fq + card[p] - nm));
+          key = ((unsigned long long)f2key(sp) << 32) | (unsigned long long)f2key(sv);
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (lane == 0) wtot[w] = __popc(m);
+      __syncthreads();
+      if (w == 0) {  // exclusive scan of the warp totals
+        const int x = wtot[lane];
+        int y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int z = __shfl_up_sync(0xffffffffu, y, o);
+          if (lane >= o) y += z;
+        }
+        wtot[lane] = y - x;
+      }
+      __syncthreads();
+      const int base = s_count;
+      const int pos = base + wtot[w] + __popc(m & ((1u << lane) - 1u));
+      const int limit = pass == 0 ? (int)cap : need;
+      if (in && pos < limit) {
+        oid[pos] = p;
+        okey[pos] = key;
+      }
+      __syncthreads();
+      if (t == kCompactT - 1) s_count = min(limit, pos + (in ? 1 : 0));
+      __syncthreads();
+      if (pass == 1 && s_count >= need) break;  // block-uniform
+    }
+    __syncthreads();
+  }
+  for (int64_t j = s_count + t; j < cap; j += kCompactT) {
+    oid[j] = -1;
+    okey[j] = 0ull;
+  }
+}
+
+// output of the selection over compact rows: positions -> shape ids, keys -> S'
+__global__ void k_rerank_out(const int32_t* __restrict__ pos, const unsigned long long* __restrict__ kout,
+                             const int32_t* __restrict__ ids, int64_t cap, int32_t B, int32_t topk,
+                             int32_t* __restrict__ out_ids, float* __restrict__ out_sprime) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * topk) return;
+  const int64_t b = i / topk;
+  const int32_t q = pos[i];
+  const bool ok = q >= 0 && kout[i] != 0ull;
+  out_ids[i] = ok ? ids[b * cap + q] : -1;
+  out_sprime[i] = ok ? key2f((uint32_t)(kout[i] >> 32)) : -INFINITY;
+}
+
 __global__ void k_keys_to_sprime(const unsigned long long* __restrict__ keys, int64_t n,
                                  float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,16 +565,23 @@ void sif_rerank(const Index& ix, const int32_t* cand_ids, const float* cand_scor
   k_rerank_walk<<<dim3((unsigned)B, (unsigned)k1), 128, 0, s>>>(cand_ids, cand_scores, n_cand, k1, N, ix.sif_off,
                                                              ix.sif_ids, ix.sif_mem, num);
   GIFT_LAUNCHED("k_rerank_walk");
-  unsigned long long* keys = sc.get<unsigned long long>(BN);
-  k_rerank_keys<<<(unsigned)cdiv(BN, 256), 256, 0, s>>>(num, fqn,
-                                                          reinterpret_cast<const unsigned long long*>(ix.sif_card),
-                                                          Srow, B, N, keys);
-  GIFT_LAUNCHED("k_rerank_keys");
+  // a query reaches at most n_cand candidates and k1 S-IF entries of at most
+  // max_sif_entry shapes: the selection runs over those, not over all N
+  const int need = std::min(topk, N);
+  const int64_t cap = std::min<int64_t>(
+      N, std::max<int64_t>(need, (int64_t)n_cand + (int64_t)k1 * std::max(1, ix.max_sif_entry)));
+  int32_t* cids = sc.get<int32_t>((size_t)B * cap);
+  unsigned long long* keys = sc.get<unsigned long long>((size_t)B * cap);
+  k_rerank_compact<<<(unsigned)B, kCompactT, 0, s>>>(num, fqn, reinterpret_cast<const unsigned long long*>(ix.sif_card),
+                                                      Srow, N, cap, need, cids, keys);
+  GIFT_LAUNCHED("k_rerank_compact");
+  int32_t* pos = sc.get<int32_t>((size_t)B * topk);
   unsigned long long* kout = sc.get<unsigned long long>((int64_t)B * topk);
-  topk_rows_u64(reinterpret_cast<const uint64_t*>(keys), B, N, topk, out_ids,
-                reinterpret_cast<uint64_t*>(kout), sc, s);
-  k_keys_to_sprime<<<(unsigned)cdiv((int64_t)B * topk, 256), 256, 0, s>>>(kout, (int64_t)B * topk, out_sprime);
-  GIFT_LAUNCHED("k_keys_to_sprime");
+  topk_rows_u64(reinterpret_cast<const uint64_t*>(keys), B, cap, topk, pos, reinterpret_cast<uint64_t*>(kout), sc,
+                s);
+  k_rerank_out<<<(unsigned)cdiv((int64_t)B * topk, 256), 256, 0, s>>>(pos, kout, cids, cap, B, topk, out_ids,
+                                                                     out_sprime);
+  GIFT_LAUNCHED("k_rerank_out");
 }
 
 namespace {
