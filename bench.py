@@ -226,18 +226,27 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
     # a BF16 store with its two-part rows runs scan and rescore as one fused pass
     # (three products over every touched pair, reported as the rescore kernel)
     fused = cfg.storage == "bf16" and st["scan_kernel_ms"] <= 0 and st["rescore_kernel_ms"] > 0
-    resc_name = "tc_engine<FusedPolicy>" if fused else "tc_engine<RescorePolicy>"
+    resc_name = "fused scan + rescore" if fused else "rescore"
+    # the launches behind each timed role (lists of up to 64 query slots run with the
+    # entries as MMA rows, one launch per slot tile of 16, 32 or 64)
+    classes = ["16", "32", "64"]
+    launches = {
+        "scan": (["tc_engine<ScanPolicy<1>>"] + [f"tc_engine<SlotsPolicy<1,1,{c}>>" for c in classes]
+                 if cfg.storage == "fp8" else ["tc_engine<ScanPolicy<2>>"]),
+        "rescore": ["tc_engine<RescorePolicy>"] + [f"tc_engine<SlotsPolicy<2,3,{c}>>" for c in classes],
+        "fused scan + rescore": ["tc_engine<FusedPolicy>"],
+        "quantiser": ["tc_engine<AssignPolicy>"],
+    }
     resc_flops, resc_bytes = 6.0 * scan_pairs * D, rescore_bytes
     if cand and not fused:
         # the rescore runs the work items holding candidate runs; its work is the
         # candidates' (slot, entry) pairs and the candidate rows, each read once
         resc_flops, resc_bytes = 6.0 * cand["cand_pairs"] * D, cand["cand_rows"] * (4.0 * D + 12)
     kernels = {
-        "tc_engine<ScanPolicy>": (st["scan_kernel_ms"], 2.0 * scan_pairs * D, scan_bytes, ["k_scan_tc.cu"],
-                                  scan_peak),
+        "scan": (st["scan_kernel_ms"], 2.0 * scan_pairs * D, scan_bytes, ["k_scan_tc.cu"], scan_peak),
         resc_name: (st["rescore_kernel_ms"], resc_flops, resc_bytes, ["k_scan_tc.cu"], bf16_peak),
-        "tc_engine<AssignPolicy>": (st["assign_kernel_ms"], 6.0 * assign_rows * cfg.n_codewords * D,
-                                    assign_rows * D * 4 + cfg.n_codewords * D * 4, ["k_assign.cu"], bf16_peak),
+        "quantiser": (st["assign_kernel_ms"], 6.0 * assign_rows * cfg.n_codewords * D,
+                      assign_rows * D * 4 + cfg.n_codewords * D * 4, ["k_assign.cu"], bf16_peak),
     }
     # each kernel against both roofs; its bound is the roof it is closer to
     table = {}
@@ -252,6 +261,7 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
             else:
                 table[name] = {"ms": ms, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                                "frac": t_frac, "hbm_frac": h_frac}
+            table[name]["launches"] = launches[name]
     if not table:  # no engine kernel ran (FP32 store scanned on the CUDA cores, no tensor-core quantiser)
         return None
     dom = max(table, key=lambda k: table[k]["ms"])
@@ -272,9 +282,9 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
         psrc = f"{peak_src} bf16_tflops (burst)" + (" x 2 for E4M3" if dt["peak"] != bf16_peak else "")
         work = ("useful MMA FLOPs on unpadded pairs; the rescore (or fused scan + rescore) and quantiser run "
                 "three BF16 products per FP32-accurate product")
-    if dom == "tc_engine<RescorePolicy>" and cand:
+    if dom == "rescore" and cand:
         work = "algorithmic bytes: the candidate rows (two-part BF16 row + id + scale) of the touched lists, read once"
-    out = {"kernel": dom, "bound": dt["bound"], "achieved": dt["achieved"], "peak": dt["peak"],
+    out = {"kernel": dom, "launches": dt["launches"], "bound": dt["bound"], "achieved": dt["achieved"], "peak": dt["peak"],
            "unit": dt["unit"], "frac": dt["frac"], "traffic": traffic,
            "traffic_source": (f"ncu dram__bytes_read + write on {capture}: {per_unit:.4g} B per {unit}, x {units:.4g}"
                               if traffic is not None else None),
@@ -499,8 +509,10 @@ def measure_workload(cfg, args, gift, torch, dev, rank, world, codebook=None, se
     if args.profile:
         # one more step, timed by the library, outside the captured range: the work
         # counters that scale an ncu capture of these launches to other workloads
+        # (the batch of the first timed step; a capture of one step, or of a
+        # workload with a single batch, matches them exactly)
         ix.set_timing(True)
-        st_q, _ = step(0, timing=True)
+        st_q, _ = step(args.warmup, timing=True)
         ix.set_timing(False)
         eb = 1 if cfg.storage == "fp8" else (2 if cfg.storage == "bf16" else 4)
         counters = {k: st_q[k] for k in ("scan_bytes", "rescore_bytes", "scan_pairs", "assign_rows", "rescore_items",
@@ -733,6 +745,8 @@ def main():
     ap.add_argument("--diff-shapes", type=int, default=None, help="override its database shapes (small ncu case)")
     ap.add_argument("--diff-queries", type=int, default=None, help="override its query shapes (small ncu case)")
     ap.add_argument("--rescore", type=int, default=None, help="override the config's rescore depth R")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="override the config's queries per call (profiling cases of the timed workload's list mix)")
     ap.add_argument("--oracle-queries", type=int, default=8, help="sampled queries for recall (large configs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.profile else args.warmup
@@ -743,6 +757,9 @@ def main():
 
     from synth import CONFIGS
     cfg = CONFIGS[args.config]
+    if args.batch:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, batch=int(args.batch))
     if args.impl == "reference":
         reference_arm(cfg, args, rank)
         return

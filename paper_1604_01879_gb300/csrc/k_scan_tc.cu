@@ -297,8 +297,12 @@ struct SlotsPolicy : ListSched {
   static constexpr int NBUF = kResc ? kRescChunks : (TS_ <= 64 ? 4 : 2);
   // stage bytes: entries (A) 16 KB per part, slots (B) TS x 128 bytes per part
   static constexpr int kStage = (kResc ? 2 : 1) * (16384 + TS_ * 128);
-  static constexpr int STAGES = (200 * 1024) / kStage > 12 ? 12 : (200 * 1024) / kStage;
   static constexpr int kWarpSmem = TS_ * 12;
+  // as many stages as fit beside the engine's alignment pad, barriers and warp
+  // areas in 227 KB, at most 11 (the barrier area): rescore 6, 5, 4; scan 11,
+  // 11, 9 (TS = 16, 32, 64)
+  static constexpr int kFit = (232448 - 1024 - 256 - 4 * kWarpSmem) / kStage;
+  static constexpr int STAGES = kFit > 11 ? 11 : kFit;
   static_assert(TS_ == 16 || TS_ == 32 || TS_ == 64, "slot tile of 16, 32 or 64");
   static_assert(kResc ? EB_ == 2 : (EB_ == 1 && SPLIT_ == 1), "E4M3 scan or two-part BF16 rescore");
   SlotInfo si;

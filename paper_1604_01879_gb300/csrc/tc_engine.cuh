@@ -110,7 +110,8 @@ struct EngineLayout {
   static constexpr int kPartsB = P::SPLIT == 3 ? 2 : 1;
   // stage: A, B, then (two-part) A lo, then (SPLIT 3) B lo
   static constexpr int kStageBytes = kPartsA * kABytes + kPartsB * kBBytes;
-  static constexpr int kBarBytes = 256;
+  static constexpr int kBarBytes = 256;  // full/empty per stage, full/empty per TMEM buffer, then the TMEM address
+  static_assert((2 * P::STAGES + 2 * P::NBUF) * 8 + 4 <= kBarBytes, "barriers and TMEM address fit in 256 bytes");
   static constexpr int kEpiWarps = 4 * epi_split_of<P>::value;
   static_assert(epi_split_of<P>::value == 1 || epi_split_of<P>::value == 2 || epi_split_of<P>::value == 4,
                 "EPI_SPLIT is 1, 2 or 4");

@@ -15,7 +15,7 @@ def test_roofline_picks_dominant_kernel_and_its_roof():
     pairs, D = 7.3e8, cfg.dim
     # rescore dominant and compute-bound: 6 * pairs * D flops in 12 ms
     r = bench.roofline(cfg, _st(3.0, 12.0, 1.0), pairs, 6e9, 12e9, 64000, peaks, "measured")
-    assert r["kernel"] == "tc_engine<RescorePolicy>" and r["bound"] == "tensor"
+    assert r["kernel"] == "rescore" and r["bound"] == "tensor"
     assert abs(r["achieved"] - 6 * pairs * D / 12e-3 / 1e12) < 1e-6 * r["achieved"]
     assert abs(r["frac"] - r["achieved"] / 2000.0) < 1e-12
     assert r["unit"] == "TFLOP/s" and json.dumps(r)
@@ -25,7 +25,7 @@ def test_roofline_picks_dominant_kernel_and_its_roof():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
     assert abs(r["achieved"] - 210e9 / 31e-3 / 1e9) < 1e-6 * r["achieved"]
     # the FP8 scan is held against twice the BF16 peak
-    assert r["all"]["tc_engine<ScanPolicy>"].get("tensor_frac") is not None
+    assert r["all"]["scan"].get("tensor_frac") is not None
 
 
 def test_recorded_traffic_ignores_other_sources(tmp_path, monkeypatch):
@@ -37,7 +37,7 @@ def test_roofline_without_tensor_core_scan():
     cfg = CONFIGS["db200x64_d128_k64"]
     r = bench.roofline(cfg, _st(0.0, 0.0, 0.05), 1e6, 1e8, 0, 640, {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0},
                        "measured")
-    assert r["kernel"] == "tc_engine<AssignPolicy>" and r["scan_hbm"]["achieved_gbs"] is None
+    assert r["kernel"] == "quantiser" and r["scan_hbm"]["achieved_gbs"] is None
     assert bench.roofline(cfg, _st(0.0, 0.0, 0.0), 0, 0, 0, 0, {"hbm_gbs": 1.0, "bf16_tflops": 1.0}, "m") is None
 
 
@@ -48,13 +48,13 @@ def test_roofline_names_the_fused_pass():
     peaks = {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}
     pairs = 7.46e8
     r = bench.roofline(cfg, _st(0.0, 12.35, 0.97), pairs, 6e9, 12.5e9, 64000, peaks, "measured", with_traffic=False)
-    assert r["kernel"] == "tc_engine<FusedPolicy>" and r["bound"] == "tensor"
+    assert r["kernel"] == "fused scan + rescore" and r["bound"] == "tensor"
     assert abs(r["achieved"] - 6 * pairs * cfg.dim / 12.35e-3 / 1e12) < 1e-6 * r["achieved"]
-    assert "tc_engine<ScanPolicy>" not in r["all"] and "tc_engine<RescorePolicy>" not in r["all"]
+    assert "scan" not in r["all"] and "rescore" not in r["all"]
     # an FP8 store keeps the separate scan and rescore
     r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.1, 32.0, 1.0), pairs, 47e9, 188e9, 32768,
                        peaks, "measured", with_traffic=False)
-    assert r["kernel"] == "tc_engine<RescorePolicy>" and "tc_engine<ScanPolicy>" in r["all"]
+    assert r["kernel"] == "rescore" and "scan" in r["all"]
 
 
 def test_roofline_counts_the_rescore_candidates():
@@ -66,13 +66,13 @@ def test_roofline_counts_the_rescore_candidates():
             "rescore_rows_read": 5.1e6}
     r = bench.roofline(cfg, _st(8.0, 14.0, 1.0), 7.3e8, 47e9, 188e9, 32768, peaks, "measured", with_traffic=False,
                        cand=cand)
-    assert r["kernel"] == "tc_engine<RescorePolicy>" and r["bound"] == "hbm"
+    assert r["kernel"] == "rescore" and r["bound"] == "hbm"
     assert abs(r["achieved"] - 5e6 * (4 * cfg.dim + 12) / 14e-3 / 1e9) < 1e-6 * r["achieved"]
     assert r["candidate_work"]["items_kept_fraction"] == 0.4
     c2 = CONFIGS["db12000x64_d4096_k1024"]
     r = bench.roofline(c2, _st(0.0, 12.0, 1.0), 7.3e8, 6e9, 12e9, 64000, peaks, "measured", with_traffic=False,
                        cand=dict(cand, cand_pairs=1e8))
-    assert r["kernel"] == "tc_engine<FusedPolicy>"
+    assert r["kernel"] == "fused scan + rescore"
     assert abs(r["achieved"] - 6 * 7.3e8 * c2.dim / 12e-3 / 1e12) < 1e-6 * r["achieved"]
     m = (2 * 7.3e8 + 6 * 1e8) * c2.dim / 12e-3 / 1e12 / 2000.0
     assert abs(r["candidate_work"]["method_work_frac"] - m) < 1e-9
@@ -85,14 +85,14 @@ def test_traffic_is_scaled_by_the_launch_units(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "traffic.md").write_text(
         "| kernel | source hash | capture | bytes per unit | unit | note |\n"
         "|---|---|---|---|---|---|\n"
-        "| tc_engine<RescorePolicy> | abc123 | reduced | 16500 | rescore row read | x |\n")
+        "| rescore | abc123 | reduced | 16500 | rescore row read | x |\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda files: "abc123")
     cand = {"rescore_items": 10, "rescore_items_kept": 9, "cand_pairs": 1e8, "cand_rows": 9e6,
             "rescore_rows_read": 1.1e7}
     r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.0, 31.0, 1.0), 7e8, 47e9, 188e9, 32768,
                        {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}, "measured", cand=cand)
-    assert r["kernel"] == "tc_engine<RescorePolicy>"
+    assert r["kernel"] == "rescore"
     assert r["traffic"] == 16500 * 1.1e7 and "reduced" in r["traffic_source"]
     monkeypatch.setattr(bench, "kernel_source_hash", lambda files: "changed")
     r = bench.roofline(CONFIGS["db200000x64_d4096_k4096_fp8"], _st(8.0, 31.0, 1.0), 7e8, 47e9, 188e9, 32768,
