@@ -1014,7 +1014,7 @@ def bench_kmeans(cfg, gift, torch, dev, stream, data):
     torch.cuda.empty_cache()
     return {"rows": len(X), "dim": cfg.dim, "K": cfg.n_codewords, "iters": cfg.kmeans_iters, "gpu_ms": ms,
             "gpu_ms_per_iter": ms / max(1, cfg.kmeans_iters), "host_fixture_s_per_iter": host_it,
-            "note": "exact assignment (tensor-core quantiser) + float64 means; the host fixture uses FP32 distances"}
+            "note": "exact assignment (tensor-core quantiser) + two-float FP32 means; the host fixture uses FP32 distances"}
 
 
 def bench_differentiation(gift, torch, dev, stream, reps=3, n_shapes=None, n_queries=None):
