@@ -97,6 +97,13 @@ CONFIGS = {
         name="db3200x64_d4096_k512_fp8", n_shapes=3200, n_views=64, dim=4096, n_classes=64, n_codewords=512,
         n_queries=256, query_ma=2, storage="fp8", rescore_r=100, topk=100, sif_k1=50, batch=32,
         kmeans_shapes=128, kmeans_iters=6, seed=6, generator="counter"),
+    # the 200,000-shape workload with a tenth of the shapes per class (same classes, vocabulary, batch, MA), rescore
+    # depth scaled with the database: the same list and slot structure per batch at 26 GB, for DRAM counters
+    "db20000x64_d4096_k4096_fp8": Config(
+        name="db20000x64_d4096_k4096_fp8", n_shapes=20000, n_views=64,
+        dim=4096, n_classes=400, n_codewords=4096, n_queries=256, query_ma=2,
+        storage="fp8", rescore_r=100, topk=100, sif_k1=50, batch=256,
+        kmeans_shapes=512, kmeans_iters=6, seed=3, generator="counter"),
     # 16x scale-up of ModelNet40 with FP8 store and query-side MA = 2
     "db200000x64_d4096_k4096_fp8": Config(
         name="db200000x64_d4096_k4096_fp8", n_shapes=200000, n_views=64,
