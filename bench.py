@@ -227,9 +227,9 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
     # (three products over every touched pair, reported as the rescore kernel)
     fused = cfg.storage == "bf16" and st["scan_kernel_ms"] <= 0 and st["rescore_kernel_ms"] > 0
     resc_name = "fused scan + rescore" if fused else "rescore"
-    # the launches behind each timed role (lists of up to 64 query slots run with the
-    # entries as MMA rows, one launch per slot tile of 16, 32 or 64)
-    classes = ["16", "32", "64"]
+    # the launches behind each timed role (lists of up to 80 query slots run with the
+    # entries as MMA rows, one launch per slot tile of 16, 32, 64 or 80)
+    classes = ["16", "32", "64", "80"]
     launches = {
         "scan": (["tc_engine<ScanPolicy<1>>"] + [f"tc_engine<SlotsPolicy<1,1,{c}>>" for c in classes]
                  if cfg.storage == "fp8" else ["tc_engine<ScanPolicy<2>>"]),

@@ -9,7 +9,7 @@
 // into the per-(slot, run) table with atomicMax on its order-preserving key
 // (f2key, so negative cosines keep their order; 0 = not written).
 //
-// (Lists touched by at most 64 slots of a batch swap the roles: entries are the
+// (Lists touched by at most 80 slots of a batch swap the roles: entries are the
 // MMA rows and slots the columns, see the slot-column policies below.)
 //
 // Scan: BF16 or E4M3 store, one product per k-block, 256 entries per tile.
@@ -266,11 +266,11 @@ struct RescorePolicy : ListSched {
 
 // ---------------------------------------------------------------- slot-column policies
 // Most lists are touched by few query slots of a batch (a few to a few dozen,
-// from the queries whose views share its codeword). For lists of up to 64
+// from the queries whose views share its codeword). For lists of up to 80
 // slots these policies make the list entries the 128 MMA rows (A, TMEM lanes)
-// and the slots the N columns (B), N = TS in {16, 32, 64}, the smallest that
-// holds the list's slots. The small slot tile leaves most of shared memory to
-// the entry tiles, so more of them are in flight from DRAM (5 to 11 stages
+// and the slots the N columns (B), N = TS in {16, 32, 64, 80}, the smallest
+// that holds the list's slots. The small slot tile leaves most of shared memory
+// to the entry tiles, so more of them are in flight from DRAM (4 to 11 stages
 // instead of 3 or 4), and the MMAs shrink with N. Each launch runs the lists
 // of one slot class; lists of more slots keep the slot-row policies above.
 //
@@ -285,7 +285,9 @@ struct RescorePolicy : ListSched {
 // EB = 1, SPLIT = 1: E4M3 scan (per-slot and per-entry scales, one chunk).
 // EB = 2, SPLIT = 3: FP32-level rescore with two-part BF16 operands, the
 // reduction in kRescChunks chunks summed in FP32 (as RescorePolicy).
-__host__ __device__ constexpr int slot_class(int64_t M) { return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 : 128; }
+__host__ __device__ constexpr int slot_class(int64_t M) {
+  return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 : M <= 80 ? 80 : 128;
+}
 
 template <int EB_, int SPLIT_, int TS_>
 struct SlotsPolicy : ListSched {
@@ -299,11 +301,11 @@ struct SlotsPolicy : ListSched {
   static constexpr int kStage = (kResc ? 2 : 1) * (16384 + TS_ * 128);
   static constexpr int kWarpSmem = TS_ * 12;
   // as many stages as fit beside the engine's alignment pad, barriers and warp
-  // areas in 227 KB, at most 11 (the barrier area): rescore 6, 5, 4; scan 11,
-  // 11, 9 (TS = 16, 32, 64)
+  // areas in 227 KB, at most 11 (the barrier area): rescore 6, 5, 4, 4; scan
+  // 11, 11, 9, 8 (TS = 16, 32, 64, 80)
   static constexpr int kFit = (232448 - 1024 - 256 - 4 * kWarpSmem) / kStage;
   static constexpr int STAGES = kFit > 11 ? 11 : kFit;
-  static_assert(TS_ == 16 || TS_ == 32 || TS_ == 64, "slot tile of 16, 32 or 64");
+  static_assert(TS_ == 16 || TS_ == 32 || TS_ == 64 || TS_ == 80, "slot tile of 16, 32, 64 or 80");
   static_assert(kResc ? EB_ == 2 : (EB_ == 1 && SPLIT_ == 1), "E4M3 scan or two-part BF16 rescore");
   SlotInfo si;
   const int64_t* item_map;  // rescore: [n_items] the kept work items (ascending); scan: null
@@ -355,21 +357,20 @@ struct SlotsPolicy : ListSched {
     for (int j = 0; j < TS_; ++j) x.sum[j] = 0.f;
   }
   __device__ __forceinline__ void epi_chunk(const Item&, int, uint32_t taddr, Ctx& x, int, uint8_t*) const {
-    if constexpr (TS_ == 16) {
-      uint32_t r[16];
-      tc::tmem_ld16(taddr, r);
+#pragma unroll
+    for (int pc = 0; pc < TS_ / 32; ++pc) {
+      uint32_t r[32];
+      tc::tmem_ld32(taddr + pc * 32, r);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) x.sum[j] += __uint_as_float(r[j]);
-    } else {
+      for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
+    }
+    if constexpr (TS_ % 32 == 16) {  // the last 16 columns (TS = 16, 80)
+      uint32_t r[16];
+      tc::tmem_ld16(taddr + (TS_ / 32) * 32, r);
+      tc::tmem_wait_ld();
 #pragma unroll
-      for (int pc = 0; pc < TS_ / 32; ++pc) {
-        uint32_t r[32];
-        tc::tmem_ld32(taddr + pc * 32, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
-      }
+      for (int j = 0; j < 16; ++j) x.sum[(TS_ / 32) * 32 + j] += __uint_as_float(r[j]);
     }
   }
   __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int, uint8_t* ws) const {
@@ -651,7 +652,7 @@ void scan_fp8_class(const Index& ix, const FifPlan& P, const SlotInfo& si, const
 }
 
 // the rescore work of one slot class: its items that hold a candidate run
-// (slot classes of up to 64 slots: slot columns; 128: slot rows, RescorePolicy)
+// (slot classes of up to 80 slots: slot columns; 128: slot rows, RescorePolicy)
 template <int TS>
 struct RescoreClass {
   using Pol = std::conditional_t<TS == 128, RescorePolicy, SlotsPolicy<2, 3, (TS < 128 ? TS : 64)>>;
@@ -753,14 +754,15 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   si.table = table;
   const int grid = device_sm_count();
   if (fp8) {
-    // lists of up to 64 slots: list entries are the MMA rows, query slots the columns,
+    // lists of up to 80 slots: list entries are the MMA rows, query slots the columns,
     // one launch per slot class
     const CUtensorMap tA = make_tmap_u8(ix.list_feat, ix.list_rows_alloc, D, tc::kTM);
     if (P.kc) P.kc->begin(1);
     scan_fp8_class<16>(ix, P, si, tA, q8, qrows, sc, s, grid);
     scan_fp8_class<32>(ix, P, si, tA, q8, qrows, sc, s, grid);
     scan_fp8_class<64>(ix, P, si, tA, q8, qrows, sc, s, grid);
-    {  // lists of more than 64 slots: slots are the MMA rows, 256 entries per item
+    scan_fp8_class<80>(ix, P, si, tA, q8, qrows, sc, s, grid);
+    {  // lists of more than 80 slots: slots are the MMA rows, 256 entries per item
       ScanPolicy<1> pol;
       static_cast<ListSched&>(pol) = list_sched(ix, P, kScanTN, sc, s, 128);
       pol.nkb = (int)cdiv(D, 128);
@@ -804,10 +806,12 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     RescoreClass<16> c16;
     RescoreClass<32> c32;
     RescoreClass<64> c64;
+    RescoreClass<80> c80;
     RescoreClass<128> c128;
     c16.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
     c32.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
     c64.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
+    c80.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
     c128.plan(ix, P, sr, cand_sorted, R, upper, flags, pos, sc, s);
     const CUtensorMap tA = make_tmap_bf16(bhi, ix.list_rows_alloc, D, tc::kTM);
     const CUtensorMap tA2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, tc::kTM);
@@ -815,6 +819,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     c16.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
     c32.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
     c64.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
+    c80.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
     c128.run(ix, tA, tA2, qhi, qlo, qrows, grid, s);
     if (P.kc) P.kc->end(2);
   }

@@ -200,8 +200,8 @@ def test_reduced_precision_store_without_rescore(gpu_lib, storage, tol):
 
 def test_fp8_lists_of_every_slot_class(gpu_lib):
     """E4M3 scan and FP32-level rescore with query MA = 2 where the touched lists hold from 16 to
-    386 query slots: lists of up to 64 slots run with entries as the MMA rows (slot tiles of 16,
-    32, 64), larger ones with slots as the rows, in one or several slot tiles of 128."""
+    386 query slots: lists of up to 80 slots run with entries as the MMA rows (slot tiles of 16,
+    32, 64, 80), larger ones with slots as the rows, in one or several slot tiles of 128."""
     import torch
     N, Nv, D, C, K = 96, 16, 128, 4, 12
     X, cb, _, _, dbc, _ = _case(N, Nv, D, C, K, 1, (16,), 151)
@@ -212,7 +212,7 @@ def test_fp8_lists_of_every_slot_class(gpu_lib):
     M = np.bincount(qc.ravel(), minlength=K)
     M = M[M > 0]
     assert (M <= 16).any() and ((M > 16) & (M <= 32)).any() and ((M > 32) & (M <= 64)).any()
-    assert ((M > 64) & (M <= 128)).any() and (M > 256).any()
+    assert ((M > 64) & (M <= 80)).any() and ((M > 80) & (M <= 128)).any() and (M > 256).any()
     ref = O.fif_scores(Q, qoff, qc, X, dbc)
     Qd = torch.from_numpy(Q).cuda()
     plain = _index(gpu_lib, torch, X, cb, N, Nv, K, storage="fp8", query_ma=2, keep_exact=False)
