@@ -9,11 +9,12 @@
 //   dU_i  = (1/|u_i|)  ( g_i - (g_i . u_i/|u_i|) u_i/|u_i| ),  g_i = sum_p c v_j*/|v_j*|
 //   dV_r  = (1/|v_r|)  ( h_r - (h_r . v_r/|v_r|) v_r/|v_r| ),  h_r = sum_{(i,p): j*=r} c u_i/|u_i|
 // (the projections use s = g-weighted cosines: sum_p c s = g_i . u_i/|u_i|).
-// G = A V and H = A^T U are GEMMs with the one-hot matrix A[i, r] =
-// c v-norm-weight where r is the argmax view of (i, shape(r)); A is never
-// stored: the engine's producer warp writes each A tile from the argmax
-// (transposed to shape-major) into shared memory, and the tensor cores
-// multiply it with two-part operands. Then
+// G = A V is a GEMM with the one-hot matrix A[i, r] = c v-norm-weight where r
+// is the argmax view of (i, shape(r)); A is never stored: the engine's producer
+// warp writes each A tile from the argmax (transposed to shape-major) into
+// shared memory, and the tensor cores multiply it with two-part operands.
+// H = A^T U is a segmented sum on the CUDA cores over the entries sorted by
+// their argmax view (N_v times fewer multiply-adds than the dense product). Then
 //   dW = dU^T Q + dV^T P,  dQ = dU W,  dP = dV W
 // as engine GEMMs on transposed two-part operands.
 #include "gift_internal.cuh"
@@ -411,6 +412,80 @@ __global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restri
   for (int v = qoff[b] + threadIdx.x; v < qoff[b + 1]; v += blockDim.x) vq[v] = b;
 }
 
+// ---------------------------------------------------------------- H = A^T U on the CUDA cores
+// Every database view's row of H is the weighted sum of the query views whose
+// argmax in its shape is that view:
+//   H[p N_v + j] = sum_{i : j(i, p) = j} wV[p, i] U[i]
+// The (shape, query view) entries are sorted by that database view (stably, so in
+// ascending entry order), and one warp per database view sums its entries' rows of
+// U (L2-resident) in FP32 in that order: N_v times fewer multiply-adds than the dense
+// one-hot GEMM, and a result that does not depend on the launch.
+// key of every (shape p, query view i) entry of the shape-major argmax: its database
+// view r = p N_v + j (nr when the view has no argmax)
+__global__ void k_onehot_keys(const int16_t* __restrict__ amT, int64_t nq, int Np, int nv,
+                              int32_t* __restrict__ keys) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * (int64_t)Np) return;
+  const int p = (int)(e / nq);
+  const int j = amT[e];
+  keys[e] = (j >= 0 && j < nv) ? p * nv + j : Np * nv;
+}
+
+// H[r] = sum of wV[e] U[e mod nq] over the entries e of row r (perm[off[r]] ..
+// perm[off[r + 1]]), in ascending e: one warp per database view, lane c owns columns
+// 4 c + 128 t, up to kHCols columns per pass (dout % 4 == 0)
+constexpr int kHCols = 512;
+__global__ __launch_bounds__(256) void k_segment_rows_sum(const float* __restrict__ U, const int32_t* __restrict__ perm,
+                                                          const int64_t* __restrict__ off,
+                                                          const float* __restrict__ wT, int64_t nq, int64_t nr,
+                                                          int dout, float* __restrict__ H) {
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nr) return;
+  constexpr int kT = kHCols / 128;  // float4 pieces per lane and pass
+  const int64_t e0 = off[r], e1 = off[r + 1];
+  for (int cb = 0; cb < dout; cb += kHCols) {
+    float acc[kT][4];
+#pragma unroll
+    for (int t = 0; t < kT; ++t)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+      const int n = (int)min((int64_t)32, e1 - eb);
+      int64_t src = 0;
+      float wl = 0.f;
+      if (lane < n) {
+        const int32_t e = perm[eb + lane];
+        src = (int64_t)(e % nq) * dout;
+        wl = wT[e];
+      }
+#pragma unroll 4
+      for (int k = 0; k < n; ++k) {  // unrolled: several entries' row loads in flight
+        const int64_t sk = __shfl_sync(0xffffffffu, src, k);
+        const float wk = __shfl_sync(0xffffffffu, wl, k);
+        const float* u = U + sk + cb;
+#pragma unroll
+        for (int t = 0; t < kT; ++t) {
+          const int c = 4 * lane + 128 * t;
+          if (cb + c < dout) {
+            const float4 x = *reinterpret_cast<const float4*>(u + c);
+            acc[t][0] = fmaf(wk, x.x, acc[t][0]);
+            acc[t][1] = fmaf(wk, x.y, acc[t][1]);
+            acc[t][2] = fmaf(wk, x.z, acc[t][2]);
+            acc[t][3] = fmaf(wk, x.w, acc[t][3]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      const int c = 4 * lane + 128 * t;
+      if (cb + c < dout)
+        *reinterpret_cast<float4*>(H + r * dout + cb + c) = make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+    }
+  }
+}
+
 // two-part BF16 operand with one TMA box of padding rows
 struct Operand {
   __nv_bfloat16* hi = nullptr;
@@ -565,6 +640,7 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
       argmax, nq, Np, nv, vquery, vcoef, gS, P.vinv, P.uinv, amT, wU, wV);
   GIFT_LAUNCHED("k_onehot_prep");
   float* G = sc.get<float>((size_t)std::max(nq, nr) * dout);  // G = A V, then H = A^T U
+  GIFT_REQUIRE(dout % 4 == 0, "projected width must be a multiple of 4");
   const int sms = device_sm_count();
   {
     int64_t ldr = 0;
@@ -594,29 +670,21 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     GIFT_LAUNCHED("k_tangent");
   }
   {
-    int64_t ldq = 0;
-    const Operand Ut = make_transposed(P.U, GIFT_F32, nq, dout, ldq, sc, s);  // [dout, ldq], K = query views
-    OneHotPolicy<false> pol;
-    pol.M = nr;
-    pol.N = dout;
-    pol.nkb = (int)(ldq / 64);
-    pol.nq = nq;
-    pol.nr = nr;
-    pol.Np = Np;
-    pol.nv = nv;
-    pol.amT = amT;
-    pol.gS = gS;
-    pol.vquery = vquery;
-    pol.vcoef = vcoef;
-    pol.kinv = P.uinv;
-    pol.wT = wV;
-    pol.C = G;
-    pol.fast = nv >= 64 && nr < ((int64_t)1 << 31);
-    pol.kb_per_shape = 1;
-    const CUtensorMap tB = make_tmap_bf16(Ut.hi, Ut.rows_alloc, ldq, 128);
-    const CUtensorMap tB2 = make_tmap_bf16(Ut.lo, Ut.rows_alloc, ldq, 128);
-    tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nr, tc::kTM) * cdiv(dout, 128)),
-                      s);
+    // the (shape, query view) entries grouped by their argmax database view, in
+    // ascending entry order (a stable sort), then one warp per database view
+    const int64_t ne = nq * (int64_t)Np;
+    GIFT_REQUIRE(ne < (int64_t)INT32_MAX && nr + 1 < (int64_t)INT32_MAX,
+                 "query views x database shapes must stay below 2^31 for the gradient");
+    int32_t* keys = sc.get<int32_t>((size_t)ne);
+    k_onehot_keys<<<(unsigned)cdiv(ne, (int64_t)256), 256, 0, s>>>(amT, nq, Np, nv, keys);
+    GIFT_LAUNCHED("k_onehot_keys");
+    int32_t* perm = sc.get<int32_t>((size_t)ne);
+    int32_t* skeys = sc.get<int32_t>((size_t)ne);
+    stable_sort_by_key(keys, ne, (int32_t)(nr + 1), perm, skeys, sc, s);
+    int64_t* off = sc.get<int64_t>((size_t)nr + 2);
+    bin_offsets(skeys, ne, (int32_t)(nr + 1), off, s);
+    k_segment_rows_sum<<<(unsigned)cdiv(nr, (int64_t)8), 256, 0, s>>>(P.U, perm, off, wV, nq, nr, dout, G);
+    GIFT_LAUNCHED("k_segment_rows_sum");
     k_tangent<<<(unsigned)cdiv(nr, 8), 256, 0, s>>>(P.V, P.vinv, G, nr, dout, dV);
     GIFT_LAUNCHED("k_tangent");
   }

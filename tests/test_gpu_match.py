@@ -53,6 +53,23 @@ def test_backward_matches_oracle(gpu_lib, with_w):
         assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
 
 
+@pytest.mark.parametrize("nv,dout", [(70, 16), (5, 144)])
+def test_backward_ragged_widths(gpu_lib, nv, dout):
+    """Gradients with database shapes of 70 views (more than one 64-view k-block of the query-side
+    GEMM) and of 5 views, and a projected width above 128 that is not a multiple of 128 (a partial
+    last column piece of the database-side segmented sum)."""
+    import torch
+    Q, off, P, W, G = _tie_free(8, B=3, Np=6, nv=nv, din=32, dout=dout, margin=1e-5, counts=(7, 12, 3))
+    qd, pd, Wd = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(), torch.from_numpy(W).cuda()
+    S, am = gpu_lib.match_forward(qd, off, pd, Wd)
+    dW, dQ, dP = gpu_lib.match_backward(qd, off, pd, Wd, torch.from_numpy(G).cuda(), am)
+    rW, rQ, rP = O.match_backward(Q, off, P, W, G)
+    scale = max(np.abs(rQ).max(), np.abs(rP).max())
+    assert np.allclose(dQ.cpu().numpy(), rQ, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dP.cpu().numpy(), rP, rtol=1e-4, atol=1e-5 * scale)
+    assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
+
+
 def test_autograd_function(gpu_lib):
     import torch
     Q, off, P, W, G = _tie_free(3, B=3, Np=11, nv=8, din=32, dout=16)
@@ -109,10 +126,9 @@ def test_bf16_inputs_forward_backward(gpu_lib):
 def test_wide_shapes_several_tiles(gpu_lib, dtype):
     """64 views per database shape and ragged query view counts: the forward's
     short-reduction epilogue (two whole shapes per 128-column tile), the
-    gradient GEMMs with the A tile generated by four warps (one shape per
-    k-block on the query side, up to three shapes per 128-row tile on the
-    database side), BF16 inputs read in place, several row tiles with ragged
-    tails — all against the oracle in full."""
+    query-side gradient GEMM with the A tile generated by four warps (one shape
+    per k-block), the database-side segmented sum, BF16 inputs read in place,
+    several row tiles with ragged tails — all against the oracle in full."""
     import torch
     Q, off, P, W, G = _tie_free(6, B=4, Np=5, nv=64, din=96, dout=128, margin=1e-5, counts=(40, 100, 64, 57))
     if dtype == "bf16":
