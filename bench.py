@@ -234,7 +234,7 @@ def roofline(cfg, st, scan_pairs, scan_bytes, rescore_bytes, assign_rows, peaks,
         "scan": (["tc_engine<ScanPolicy<1>>"] + [f"tc_engine<SlotsPolicy<1,1,{c}>>" for c in classes]
                  if cfg.storage == "fp8" else ["tc_engine<ScanPolicy<2>>"]),
         "rescore": ["tc_engine<RescorePolicy>"] + [f"tc_engine<SlotsPolicy<2,3,{c}>>" for c in classes],
-        "fused scan + rescore": ["tc_engine<FusedPolicy>"],
+        "fused scan + rescore": ["tc_engine<RescorePolicy> (every touched pair, FP32 level)"],
         "quantiser": ["tc_engine<AssignPolicy>"],
     }
     resc_flops, resc_bytes = 6.0 * scan_pairs * D, rescore_bytes

@@ -401,14 +401,11 @@ void run_fif(Index& ix, const float* q, int64_t nv, const std::vector<int32_t>& 
   fif_plan(ix, P, sc, s);
   uint32_t* table = sc.get<uint32_t>(P.table_upper);
   fif_zero_table(P, table, s);
-  // a BF16 store that is the hi part of the rescore rows: one fused pass gives
-  // the BF16 maxima (candidate selection) and the FP32-level maxima (rescore)
+  // a BF16 store that is the hi part of the rescore rows: one pass over every
+  // touched pair at FP32 level gives the maxima both the candidate selection and
+  // the candidates' scores read (no separate rescore)
   const bool fused = R > 0 && fused_scan_ok(ix);
-  uint32_t* table32 = nullptr;
-  if (fused) {
-    table32 = sc.get<uint32_t>(P.table_upper);
-    fif_zero_table(P, table32, s);
-  }
+  uint32_t* table32 = fused ? table : nullptr;
 
   tm.mark(ST_SCAN);
   if (fused)

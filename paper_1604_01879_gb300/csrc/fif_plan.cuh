@@ -41,12 +41,13 @@ void fif_zero_table(const FifPlan& P, uint32_t* table, cudaStream_t s);
 void fif_scan(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore,
               const int32_t* cand_sorted, int R, cudaStream_t s);
 // tcgen05 scan of a BF16 or E4M3 store (rescore: two-part BF16, candidates only;
-// table32 non-null: the fused pass of a BF16 store with its two-part rows, which
-// fills `table` with BF16 maxima and `table32` with FP32-level maxima of every run)
+// table32 non-null: a BF16 store with its two-part rows scanned at FP32 level over
+// every touched pair, which fills `table32` with the maxima of every run: the
+// candidates and their scores both come from it, with no separate rescore)
 void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescore, const int32_t* cand_sorted,
                  int R, Scratch& sc, cudaStream_t s, uint32_t* table32 = nullptr);
 // counts of the candidate work of a batch (stats [3..7]) without running the
-// rescore: for the fused pass, whose FP32-level products cover every touched pair
+// rescore: for the FP32-level pass over every touched pair of a BF16 store
 void fif_rescore_stats(const Index& ix, const FifPlan& P, const int32_t* cand_sorted, int R, Scratch& sc,
                        cudaStream_t s);
 void fif_combine(const Index& ix, const FifPlan& P, const uint32_t* table, float* S_dense,

@@ -18,7 +18,9 @@
 // summed in FP32 by the epilogue; only runs of the query's top-R candidate
 // shapes are kept, and only work items that hold such a run are run (a
 // pre-pass lists them): the FP32-level rescore needs the rows of its
-// candidates' runs, not every row of a touched list.
+// candidates' runs, not every row of a touched list. For a BF16 store whose
+// rows are the hi parts of the two-part store, the same policy runs over every
+// touched pair with every run written: the scan itself is FP32-level.
 #include <type_traits>
 
 #include "fif_plan.cuh"
@@ -196,15 +198,17 @@ struct RescorePolicy : ListSched {
   SlotInfo si;
   const int32_t* cand;      // [B, R] candidate ids sorted ascending
   int R;
-  const int64_t* item_map;  // [n_items] the work items holding a candidate run (ascending)
-  const int64_t* n_items;
+  const int64_t* item_map;  // [n_items] the work items holding a candidate run (ascending); null: every item,
+  const int64_t* n_items;   // every run written (the FP32-level scan of a BF16 store with its two-part rows)
   using Item = ListItem;
   struct Ctx {
     RowCtx row;
     float sum[TN];
   };
-  __device__ __forceinline__ int64_t total() const { return *n_items; }
-  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item_map[item]); }
+  __device__ __forceinline__ int64_t total() const { return item_map ? *n_items : total_items(); }
+  __device__ __forceinline__ Item decode(int64_t item) const {
+    return decode_list<TN>(item_map ? item_map[item] : item);
+  }
   // never an empty chunk: each chunk must write its own accumulator
   // chunks bound the MMA steps feeding one accumulator (about 192, 3 products
   // x 4 sub-steps per k-block); short reductions use one chunk
@@ -242,7 +246,7 @@ struct RescorePolicy : ListSched {
     const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
     const int* e_shape = e_run + 2 * TN;
     if (!x.row.valid) return;
-    const int32_t* cq = cand + (int64_t)x.row.qq * R;
+    const int32_t* cq = cand ? cand + (int64_t)x.row.qq * R : nullptr;
     int cur_run = -1, cur_shape = 0;
     float cur_max = 0.f;
 #pragma unroll
@@ -250,7 +254,7 @@ struct RescorePolicy : ListSched {
       const int run = e_run[c];
       const float v = x.sum[c] * x.row.qi * e_scale[c];
       if (run != cur_run) {
-        if (cur_run >= 0 && is_candidate(cq, R, cur_shape))
+        if (cur_run >= 0 && (!cand || is_candidate(cq, R, cur_shape)))
           atomicMax(si.table + x.row.rb + cur_run, f2key(cur_max));
         cur_run = run;
         cur_max = v;
@@ -259,7 +263,8 @@ struct RescorePolicy : ListSched {
         cur_max = fmaxf(cur_max, v);
       }
     }
-    if (cur_run >= 0 && is_candidate(cq, R, cur_shape)) atomicMax(si.table + x.row.rb + cur_run, f2key(cur_max));
+    if (cur_run >= 0 && (!cand || is_candidate(cq, R, cur_shape)))
+      atomicMax(si.table + x.row.rb + cur_run, f2key(cur_max));
     (void)it;
   }
 };
@@ -401,88 +406,6 @@ struct SlotsPolicy : ListSched {
       }
     }
   }
-};
-
-// ---------------------------------------------------------------- fused scan + rescore policy
-// For a BF16 store that is also the hi part of the two-part rescore store:
-// one pass computes, per (slot, entry), hi*hi in two accumulators (first and
-// second half of the k-blocks, 128 MMA steps or fewer each) and hi*lo + lo*hi
-// in a third. The BF16 score (both hi*hi halves) fills the scan table, whose
-// top-R shapes are the rescore candidates; the FP32-level score (all three)
-// fills a second table, from which the candidates' rescored values are read,
-// so the separate scan pass over the BF16 store is not needed.
-struct FusedPolicy : ListSched {
-  // three accumulators leave room for one TMEM buffer, so the epilogue's drain
-  // stalls the next tile's MMAs: sixteen epilogue warps (four per lane
-  // quadrant, each over a quarter of the columns) shorten it; a run split
-  // between quarters is merged by the atomicMax of the partial maxima
-  static constexpr int TN = kRescTN, NBUF = 1, STAGES = 3, SPLIT = 3, EB = 2, ACCS = 3, EPI_SPLIT = 4;
-  static constexpr int kWarpSmem = TN * 12;
-  SlotInfo si;
-  uint32_t* table32;  // per-(slot, run) FP32-level maxima
-  using Item = ListItem;
-  struct Ctx {
-    RowCtx row;
-    int cur_run, part;
-    float cur_bf, cur_fp;
-  };
-  __device__ __forceinline__ static int acc_of(int product, int kb, int n) {
-    return product == 0 ? (kb < n / 2 ? 0 : 1) : 2;
-  }
-  __device__ __forceinline__ int64_t total() const { return total_items(); }
-  __device__ __forceinline__ Item decode(int64_t item) const { return decode_list<TN>(item); }
-  __device__ __forceinline__ int nchunks(const Item&) const { return 1; }
-  __device__ __forceinline__ void chunk(const Item& it, int, int& br, int& kb0, int& kb1) const {
-    br = (int)it.e0;
-    kb0 = 0;
-    kb1 = nkb;
-  }
-  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.s0; }
-  __device__ __forceinline__ void epi_begin(const Item& it, Ctx& x, int m, int ew, uint8_t* ws) const {
-    load_entry_meta<TN>(si, it, ws);
-    load_row(si, it, m, x.row);
-    x.cur_run = -1;
-    x.part = ew >> 2;
-    x.cur_bf = x.cur_fp = 0.f;
-  }
-  __device__ __forceinline__ void flush(const Ctx& x) const {
-    if (!x.row.valid || x.cur_run < 0) return;
-    atomicMax(si.table + x.row.rb + x.cur_run, f2key(x.cur_bf));
-    atomicMax(table32 + x.row.rb + x.cur_run, f2key(x.cur_fp));
-  }
-  __device__ __forceinline__ void epi_chunk(const Item& it, int, uint32_t taddr, Ctx& x, int, uint8_t* ws) const {
-    const int* e_run = reinterpret_cast<const int*>(ws);
-    const float* e_scale = reinterpret_cast<const float*>(e_run + TN);
-    // this warp's 32 columns, 16 at a time
-    const int npieces = (it.ne + 15) >> 4;
-    const int pc1 = min(npieces, 2 * x.part + 2);
-    for (int pc = 2 * x.part; pc < pc1; ++pc) {
-      uint32_t h0[16], h1[16], cr[16];
-      tc::tmem_ld16(taddr + pc * 16, h0);
-      tc::tmem_ld16(taddr + TN + pc * 16, h1);
-      tc::tmem_ld16(taddr + 2 * TN + pc * 16, cr);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int c = pc * 16 + j;
-        const int run = e_run[c];
-        const float f = x.row.qi * e_scale[c];
-        const float hh = __uint_as_float(h0[j]) + __uint_as_float(h1[j]);
-        const float u = hh * f;
-        const float v = (hh + __uint_as_float(cr[j])) * f;
-        if (run != x.cur_run) {
-          flush(x);
-          x.cur_run = run;
-          x.cur_bf = u;
-          x.cur_fp = v;
-        } else {
-          x.cur_bf = fmaxf(x.cur_bf, u);
-          x.cur_fp = fmaxf(x.cur_fp, v);
-        }
-      }
-    }
-  }
-  __device__ __forceinline__ void epi_end(const Item&, Ctx& x, int, uint8_t*) const { flush(x); }
 };
 
 // slot-ordered BF16 copies of the query views: hi = bf16(q), lo = bf16(q - hi)
@@ -710,7 +633,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
   if (ns <= 0) return;
   const bool fused = table32 != nullptr;
   GIFT_REQUIRE(!fused || (!rescore && ix.prm.storage == GIFT_BF16 && ix.list_lo && !ix.list_hi && D > 64),
-               "the fused scan needs a BF16 store with its two-part rescore rows");
+               "the FP32-level scan needs a BF16 store with its two-part rescore rows");
   if (fused) rescore = true;  // slot low parts, rescore tile width
   const bool fp8 = !rescore && ix.prm.storage == GIFT_FP8_E4M3;
   const int64_t qrows = ns + tc::kTM;  // one box of padding rows
@@ -736,7 +659,7 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     P.slot_hi = qhi;
     P.slot_lo = qlo;
   }
-  // the BF16 scan and the fused pass schedule 128 slots x tn entries per item
+  // the BF16 scan and the FP32-level pass schedule 128 slots x tn entries per item
   auto sched = [&](int tn) {
     ListSched ls = list_sched(ix, P, tn, sc, s);
     ls.nkb = (int)cdiv(D, 64);
@@ -782,14 +705,20 @@ void fif_scan_tc(const Index& ix, const FifPlan& P, uint32_t* table, bool rescor
     tc::launch_engine(tA, tB, tA, tB, pol, ix.d_err, grid, s);
     if (P.kc) P.kc->end(1);
   } else if (fused) {
-    FusedPolicy pol;
+    // every touched pair at FP32 level (three products, reduction in chunks), every
+    // run written: the top-R then comes from FP32-level scores and needs no rescore
+    RescorePolicy pol;
     static_cast<ListSched&>(pol) = sched(kRescTN);
     pol.si = si;
-    pol.table32 = table32;
+    pol.si.table = table32;
+    pol.cand = nullptr;
+    pol.R = 0;
+    pol.item_map = nullptr;
+    pol.n_items = nullptr;
     const CUtensorMap tA = make_tmap_bf16(qhi, qrows, D, tc::kTM);
-    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, FusedPolicy::TN);
+    const CUtensorMap tB = make_tmap_bf16(ix.list_feat, ix.list_rows_alloc, D, RescorePolicy::TN);
     const CUtensorMap tA2 = make_tmap_bf16(qlo, qrows, D, tc::kTM);
-    const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, FusedPolicy::TN);
+    const CUtensorMap tB2 = make_tmap_bf16(ix.list_lo, ix.list_rows_alloc, D, RescorePolicy::TN);
     if (P.kc) P.kc->begin(2);
     tc::launch_engine(tA, tB, tA2, tB2, pol, ix.d_err, grid, s);
     if (P.kc) P.kc->end(2);
