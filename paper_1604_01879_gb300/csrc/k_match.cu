@@ -120,25 +120,23 @@ __global__ __launch_bounds__(256) void k_transpose_bf16(const __nv_bfloat16* __r
 // k-blocks per accumulator chunk: 16 x 4 sub-steps x 3 products = 192 MMA steps
 constexpr int kOneHotChunkKB = 16;
 
-// ROWS_Q: rows are query views i and the reduction runs over database views r
-// (G = A V); otherwise rows are database views r and the reduction runs over
-// query views i (H = A^T U). B is the transposed two-part operand of V or U.
-template <bool ROWS_Q>
+// G = A V: rows are query views i and the reduction runs over database views r;
+// B is the transposed two-part operand of V.
 struct OneHotPolicy {
   static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
   static constexpr bool GEN_A = true;
-  static constexpr int GEN_WARPS = 4;  // generator thread g: row g (ROWS_Q) or column g % 64
+  static constexpr int GEN_WARPS = 4;  // generator thread g: row g of the A tile
   static constexpr int kWarpSmem = 16;
-  int64_t M, N;             // rows (query or database views), dout
+  int64_t M, N;             // rows (query views), dout
   int nkb;                  // 64-wide k-blocks of the reduction
   int64_t nq, nr;           // query views, database views
   int Np, nv;               // shapes, views per shape
   const int16_t* amT;       // [Np, nq] argmax view of (i, p), shape-major
-  const float* wT;          // [Np, nq] weight of that non-zero (ROWS_Q: c / |v_r|; else c / |u_i|)
+  const float* wT;          // [Np, nq] weight of that non-zero, c / |v_r|
   const float* gS;          // [B, Np]
   const int32_t* vquery;    // [nq] query of each view
   const float* vcoef;       // [nq] 1 / |V(x_b)| of the view's query
-  const float* kinv;        // ROWS_Q: 1/|v_r| [nr]; else 1/|u_i| [nq]
+  const float* kinv;        // 1/|v_r| [nr]
   float* C;                 // [M, N]
   struct Item {
     int64_t r0, c0;
@@ -147,19 +145,17 @@ struct OneHotPolicy {
   struct Ctx {
     float sum[TN];
   };
-  // non-zeros of one k-block prefetched by each generator thread (fast
-  // layouts: ROWS_Q with N_v a multiple of 64, one shape per k-block: thread g
-  // owns row g; !ROWS_Q with N_v >= 64, at most three shapes per 128-row tile:
-  // thread g owns column g % 64 of shapes 0 and 2 (g < 64) or shape 1); other
-  // layouts are written by warp 0 alone inside gen_store
+  // the non-zero of one k-block prefetched by each generator thread (fast
+  // layout, N_v a multiple of 64, one shape per k-block: thread g owns row g);
+  // other layouts are written by warp 0 alone inside gen_store
   bool fast;
-  int kb_per_shape;  // ROWS_Q fast layout: N_v / 64 k-blocks per shape
-  struct GenRegs {  // loaded argmax (-1: none) and weight of the thread's entries
-    int j[2];
-    float w[2];
+  int kb_per_shape;  // fast layout: N_v / 64 k-blocks per shape
+  struct GenRegs {  // loaded argmax (-1: none) and weight of the thread's entry
+    int j;
+    float w;
   };
   struct GenPos {
-    int pos[2];  // row * 64 + column in the A tile, -1 = none
+    int pos;  // row * 64 + column in the A tile, -1 = none
   };
   __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
   __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
@@ -179,69 +175,37 @@ struct OneHotPolicy {
     kb0 = c * kOneHotChunkKB;
     kb1 = min(nkb, kb0 + kOneHotChunkKB);
   }
-  __device__ __forceinline__ int a_row(const Item& it) const { return (int)it.r0; }
   // the argmax and weight lines of k-block kb + kPrefetchKB are pulled into L2
   // while this k-block's are loaded
   static constexpr int kPrefetchKB = 8;
   // issue the loads of k-block kb (their values are first read by gen_store)
   __device__ __forceinline__ void gen_load(const Item& it, int kb, int g, GenRegs& r) const {
-    r.j[0] = r.j[1] = -1;
-    r.w[0] = r.w[1] = 0.f;
+    r.j = -1;
+    r.w = 0.f;
     if (!fast) return;
     const int64_t k0 = (int64_t)kb * 64;
-    if (ROWS_Q) {
-      if (k0 >= nr) return;
-      const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
-      {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 32..37
-         // (not warp 0, which also starts the B copies)
-        const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
-        const int u = g - 32;
-        if (kp < nr && u >= 0 && u < 6) {
-          const int pp = kb_per_shape == 1 ? kb + kPrefetchKB : (kb + kPrefetchKB) / kb_per_shape;
-          const int64_t e = (int64_t)pp * nq + it.r0;
-          const int off = u < 2 ? u * 64 : (u - 2) * 32;  // first row of the line
-          if (it.r0 + off < nq) {
-            if (u < 2)
-              tc::prefetch_l2(amT + e + off);
-            else
-              tc::prefetch_l2(wT + e + off);
-          }
+    if (k0 >= nr) return;
+    const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
+    {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 32..37
+       // (not warp 0, which also starts the B copies)
+      const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
+      const int u = g - 32;
+      if (kp < nr && u >= 0 && u < 6) {
+        const int pp = kb_per_shape == 1 ? kb + kPrefetchKB : (kb + kPrefetchKB) / kb_per_shape;
+        const int64_t e = (int64_t)pp * nq + it.r0;
+        const int off = u < 2 ? u * 64 : (u - 2) * 32;  // first row of the line
+        if (it.r0 + off < nq) {
+          if (u < 2)
+            tc::prefetch_l2(amT + e + off);
+          else
+            tc::prefetch_l2(wT + e + off);
         }
       }
-      if (g < it.nr) {  // read-only for the kernel's lifetime
-        const int64_t e = (int64_t)p * nq + it.r0 + g;
-        r.j[0] = __ldg(amT + e);
-        r.w[0] = __ldg(wT + e);
-      }
-    } else {
-      if (k0 >= nq) return;
-      const int p0 = (int)it.r0 / nv;  // rows < 2^31
-      {  // three shapes x 64 query views: 128 bytes of argmax and 256 of weights each,
-         // one line per thread 32..40
-        const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
-        if (kp < nq && g >= 32 && g < 41) {
-          const int t = (g - 32) / 3, u = (g - 32) % 3;
-          const int off = u == 0 ? 0 : (u - 1) * 32;  // first query view of the line
-          if (p0 + t < Np && kp + off < nq) {
-            const int64_t e = (int64_t)(p0 + t) * nq + kp + off;
-            if (u == 0)
-              tc::prefetch_l2(amT + e);
-            else
-              tc::prefetch_l2(wT + e);
-          }
-        }
-      }
-      const int64_t i = k0 + (g & 63);
-      if (i >= nq) return;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int t = (g >> 6) + 2 * q;
-        if (t < 3 && p0 + t < Np) {
-          const int64_t e = (int64_t)(p0 + t) * nq + i;
-          r.j[q] = __ldg(amT + e);
-          r.w[q] = __ldg(wT + e);
-        }
-      }
+    }
+    if (g < it.nr) {  // read-only for the kernel's lifetime
+      const int64_t e = (int64_t)p * nq + it.r0 + g;
+      r.j = __ldg(amT + e);
+      r.w = __ldg(wT + e);
     }
   }
   // one non-zero of the A tile, hi and lo parts, 128-byte swizzled K-major layout
@@ -254,37 +218,19 @@ struct OneHotPolicy {
   }
   __device__ __forceinline__ void gen_store(const Item& it, int kb, int g, const GenRegs& r, const GenPos* prev,
                                             GenPos& now, uint8_t* a_hi, uint8_t* a_lo) const {
-    now.pos[0] = now.pos[1] = -1;
+    now.pos = -1;
     if (fast) {
-      // the tile is zero but for the entries this thread wrote into it last time
-      // (a position belongs to one thread: its row, or its column and shape)
-      if (prev) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e)
-          if (prev->pos[e] >= 0) put(a_hi, a_lo, prev->pos[e] >> 6, prev->pos[e] & 63, 0.f);
-      }
+      // the tile is zero but for the entry this thread wrote into it last time
+      // (a position belongs to one thread: its row)
+      if (prev && prev->pos >= 0) put(a_hi, a_lo, prev->pos >> 6, prev->pos & 63, 0.f);
       const int64_t k0 = (int64_t)kb * 64;
-      if (ROWS_Q) {
-        const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
-        const int j = r.j[0];
-        if (j >= 0) {  // argmax comes from the forward; stay inside the shape
-          const int64_t rr = (int64_t)p * nv + (j < nv ? j : 0);
-          if (rr >= k0 && rr < k0 + 64) now.pos[0] = g * 64 + (int)(rr - k0);
-        }
-      } else {
-        const int p0 = (int)it.r0 / nv;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int j = r.j[q];
-          if (j < 0) continue;
-          const int t = (g >> 6) + 2 * q;
-          const int64_t rr = (int64_t)(p0 + t) * nv + (j < nv ? j : 0);
-          if (rr >= it.r0 && rr < it.r0 + it.nr) now.pos[q] = (int)(rr - it.r0) * 64 + (g & 63);
-        }
+      const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
+      const int j = r.j;
+      if (j >= 0) {  // argmax comes from the forward; stay inside the shape
+        const int64_t rr = (int64_t)p * nv + (j < nv ? j : 0);
+        if (rr >= k0 && rr < k0 + 64) now.pos = g * 64 + (int)(rr - k0);
       }
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-        if (now.pos[e] >= 0) put(a_hi, a_lo, now.pos[e] >> 6, now.pos[e] & 63, r.w[e]);
+      if (now.pos >= 0) put(a_hi, a_lo, now.pos >> 6, now.pos & 63, r.w);
       return;
     }
     if (g >= 32) return;  // warp 0 writes the general layouts
@@ -296,7 +242,7 @@ struct OneHotPolicy {
     }
     __syncwarp();
     const int64_t k0 = (int64_t)kb * 64;
-    if (ROWS_Q) {
+    {
       if (k0 >= nr) return;
       const int p0 = (int)(k0 / nv), p1 = (int)min((int64_t)Np - 1, (k0 + 63) / nv);
       for (int q = 0; q < 4; ++q) {
@@ -311,23 +257,6 @@ struct OneHotPolicy {
           const int64_t rr = (int64_t)p * nv + j;
           if (rr < k0 || rr >= k0 + 64) continue;
           put(a_hi, a_lo, row, (int)(rr - k0), gS[(int64_t)b * Np + p] * cb * kinv[rr]);
-        }
-      }
-    } else {
-      if (k0 >= nq) return;
-      const int p0 = (int)(it.r0 / nv), p1 = (int)min((int64_t)Np - 1, (it.r0 + it.nr - 1) / nv);
-      for (int q = 0; q < 2; ++q) {
-        const int col = lane + 32 * q;
-        const int64_t i = k0 + col;
-        if (i >= nq) continue;
-        const int b = vquery[i];
-        const float cu = vcoef[i] * kinv[i];
-        for (int p = p0; p <= p1; ++p) {
-          int j = amT[(int64_t)p * nq + i];
-          if (j < 0 || j >= nv) j = 0;
-          const int64_t rr = (int64_t)p * nv + j;
-          if (rr < it.r0 || rr >= it.r0 + it.nr) continue;
-          put(a_hi, a_lo, (int)(rr - it.r0), col, gS[(int64_t)b * Np + p] * cu);
         }
       }
     }
@@ -645,7 +574,7 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   {
     int64_t ldr = 0;
     const Operand Vt = make_transposed(P.V, GIFT_F32, nr, dout, ldr, sc, s);  // [dout, ldr], K = database views
-    OneHotPolicy<true> pol;
+    OneHotPolicy pol;
     pol.M = nq;
     pol.N = dout;
     pol.nkb = (int)(ldr / 64);
