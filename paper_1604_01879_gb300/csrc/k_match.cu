@@ -349,6 +349,69 @@ __global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restri
 // ascending entry order), and one warp per database view sums its entries' rows of
 // U (L2-resident) in FP32 in that order: N_v times fewer multiply-adds than the dense
 // one-hot GEMM, and a result that does not depend on the launch.
+// The entries of shape p grouped by their argmax view j, ascending query view
+// within a group (a stable counting sort, one block per shape): perm[p nq + ...]
+// holds the entry indices e = p nq + i, beg[p N_v + j] the first position of
+// view j's group and cnt[p N_v + j] its size; entries without an argmax (j
+// outside [0, N_v)) are left out. Shared memory: 32 x N_v per-warp counts and
+// N_v running group ends.
+constexpr int kCsrT = 1024;
+constexpr int kCsrMaxNv = 1024;  // 33 x 1024 ints of shared memory
+__global__ __launch_bounds__(kCsrT) void k_onehot_csr(const int16_t* __restrict__ amT, int64_t nq, int nv,
+                                                      int32_t* __restrict__ perm, int64_t* __restrict__ beg,
+                                                      int32_t* __restrict__ cnt) {
+  extern __shared__ int csr_sm[];
+  int* wc = csr_sm;            // [32][nv]
+  int* base = csr_sm + 32 * nv;  // [nv]
+  const int p = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int16_t* a = amT + (int64_t)p * nq;
+  const int64_t e0 = (int64_t)p * nq;
+  for (int j = t; j < nv; j += kCsrT) base[j] = 0;
+  __syncthreads();
+  for (int64_t i = t; i < nq; i += kCsrT) {
+    const int j = a[i];
+    if (j >= 0 && j < nv) atomicAdd(&base[j], 1);
+  }
+  __syncthreads();
+  if (t == 0) {  // exclusive prefix over the views (N_v steps)
+    int run = 0;
+    for (int j = 0; j < nv; ++j) {
+      const int c = base[j];
+      cnt[(int64_t)p * nv + j] = c;
+      beg[(int64_t)p * nv + j] = e0 + run;
+      base[j] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < nq; c0 += kCsrT) {
+    const int64_t i = c0 + t;
+    int j = -1;
+    if (i < nq) {
+      j = a[i];
+      if (j < 0 || j >= nv) j = -1;
+    }
+    for (int k = t; k < 32 * nv; k += kCsrT) wc[k] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, j);
+    const int rank = __popc(peers & ((1u << lane) - 1u));  // earlier lanes of this warp with view j
+    if (j >= 0 && rank == 0) wc[w * nv + j] = __popc(peers);
+    __syncthreads();
+    for (int v = t; v < nv; v += kCsrT) {  // per view: the warps' starts, in warp order
+      int run = base[v];
+      for (int w2 = 0; w2 < 32; ++w2) {
+        const int c = wc[w2 * nv + v];
+        wc[w2 * nv + v] = run;
+        run += c;
+      }
+      base[v] = run;
+    }
+    __syncthreads();
+    if (j >= 0) perm[e0 + wc[w * nv + j] + rank] = (int32_t)(e0 + i);
+    __syncthreads();  // before the counts are cleared for the next chunk
+  }
+}
+
 // key of every (shape p, query view i) entry of the shape-major argmax: its database
 // view r = p N_v + j (nr when the view has no argmax)
 __global__ void k_onehot_keys(const int16_t* __restrict__ amT, int64_t nq, int Np, int nv,
@@ -360,19 +423,29 @@ __global__ void k_onehot_keys(const int16_t* __restrict__ amT, int64_t nq, int N
   keys[e] = (j >= 0 && j < nv) ? p * nv + j : Np * nv;
 }
 
-// H[r] = sum of wV[e] U[e mod nq] over the entries e of row r (perm[off[r]] ..
-// perm[off[r + 1]]), in ascending e: one warp per database view, lane c owns columns
+// group bounds from sorted-key offsets
+__global__ void k_off_to_groups(const int64_t* __restrict__ off, int64_t nr, int64_t* __restrict__ beg,
+                                int32_t* __restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  beg[r] = off[r];
+  cnt[r] = (int32_t)(off[r + 1] - off[r]);
+}
+
+// H[r] = sum of wV[e] U[e mod nq] over the entries e of row r (perm[beg[r]] ..
+// perm[beg[r] + cnt[r]]), in ascending e: one warp per database view, lane c owns columns
 // 4 c + 128 t, up to kHCols columns per pass (dout % 4 == 0)
 constexpr int kHCols = 512;
 __global__ __launch_bounds__(256) void k_segment_rows_sum(const float* __restrict__ U, const int32_t* __restrict__ perm,
-                                                          const int64_t* __restrict__ off,
+                                                          const int64_t* __restrict__ beg,
+                                                          const int32_t* __restrict__ cnt,
                                                           const float* __restrict__ wT, int64_t nq, int64_t nr,
                                                           int dout, float* __restrict__ H) {
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= nr) return;
   constexpr int kT = kHCols / 128;  // float4 pieces per lane and pass
-  const int64_t e0 = off[r], e1 = off[r + 1];
+  const int64_t e0 = beg[r], e1 = e0 + cnt[r];
   for (int cb = 0; cb < dout; cb += kHCols) {
     float acc[kT][4];
 #pragma unroll
@@ -600,19 +673,30 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   }
   {
     // the (shape, query view) entries grouped by their argmax database view, in
-    // ascending entry order (a stable sort), then one warp per database view
+    // ascending entry order (stable sorts), then one warp per database view
     const int64_t ne = nq * (int64_t)Np;
     GIFT_REQUIRE(ne < (int64_t)INT32_MAX && nr + 1 < (int64_t)INT32_MAX,
                  "query views x database shapes must stay below 2^31 for the gradient");
-    int32_t* keys = sc.get<int32_t>((size_t)ne);
-    k_onehot_keys<<<(unsigned)cdiv(ne, (int64_t)256), 256, 0, s>>>(amT, nq, Np, nv, keys);
-    GIFT_LAUNCHED("k_onehot_keys");
     int32_t* perm = sc.get<int32_t>((size_t)ne);
-    int32_t* skeys = sc.get<int32_t>((size_t)ne);
-    stable_sort_by_key(keys, ne, (int32_t)(nr + 1), perm, skeys, sc, s);
-    int64_t* off = sc.get<int64_t>((size_t)nr + 2);
-    bin_offsets(skeys, ne, (int32_t)(nr + 1), off, s);
-    k_segment_rows_sum<<<(unsigned)cdiv(nr, (int64_t)8), 256, 0, s>>>(P.U, perm, off, wV, nq, nr, dout, G);
+    int64_t* beg = sc.get<int64_t>((size_t)nr);
+    int32_t* cnt = sc.get<int32_t>((size_t)nr);
+    if (nv <= kCsrMaxNv) {  // per shape: a counting sort over its N_v views
+      const size_t smem = (size_t)33 * nv * sizeof(int);
+      GIFT_CUDA(cudaFuncSetAttribute(k_onehot_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_onehot_csr<<<(unsigned)Np, kCsrT, smem, s>>>(amT, nq, nv, perm, beg, cnt);
+      GIFT_LAUNCHED("k_onehot_csr");
+    } else {  // many views per shape: one radix sort of all entries by database view
+      int32_t* keys = sc.get<int32_t>((size_t)ne);
+      k_onehot_keys<<<(unsigned)cdiv(ne, (int64_t)256), 256, 0, s>>>(amT, nq, Np, nv, keys);
+      GIFT_LAUNCHED("k_onehot_keys");
+      int32_t* skeys = sc.get<int32_t>((size_t)ne);
+      stable_sort_by_key(keys, ne, (int32_t)(nr + 1), perm, skeys, sc, s);
+      int64_t* off = sc.get<int64_t>((size_t)nr + 2);
+      bin_offsets(skeys, ne, (int32_t)(nr + 1), off, s);
+      k_off_to_groups<<<(unsigned)cdiv(nr, (int64_t)256), 256, 0, s>>>(off, nr, beg, cnt);
+      GIFT_LAUNCHED("k_off_to_groups");
+    }
+    k_segment_rows_sum<<<(unsigned)cdiv(nr, (int64_t)8), 256, 0, s>>>(P.U, perm, beg, cnt, wV, nq, nr, dout, G);
     GIFT_LAUNCHED("k_segment_rows_sum");
     k_tangent<<<(unsigned)cdiv(nr, 8), 256, 0, s>>>(P.V, P.vinv, G, nr, dout, dV);
     GIFT_LAUNCHED("k_tangent");

@@ -53,13 +53,14 @@ def test_backward_matches_oracle(gpu_lib, with_w):
         assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
 
 
-@pytest.mark.parametrize("nv,dout", [(70, 16), (5, 144)])
-def test_backward_ragged_widths(gpu_lib, nv, dout):
+@pytest.mark.parametrize("nv,dout,Np", [(70, 16, 6), (5, 144, 6), (1030, 16, 3)])
+def test_backward_ragged_widths(gpu_lib, nv, dout, Np):
     """Gradients with database shapes of 70 views (more than one 64-view k-block of the query-side
-    GEMM) and of 5 views, and a projected width above 128 that is not a multiple of 128 (a partial
+    GEMM), of 5 views, and of 1,030 views (the database side grouped by one sort over all entries
+    instead of per shape), and a projected width above 128 that is not a multiple of 128 (a partial
     last column piece of the database-side segmented sum)."""
     import torch
-    Q, off, P, W, G = _tie_free(8, B=3, Np=6, nv=nv, din=32, dout=dout, margin=1e-5, counts=(7, 12, 3))
+    Q, off, P, W, G = _tie_free(8, B=3, Np=Np, nv=nv, din=32, dout=dout, margin=1e-6, counts=(7, 12, 3))
     qd, pd, Wd = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(), torch.from_numpy(W).cuda()
     S, am = gpu_lib.match_forward(qd, off, pd, Wd)
     dW, dQ, dP = gpu_lib.match_backward(qd, off, pd, Wd, torch.from_numpy(G).cuda(), am)
