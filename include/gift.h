@@ -116,11 +116,12 @@ typedef struct {
   float rescore_kernel_ms; /* tensor-core rescore kernel alone                */
   int64_t assign_rows;     /* rows quantised                                  */
   /* candidate work of the FP32 rescore (F-IF queries with rescore_r > 0): a
-     work item is (list, tile of 128 entries, tile of 128 query slots)        */
+     work item is (list, tile of 128 entries, tile of the list's query slots:
+     16, 32, 64 or 80 of them when the list has at most 80, else 128)         */
   int64_t rescore_items;      /* work items of the touched lists                */
   int64_t rescore_items_kept; /* items holding a run of one of their slots' query's
-                                 candidates: the items the rescore runs (the fused
-                                 pass of a BF16 store runs every item)          */
+                                 candidates: the items the rescore runs (the
+                                 FP32-level scan of a BF16 store runs every item) */
   int64_t cand_pairs;         /* (slot, entry) pairs whose entry's shape is a
                                  candidate of the slot's query                  */
   int64_t cand_rows;          /* entries whose shape is a candidate of some slot

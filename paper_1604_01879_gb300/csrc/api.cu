@@ -347,8 +347,9 @@ void build_lists(Index& ix_, Scratch& sc, cudaStream_t s, int32_t* pos = nullptr
 }
 
 // ------------------------------------------------------------------ query core
-// The BF16 store is the hi part of the two-part rescore rows (D > 64: the
-// fused pass splits the hi*hi products over two accumulators)
+// The BF16 store is the hi part of the two-part rescore rows: the scan runs at
+// FP32 level over every touched pair (for D > 64; a single k-block keeps the
+// BF16 scan and the separate rescore)
 bool fused_scan_ok(const Index& ix) {
   return ix.prm.storage == GIFT_BF16 && ix.list_lo != nullptr && ix.list_hi == nullptr && ix.prm.dim > 64;
 }
