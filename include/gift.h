@@ -439,8 +439,8 @@ GIFT_API gift_status gift_match_forward(const void* q, const int32_t* q_view_off
  * linear in the selected pair):
  *   dS/du_i = (v_j/|v_j| - s u_i/|u_i|) / |u_i|, dS/dv_j = (u_i/|u_i| - s v_j/|v_j|) / |v_j|,
  * each scaled by grad_S[b,p] / |V(x_b)|; dW = dU^T Q + dV^T P, dQ = dU W, dP = dV W.
- *  - grad_S: device float [Bq * Np]; argmax from the forward call; inputs as in
- *    gift_match_forward (same dtype).
+ *  - grad_S: device float [Bq * Np]; argmax from the forward call (an entry outside
+ *    [0, nv_p) contributes nothing); inputs as in gift_match_forward (same dtype).
  *  - dW: device float [d_out * d_in] or NULL (skipped; must be NULL when W is);
  *    dQ: device float [sum V_q * d_in] or NULL; dP: device float
  *    [Np * nv_p * d_in] or NULL. Outputs are FP32 and overwritten; d_out <= 1024.

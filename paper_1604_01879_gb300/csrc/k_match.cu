@@ -1,5 +1,6 @@
 // Matching score of Eq. 3 after a learned linear view projection u = W q,
-// and its gradient through the argmax view pair, on the tensor cores.
+// and its gradient through the argmax view pair: products on the tensor
+// cores, the gradient's one-hot gathers on the CUDA cores.
 //
 // Forward: U = Q W^T and V = P W^T (engine GEMMs; BF16 inputs multiply
 // exactly in one product, FP32 inputs in the two-part split), then the
@@ -9,12 +10,11 @@
 //   dU_i  = (1/|u_i|)  ( g_i - (g_i . u_i/|u_i|) u_i/|u_i| ),  g_i = sum_p c v_j*/|v_j*|
 //   dV_r  = (1/|v_r|)  ( h_r - (h_r . v_r/|v_r|) v_r/|v_r| ),  h_r = sum_{(i,p): j*=r} c u_i/|u_i|
 // (the projections use s = g-weighted cosines: sum_p c s = g_i . u_i/|u_i|).
-// G = A V is a GEMM with the one-hot matrix A[i, r] = c v-norm-weight where r
-// is the argmax view of (i, shape(r)); A is never stored: the engine's producer
-// warp writes each A tile from the argmax (transposed to shape-major) into
-// shared memory, and the tensor cores multiply it with two-part operands.
-// H = A^T U is a segmented sum on the CUDA cores over the entries sorted by
-// their argmax view (N_v times fewer multiply-adds than the dense product). Then
+// G = A V and H = A^T U, with the one-hot matrix A[i, r] = c / |v_r| (c / |u_i| for
+// H) where r is the argmax view of (i, shape(r)), are gathers on the CUDA cores: N_v
+// times fewer multiply-adds than the dense products, FP32 sums in a fixed order. A
+// block stages slices of V (of U for H) and of the shape-major argmax in shared
+// memory and adds one staged row per (query view, shape) entry. Then
 //   dW = dU^T Q + dV^T P,  dQ = dU W,  dP = dV W
 // as engine GEMMs on transposed two-part operands.
 #include "gift_internal.cuh"
@@ -116,177 +116,155 @@ __global__ __launch_bounds__(256) void k_transpose_bf16(const __nv_bfloat16* __r
   }
 }
 
-// ---------------------------------------------------------------- one-hot gradient GEMMs
-// k-blocks per accumulator chunk: 16 x 4 sub-steps x 3 products = 192 MMA steps
-constexpr int kOneHotChunkKB = 16;
+// ---------------------------------------------------------------- staged copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
-// G = A V: rows are query views i and the reduction runs over database views r;
-// B is the transposed two-part operand of V.
-struct OneHotPolicy {
-  static constexpr int TN = 128, NBUF = 4, STAGES = 3, SPLIT = 3, EB = 2;
-  static constexpr bool GEN_A = true;
-  static constexpr int GEN_WARPS = 4;  // generator thread g: row g of the A tile
-  static constexpr int kWarpSmem = 16;
-  int64_t M, N;             // rows (query views), dout
-  int nkb;                  // 64-wide k-blocks of the reduction
-  int64_t nq, nr;           // query views, database views
-  int Np, nv;               // shapes, views per shape
-  const int16_t* amT;       // [Np, nq] argmax view of (i, p), shape-major
-  const float* wT;          // [Np, nq] weight of that non-zero, c / |v_r|
-  const float* gS;          // [B, Np]
-  const int32_t* vquery;    // [nq] query of each view
-  const float* vcoef;       // [nq] 1 / |V(x_b)| of the view's query
-  const float* kinv;        // 1/|v_r| [nr]
-  float* C;                 // [M, N]
-  struct Item {
-    int64_t r0, c0;
-    int nr, nc;
-  };
-  struct Ctx {
-    float sum[TN];
-  };
-  // the non-zero of one k-block prefetched by each generator thread (fast
-  // layout, N_v a multiple of 64, one shape per k-block: thread g owns row g);
-  // other layouts are written by warp 0 alone inside gen_store
-  bool fast;
-  int kb_per_shape;  // fast layout: N_v / 64 k-blocks per shape
-  struct GenRegs {  // loaded argmax (-1: none) and weight of the thread's entry
-    int j;
-    float w;
-  };
-  struct GenPos {
-    int pos;  // row * 64 + column in the A tile, -1 = none
-  };
-  __device__ __forceinline__ int64_t n_mt() const { return cdiv(M, tc::kTM); }
-  __device__ __forceinline__ int64_t total() const { return n_mt() * cdiv(N, TN); }
-  __device__ __forceinline__ Item decode(int64_t item) const {
-    Item it;
-    const int64_t mt = n_mt();
-    const int64_t ct = item / mt, rt = item % mt;
-    it.r0 = rt * tc::kTM;
-    it.c0 = ct * TN;
-    it.nr = (int)min((int64_t)tc::kTM, M - it.r0);
-    it.nc = (int)min((int64_t)TN, N - it.c0);
-    return it;
-  }
-  __device__ __forceinline__ int nchunks(const Item&) const { return (int)cdiv(nkb, kOneHotChunkKB); }
-  __device__ __forceinline__ void chunk(const Item& it, int c, int& br, int& kb0, int& kb1) const {
-    br = (int)it.c0;
-    kb0 = c * kOneHotChunkKB;
-    kb1 = min(nkb, kb0 + kOneHotChunkKB);
-  }
-  // the argmax and weight lines of k-block kb + kPrefetchKB are pulled into L2
-  // while this k-block's are loaded
-  static constexpr int kPrefetchKB = 8;
-  // issue the loads of k-block kb (their values are first read by gen_store)
-  __device__ __forceinline__ void gen_load(const Item& it, int kb, int g, GenRegs& r) const {
-    r.j = -1;
-    r.w = 0.f;
-    if (!fast) return;
-    const int64_t k0 = (int64_t)kb * 64;
-    if (k0 >= nr) return;
-    const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
-    {  // 128 rows: 256 bytes of argmax and 512 of weights, one line per thread 32..37
-       // (not warp 0, which also starts the B copies)
-      const int64_t kp = k0 + (int64_t)kPrefetchKB * 64;
-      const int u = g - 32;
-      if (kp < nr && u >= 0 && u < 6) {
-        const int pp = kb_per_shape == 1 ? kb + kPrefetchKB : (kb + kPrefetchKB) / kb_per_shape;
-        const int64_t e = (int64_t)pp * nq + it.r0;
-        const int off = u < 2 ? u * 64 : (u - 2) * 32;  // first row of the line
-        if (it.r0 + off < nq) {
-          if (u < 2)
-            tc::prefetch_l2(amT + e + off);
-          else
-            tc::prefetch_l2(wT + e + off);
-        }
-      }
-    }
-    if (g < it.nr) {  // read-only for the kernel's lifetime
-      const int64_t e = (int64_t)p * nq + it.r0 + g;
-      r.j = __ldg(amT + e);
-      r.w = __ldg(wT + e);
-    }
-  }
-  // one non-zero of the A tile, hi and lo parts, 128-byte swizzled K-major layout
-  __device__ __forceinline__ static void put(uint8_t* a_hi, uint8_t* a_lo, int row, int col, float w) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(w);
-    const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
-    const int off = row * 128 + ((((col >> 3) ^ (row & 7))) << 4) + ((col & 7) << 1);
-    *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
-    *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
-  }
-  __device__ __forceinline__ void gen_store(const Item& it, int kb, int g, const GenRegs& r, const GenPos* prev,
-                                            GenPos& now, uint8_t* a_hi, uint8_t* a_lo) const {
-    now.pos = -1;
-    if (fast) {
-      // the tile is zero but for the entry this thread wrote into it last time
-      // (a position belongs to one thread: its row)
-      if (prev && prev->pos >= 0) put(a_hi, a_lo, prev->pos >> 6, prev->pos & 63, 0.f);
-      const int64_t k0 = (int64_t)kb * 64;
-      const int p = kb_per_shape == 1 ? kb : kb / kb_per_shape;
-      const int j = r.j;
-      if (j >= 0) {  // argmax comes from the forward; stay inside the shape
-        const int64_t rr = (int64_t)p * nv + (j < nv ? j : 0);
-        if (rr >= k0 && rr < k0 + 64) now.pos = g * 64 + (int)(rr - k0);
-      }
-      if (now.pos >= 0) put(a_hi, a_lo, now.pos >> 6, now.pos & 63, r.w);
-      return;
-    }
-    if (g >= 32) return;  // warp 0 writes the general layouts
-    const int lane = g;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    for (int o = lane * 16; o < tc::kTM * 128; o += 32 * 16) {
-      *reinterpret_cast<uint4*>(a_hi + o) = z;
-      *reinterpret_cast<uint4*>(a_lo + o) = z;
-    }
-    __syncwarp();
-    const int64_t k0 = (int64_t)kb * 64;
-    {
-      if (k0 >= nr) return;
-      const int p0 = (int)(k0 / nv), p1 = (int)min((int64_t)Np - 1, (k0 + 63) / nv);
-      for (int q = 0; q < 4; ++q) {
-        const int row = lane + 32 * q;
-        const int64_t i = it.r0 + row;
-        if (row >= it.nr) continue;
-        const int b = vquery[i];
-        const float cb = vcoef[i];
-        for (int p = p0; p <= p1; ++p) {
-          int j = amT[(int64_t)p * nq + i];
-          if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; stay inside the shape
-          const int64_t rr = (int64_t)p * nv + j;
-          if (rr < k0 || rr >= k0 + 64) continue;
-          put(a_hi, a_lo, row, (int)(rr - k0), gS[(int64_t)b * Np + p] * cb * kinv[rr]);
-        }
-      }
-    }
-  }
-  __device__ __forceinline__ void epi_begin(const Item&, Ctx& x, int, int, uint8_t*) const {
-#pragma unroll
-    for (int j = 0; j < TN; ++j) x.sum[j] = 0.f;
-  }
-  __device__ __forceinline__ void epi_chunk(const Item&, int, uint32_t taddr, Ctx& x, int, uint8_t*) const {
-#pragma unroll
-    for (int pc = 0; pc < TN / 32; ++pc) {
-      uint32_t r[32];
-      tc::tmem_ld32(taddr + pc * 32, r);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 32; ++j) x.sum[pc * 32 + j] += __uint_as_float(r[j]);
-    }
-  }
-  __device__ __forceinline__ void epi_end(const Item& it, Ctx& x, int m, uint8_t*) const {
-    if (m >= it.nr) return;
-    float* crow = C + (it.r0 + m) * N + it.c0;
-#pragma unroll
-    for (int j = 0; j < TN; ++j)
-      if (j < it.nc) crow[j] = x.sum[j];
-  }
+// ---------------------------------------------------------------- G = A V on the CUDA cores
+// G[i] = sum_p wU[p, i] V[p N_v + j(i, p)]: every (query view, shape) entry adds one
+// row of V, so the product has N_v times fewer multiply-adds than the dense one-hot
+// GEMM. A block owns 256 query views x 128 columns (16 warps of 16 views, 4 columns
+// per lane, accumulators in registers) and walks the shapes in ascending order. A
+// step stages, in shared memory (cp.async, three stages), the rows of up to 64
+// database views restricted to the block's columns together with the argmax and
+// weight of the block's query views in those shapes: a row of V leaves L2 once per
+// block instead of once per entry, and each entry is one 512-byte shared-memory
+// read. A step is up to kGShapes whole shapes of at most 64 views together, or one
+// 64-view piece of a larger shape. The steps may be split into parts (blockIdx.z)
+// whose partial sums k_tangent adds in part order: the result does not depend on
+// the launch.
+constexpr int kGT = 512, kGRows = 256, kGCols = 128, kGStages = 3, kGViews = 64, kGShapes = 8;
+constexpr int kGAmOff = kGViews * kGCols * 4;                // 32,768: argmax [kGShapes][kGRows] int16
+constexpr int kGWOff = kGAmOff + kGShapes * kGRows * 2;       // 36,864: weight [kGShapes][kGRows] float
+constexpr int kGStageBytes = kGWOff + kGShapes * kGRows * 4;  // 45,056
+static_assert(kGStageBytes % 16 == 0, "stage alignment");
+
+struct GatherSteps {
+  int spc;  // whole shapes per step (N_v <= 64); 0: 64-view pieces of one shape
+  int nch;  // pieces per shape (N_v > 64)
+  int n;    // steps
 };
 
-// shape-major argmax and one-hot weights: for every (query view i, shape p),
-// j = argmax[i, p], wU = c / |v_{p nv + j}|, wV = c / |u_i| with c = grad_S[b, p] / |V(x_b)|
-__global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, int Np, int nv,
+// shapes [p0, p0 + nps) and database views [vb, vb + nvs) of step s
+__device__ __forceinline__ void g_step(const GatherSteps& st, int s, int nv, int Np, int& p0, int& nps, int64_t& vb,
+                                       int& nvs) {
+  if (st.spc > 0) {
+    p0 = s * st.spc;
+    nps = min(st.spc, Np - p0);
+    vb = (int64_t)p0 * nv;
+    nvs = nps * nv;
+  } else {
+    p0 = s / st.nch;
+    const int ch = s - p0 * st.nch;
+    nps = 1;
+    vb = (int64_t)p0 * nv + ch * kGViews;
+    nvs = min(kGViews, nv - ch * kGViews);
+  }
+}
+
+// amT, wU: [Np, ldq] (ldq a multiple of kGRows; argmax -1 and weight 0 past nq);
+// V: [nr, dout] (16-byte aligned, dout % 4 == 0); Gp: [parts, nq, dout]
+__global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict__ V, const int16_t* __restrict__ amT,
+                                                         const float* __restrict__ wU, int64_t nq, int64_t ldq,
+                                                         int Np, int nv, int dout, GatherSteps st,
+                                                         float* __restrict__ Gp) {
+  extern __shared__ __align__(16) uint8_t g_sm[];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * kGRows;
+  const int c0 = blockIdx.y * kGCols;
+  const int part = blockIdx.z, parts = gridDim.z;
+  const int s0 = (int)((int64_t)st.n * part / parts), s1 = (int)((int64_t)st.n * (part + 1) / parts);
+  auto issue = [&](int s) {
+    if (s < s1) {
+      uint8_t* buf = g_sm + ((s - s0) % kGStages) * kGStageBytes;
+      int p0, nps, nvs;
+      int64_t vb;
+      g_step(st, s, nv, Np, p0, nps, vb, nvs);
+      for (int t = tid; t < nvs * 32; t += kGT) {  // rows of V, 16-byte pieces of the column slice
+        const int row = t >> 5, q = t & 31, c = c0 + 4 * q;
+        if (c < dout) cp_async16(buf + (row * kGCols + 4 * q) * 4, V + (vb + row) * dout + c);
+      }
+      for (int t = tid; t < nps * 96; t += kGT) {  // per shape: 32 pieces of argmax, 64 of weight
+        const int ps = t / 96, q = t - ps * 96;
+        const int64_t e = (int64_t)(p0 + ps) * ldq + i0;
+        if (q < 32)
+          cp_async16(buf + kGAmOff + (ps * kGRows + 8 * q) * 2, amT + e + 8 * q);
+        else
+          cp_async16(buf + kGWOff + (ps * kGRows + 4 * (q - 32)) * 4, wU + e + 4 * (q - 32));
+      }
+    }
+    cp_async_commit();  // empty groups past the last step keep the wait count uniform
+  };
+  float acc[16][4];
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[k][q] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kGStages - 1; ++k) issue(s0 + k);
+  for (int s = s0; s < s1; ++s) {
+    cp_async_wait<kGStages - 2>();  // this step's copies have landed ...
+    __syncthreads();                // ... for every thread, and the step before is done with its buffer
+    issue(s + kGStages - 1);
+    const uint8_t* buf = g_sm + ((s - s0) % kGStages) * kGStageBytes;
+    const float4* vs = reinterpret_cast<const float4*>(buf);
+    int p0, nps, nvs;
+    int64_t vb;
+    g_step(st, s, nv, Np, p0, nps, vb, nvs);
+    for (int ps = 0; ps < nps; ++ps) {
+      // the warp's 16 argmax values and weights (broadcast reads)
+      const uint4* ap = reinterpret_cast<const uint4*>(buf + kGAmOff + (ps * kGRows + 16 * w) * 2);
+      const float4* wp = reinterpret_cast<const float4*>(buf + kGWOff + (ps * kGRows + 16 * w) * 4);
+      const uint4 a0 = ap[0], a1 = ap[1];
+      const uint32_t au[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float wt[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = wp[q];
+        wt[4 * q] = f.x;
+        wt[4 * q + 1] = f.y;
+        wt[4 * q + 2] = f.z;
+        wt[4 * q + 3] = f.w;
+      }
+      const int base = (int)((int64_t)(p0 + ps) * nv - vb);  // staged row of view 0 of the shape
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int j = (int)(int16_t)((k & 1) ? (au[k >> 1] >> 16) : (au[k >> 1] & 0xffffu));
+        const int loc = base + j;
+        if (j >= 0 && (unsigned)loc < (unsigned)nvs) {  // uniform over the warp
+          const float4 x = vs[loc * 32 + lane];
+          acc[k][0] = fmaf(wt[k], x.x, acc[k][0]);
+          acc[k][1] = fmaf(wt[k], x.y, acc[k][1]);
+          acc[k][2] = fmaf(wt[k], x.z, acc[k][2]);
+          acc[k][3] = fmaf(wt[k], x.w, acc[k][3]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  const int c = c0 + 4 * lane;
+  if (c >= dout) return;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t i = i0 + 16 * w + k;
+    if (i < nq)
+      *reinterpret_cast<float4*>(Gp + ((int64_t)part * nq + i) * dout + c) =
+          make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+  }
+}
+
+// shape-major argmax and one-hot weights, rows padded to ldq: for every (query view i,
+// shape p), j = argmax[i, p], wU = c / |v_{p nv + j}|, wV = c / |u_i| with
+// c = grad_S[b, p] / |V(x_b)|; j = -1 (no entry, zero weights) for an argmax outside
+// [0, N_v) and for the padding views nq <= i < ldq
+__global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, int64_t ldq, int Np, int nv,
                               const int32_t* __restrict__ vquery, const float* __restrict__ vcoef,
                               const float* __restrict__ gS, const float* __restrict__ vinv,
                               const float* __restrict__ uinv, int16_t* __restrict__ amT, float* __restrict__ wU,
@@ -300,14 +278,19 @@ __global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, in
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int64_t p = p0 + k, i = i0 + threadIdx.x;
-    if (i >= nq || p >= Np) continue;
-    int j = t[threadIdx.x][k];
-    const int16_t js = (int16_t)j;
-    if (j < 0 || j >= nv) j = 0;  // argmax comes from the forward; stay inside the shape
+    if (i >= ldq || p >= Np) continue;
+    const int j = i < nq ? (int)t[threadIdx.x][k] : -1;
+    const int64_t e = p * ldq + i;
+    if (j < 0 || j >= nv) {
+      amT[e] = -1;
+      wU[e] = 0.f;
+      wV[e] = 0.f;
+      continue;
+    }
     const float c = gS[(int64_t)vquery[i] * Np + p] * vcoef[i];
-    amT[p * nq + i] = js;
-    wU[p * nq + i] = c * vinv[p * nv + j];
-    wV[p * nq + i] = c * uinv[i];
+    amT[e] = (int16_t)j;
+    wU[e] = c * vinv[p * nv + j];
+    wV[e] = c * uinv[i];
   }
 }
 
@@ -319,21 +302,27 @@ __global__ void k_view_coef(const int32_t* __restrict__ vquery, const int32_t* _
   coef[i] = 1.f / (float)(qoff[b + 1] - qoff[b]);
 }
 
-// out_r = inv_r (g_r - (g_r . x_r inv_r) x_r inv_r): the gradient through x / |x| (warp per row)
+// out_r = inv_r (g_r - (g_r . x_r inv_r) x_r inv_r): the gradient through x / |x| (warp per
+// row); g_r is the sum of `parts` partial rows G[s pstride + r dout], added in part order
 __global__ void k_tangent(const float* __restrict__ X, const float* __restrict__ inv, const float* __restrict__ G,
-                          int64_t n, int dout, float* __restrict__ out) {
+                          int parts, int64_t pstride, int64_t n, int dout, float* __restrict__ out) {
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= n) return;
   const float iv = inv[r];
   const float* x = X + r * dout;
   const float* g = G + r * dout;
+  auto g_at = [&](int d) {
+    float v = g[d];
+    for (int s = 1; s < parts; ++s) v += g[s * pstride + d];
+    return v;
+  };
   float dot = 0.f;
-  for (int d = lane; d < dout; d += 32) dot = fmaf(x[d], g[d], dot);
+  for (int d = lane; d < dout; d += 32) dot = fmaf(x[d], g_at(d), dot);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   const float t = dot * iv * iv;
-  for (int d = lane; d < dout; d += 32) out[r * dout + d] = iv * (g[d] - t * x[d]);
+  for (int d = lane; d < dout; d += 32) out[r * dout + d] = iv * (g_at(d) - t * x[d]);
 }
 
 __global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restrict__ vq) {
@@ -345,27 +334,147 @@ __global__ void k_view_query(const int32_t* __restrict__ qoff, int32_t* __restri
 // Every database view's row of H is the weighted sum of the query views whose
 // argmax in its shape is that view:
 //   H[p N_v + j] = sum_{i : j(i, p) = j} wV[p, i] U[i]
-// The (shape, query view) entries are sorted by that database view (stably, so in
-// ascending entry order), and one warp per database view sums its entries' rows of
-// U (L2-resident) in FP32 in that order: N_v times fewer multiply-adds than the dense
-// one-hot GEMM, and a result that does not depend on the launch.
-// The entries of shape p grouped by their argmax view j, ascending query view
-// within a group (a stable counting sort, one block per shape): perm[p nq + ...]
-// holds the entry indices e = p nq + i, beg[p N_v + j] the first position of
-// view j's group and cnt[p N_v + j] its size; entries without an argmax (j
-// outside [0, N_v)) are left out. Shared memory: 32 x N_v per-warp counts and
-// N_v running group ends.
+// (N_v times fewer multiply-adds than the dense one-hot GEMM), summed in ascending
+// query view order: a result that does not depend on the launch.
+//
+// Shapes of up to 1,024 views: the entries of each shape are grouped by their argmax
+// view (a counting sort per shape in shared memory), then one warp per database view
+// sums its entries' rows of U, gathered from L2 (U is L2-resident).
+// Larger shapes (the sort's per-warp counts would not fit in shared memory): a block
+// owns 256 database views (flattened; at most kHShapes shapes, N_v >= 16) x 128
+// columns, warp w the 16 views from 16 w on, 4 columns per lane with the accumulators
+// in registers. A step stages 64 query views' rows of U (the column slice) and the
+// argmax and weight of those query views in the block's shapes (cp.async, three
+// stages); a warp finds the query views of each of its database views with two
+// ballots over the staged argmax and adds their staged rows.
+constexpr int kHT = 512, kHRows = 256, kHQ = 64, kHStages = 3, kHShapes = 18;
+constexpr int kHMinNv = 16;                                  // kHRows / kHMinNv + 2 <= kHShapes
+constexpr int kHAmOff = kHQ * kGCols * 4;                    // 32,768: argmax [kHShapes][kHQ] int16
+constexpr int kHWOff = kHAmOff + kHShapes * kHQ * 2;         // 35,072: weight [kHShapes][kHQ] float
+constexpr int kHStageBytes = kHWOff + kHShapes * kHQ * 4;    // 39,680
+static_assert(kHStageBytes % 16 == 0 && kHWOff % 16 == 0, "stage alignment");
+static_assert(kHRows / kHMinNv + 2 <= kHShapes, "shapes of one block");
+
+// amT, wV: [Np, ldq] (ldq a multiple of kHQ; argmax -1 past nq); U: [nq, dout]
+// (16-byte aligned, dout % 4 == 0); H: [nr, dout]
+__global__ __launch_bounds__(kHT, 1) void k_gather_entries(const float* __restrict__ U, const int16_t* __restrict__ amT,
+                                                           const float* __restrict__ wV, int64_t nq, int64_t ldq,
+                                                           int64_t nr, int nv, int dout, float* __restrict__ H) {
+  extern __shared__ __align__(16) uint8_t h_sm[];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * kHRows;
+  const int c0 = blockIdx.y * kGCols;
+  const int64_t ps0 = r0 / nv;
+  const int ns = (int)((min(r0 + kHRows, nr) - 1) / nv - ps0 + 1);  // shapes of the block (<= kHShapes)
+  const int nsteps = (int)cdiv(nq, (int64_t)kHQ);
+  auto issue = [&](int s) {
+    if (s < nsteps) {
+      uint8_t* buf = h_sm + (s % kHStages) * kHStageBytes;
+      const int64_t i0 = (int64_t)s * kHQ;
+      for (int t = tid; t < kHQ * 32; t += kHT) {  // rows of U, 16-byte pieces of the column slice
+        const int row = t >> 5, q = t & 31, c = c0 + 4 * q;
+        if (c < dout && i0 + row < nq) cp_async16(buf + (row * kGCols + 4 * q) * 4, U + (i0 + row) * dout + c);
+      }
+      for (int t = tid; t < ns * 24; t += kHT) {  // per shape: 8 pieces of argmax, 16 of weight
+        const int ps = t / 24, q = t - ps * 24;
+        const int64_t e = (ps0 + ps) * ldq + i0;
+        if (q < 8)
+          cp_async16(buf + kHAmOff + (ps * kHQ + 8 * q) * 2, amT + e + 8 * q);
+        else
+          cp_async16(buf + kHWOff + (ps * kHQ + 4 * (q - 8)) * 4, wV + e + 4 * (q - 8));
+      }
+    }
+    cp_async_commit();  // empty groups past the last step keep the wait count uniform
+  };
+  // shape and view of the warp's first database view
+  const int64_t rw = r0 + 16 * w;
+  const int pw0 = (int)(rw / nv - ps0), jw0 = (int)(rw % nv);
+  float acc[16][4];
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[k][q] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kHStages - 1; ++k) issue(k);
+  for (int s = 0; s < nsteps; ++s) {
+    cp_async_wait<kHStages - 2>();  // this step's copies have landed ...
+    __syncthreads();                // ... for every thread, and the step before is done with its buffer
+    issue(s + kHStages - 1);
+    const uint8_t* buf = h_sm + (s % kHStages) * kHStageBytes;
+    const float4* us = reinterpret_cast<const float4*>(buf);
+    const int16_t* as = reinterpret_cast<const int16_t*>(buf + kHAmOff);
+    const float* ws = reinterpret_cast<const float*>(buf + kHWOff);
+    int ps = pw0, j = jw0, cur = -1;
+    int ja = -1, jb = -1;
+    float wa = 0.f, wb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (rw + k < nr) {  // uniform over the warp
+        if (ps != cur) {  // lane l holds query views l and l + 32 of the step
+          cur = ps;
+          ja = as[ps * kHQ + lane];
+          jb = as[ps * kHQ + 32 + lane];
+          wa = ws[ps * kHQ + lane];
+          wb = ws[ps * kHQ + 32 + lane];
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ja == j);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const float wk = __shfl_sync(0xffffffffu, wa, l);
+          const float4 x = us[l * 32 + lane];
+          acc[k][0] = fmaf(wk, x.x, acc[k][0]);
+          acc[k][1] = fmaf(wk, x.y, acc[k][1]);
+          acc[k][2] = fmaf(wk, x.z, acc[k][2]);
+          acc[k][3] = fmaf(wk, x.w, acc[k][3]);
+        }
+        m = __ballot_sync(0xffffffffu, jb == j);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const float wk = __shfl_sync(0xffffffffu, wb, l);
+          const float4 x = us[(l + 32) * 32 + lane];
+          acc[k][0] = fmaf(wk, x.x, acc[k][0]);
+          acc[k][1] = fmaf(wk, x.y, acc[k][1]);
+          acc[k][2] = fmaf(wk, x.z, acc[k][2]);
+          acc[k][3] = fmaf(wk, x.w, acc[k][3]);
+        }
+      }
+      if (++j == nv) {
+        j = 0;
+        ++ps;
+      }
+    }
+  }
+  cp_async_wait<0>();
+  const int c = c0 + 4 * lane;
+  if (c >= dout) return;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t r = rw + k;
+    if (r < nr)
+      *reinterpret_cast<float4*>(H + r * dout + c) = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+  }
+}
+
+// The entries of shape p grouped by their argmax view j, ascending query view within a
+// group (a stable counting sort, one block per shape): perm[p ld + ...] holds the entry
+// indices e = p ld + i, beg[p N_v + j] the first position of view j's group and
+// cnt[p N_v + j] its size; entries without an argmax (j = -1) are left out. Shared
+// memory: 32 x N_v per-warp counts and N_v running group ends.
 constexpr int kCsrT = 1024;
 constexpr int kCsrMaxNv = 1024;  // 33 x 1024 ints of shared memory
-__global__ __launch_bounds__(kCsrT) void k_onehot_csr(const int16_t* __restrict__ amT, int64_t nq, int nv,
+static_assert(kCsrMaxNv >= kHMinNv, "the staged gather takes the larger shapes");
+__global__ __launch_bounds__(kCsrT) void k_onehot_csr(const int16_t* __restrict__ amT, int64_t nq, int64_t ld,
+                                                      int nv,
                                                       int32_t* __restrict__ perm, int64_t* __restrict__ beg,
                                                       int32_t* __restrict__ cnt) {
   extern __shared__ int csr_sm[];
   int* wc = csr_sm;            // [32][nv]
   int* base = csr_sm + 32 * nv;  // [nv]
   const int p = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int16_t* a = amT + (int64_t)p * nq;
-  const int64_t e0 = (int64_t)p * nq;
+  const int16_t* a = amT + (int64_t)p * ld;
+  const int64_t e0 = (int64_t)p * ld;
   for (int j = t; j < nv; j += kCsrT) base[j] = 0;
   __syncthreads();
   for (int64_t i = t; i < nq; i += kCsrT) {
@@ -412,34 +521,14 @@ __global__ __launch_bounds__(kCsrT) void k_onehot_csr(const int16_t* __restrict_
   }
 }
 
-// key of every (shape p, query view i) entry of the shape-major argmax: its database
-// view r = p N_v + j (nr when the view has no argmax)
-__global__ void k_onehot_keys(const int16_t* __restrict__ amT, int64_t nq, int Np, int nv,
-                              int32_t* __restrict__ keys) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nq * (int64_t)Np) return;
-  const int p = (int)(e / nq);
-  const int j = amT[e];
-  keys[e] = (j >= 0 && j < nv) ? p * nv + j : Np * nv;
-}
-
-// group bounds from sorted-key offsets
-__global__ void k_off_to_groups(const int64_t* __restrict__ off, int64_t nr, int64_t* __restrict__ beg,
-                                int32_t* __restrict__ cnt) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nr) return;
-  beg[r] = off[r];
-  cnt[r] = (int32_t)(off[r + 1] - off[r]);
-}
-
-// H[r] = sum of wV[e] U[e mod nq] over the entries e of row r (perm[beg[r]] ..
+// H[r] = sum of wV[e] U[e mod ld] over the entries e of row r (perm[beg[r]] ..
 // perm[beg[r] + cnt[r]]), in ascending e: one warp per database view, lane c owns columns
 // 4 c + 128 t, up to kHCols columns per pass (dout % 4 == 0)
 constexpr int kHCols = 512;
 __global__ __launch_bounds__(256) void k_segment_rows_sum(const float* __restrict__ U, const int32_t* __restrict__ perm,
                                                           const int64_t* __restrict__ beg,
                                                           const int32_t* __restrict__ cnt,
-                                                          const float* __restrict__ wT, int64_t nq, int64_t nr,
+                                                          const float* __restrict__ wT, int64_t ld, int64_t nr,
                                                           int dout, float* __restrict__ H) {
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -458,7 +547,7 @@ __global__ __launch_bounds__(256) void k_segment_rows_sum(const float* __restric
       float wl = 0.f;
       if (lane < n) {
         const int32_t e = perm[eb + lane];
-        src = (int64_t)(e % nq) * dout;
+        src = (int64_t)(e % ld) * dout;
         wl = wT[e];
       }
 #pragma unroll 4
@@ -635,70 +724,81 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   float* vcoef = sc.get<float>(nq);
   k_view_coef<<<(unsigned)cdiv(nq, 256), 256, 0, s>>>(vquery, d_qoff, nq, vcoef);
   GIFT_LAUNCHED("k_view_coef");
-  int16_t* amT = sc.get<int16_t>((size_t)nq * Np);
-  float* wU = sc.get<float>((size_t)nq * Np);
-  float* wV = sc.get<float>((size_t)nq * Np);
-  k_onehot_prep<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(nq, 32)), dim3(32, 8), 0, s>>>(
-      argmax, nq, Np, nv, vquery, vcoef, gS, P.vinv, P.uinv, amT, wU, wV);
+  // shape-major argmax and weights, query views padded to a multiple of the gather blocks
+  const int64_t ldq = cdiv(nq, (int64_t)kGRows) * kGRows;
+  int16_t* amT = sc.get<int16_t>((size_t)ldq * Np);
+  float* wU = sc.get<float>((size_t)ldq * Np);
+  float* wV = sc.get<float>((size_t)ldq * Np);
+  k_onehot_prep<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(ldq, 32)), dim3(32, 8), 0, s>>>(
+      argmax, nq, ldq, Np, nv, vquery, vcoef, gS, P.vinv, P.uinv, amT, wU, wV);
   GIFT_LAUNCHED("k_onehot_prep");
-  float* G = sc.get<float>((size_t)std::max(nq, nr) * dout);  // G = A V, then H = A^T U
   GIFT_REQUIRE(dout % 4 == 0, "projected width must be a multiple of 4");
+  // the staged copies read 16-byte pieces of the rows of U and V
+  auto aligned16 = [&](float* x, int64_t n) {
+    if (reinterpret_cast<uintptr_t>(x) % 16 == 0) return x;
+    float* y = sc.get<float>((size_t)n);
+    GIFT_CUDA(cudaMemcpyAsync(y, x, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return y;
+  };
+  const float* U16 = aligned16(P.U, nq * dout);
+  const float* V16 = aligned16(P.V, nr * dout);
   const int sms = device_sm_count();
-  {
-    int64_t ldr = 0;
-    const Operand Vt = make_transposed(P.V, GIFT_F32, nr, dout, ldr, sc, s);  // [dout, ldr], K = database views
-    OneHotPolicy pol;
-    pol.M = nq;
-    pol.N = dout;
-    pol.nkb = (int)(ldr / 64);
-    pol.nq = nq;
-    pol.nr = nr;
-    pol.Np = Np;
-    pol.nv = nv;
-    pol.amT = amT;
-    pol.gS = gS;
-    pol.vquery = vquery;
-    pol.vcoef = vcoef;
-    pol.kinv = P.vinv;
-    pol.wT = wU;
-    pol.C = G;
-    pol.fast = nv % 64 == 0 && nr < ((int64_t)1 << 31);
-    pol.kb_per_shape = nv / 64;
-    const CUtensorMap tB = make_tmap_bf16(Vt.hi, Vt.rows_alloc, ldr, 128);
-    const CUtensorMap tB2 = make_tmap_bf16(Vt.lo, Vt.rows_alloc, ldr, 128);
-    tc::launch_engine(tB, tB, tB2, tB2, pol, err, (int)std::min<int64_t>(sms, cdiv(nq, tc::kTM) * cdiv(dout, 128)),
-                      s);
-    k_tangent<<<(unsigned)cdiv(nq, 8), 256, 0, s>>>(P.U, P.uinv, G, nq, dout, dU);
+  {  // G = A V, then dU
+    GatherSteps st;
+    if (nv <= kGViews) {
+      st.spc = std::min(kGShapes, kGViews / nv);
+      st.nch = 1;
+      st.n = (int)cdiv((int64_t)Np, (int64_t)st.spc);
+    } else {
+      st.spc = 0;
+      st.nch = (int)cdiv((int64_t)nv, (int64_t)kGViews);
+      GIFT_REQUIRE((int64_t)Np * st.nch < INT32_MAX, "too many database views for the gradient");
+      st.n = Np * st.nch;
+    }
+    // parts of the step range: a block's time is ~ steps / parts, the launch takes
+    // ceil(blocks x parts / SMs) rounds of one block per SM; partial rows cost a little
+    const int64_t units = cdiv(nq, (int64_t)kGRows) * cdiv((int64_t)dout, (int64_t)kGCols);
+    int parts = 1;
+    double best = 1e30;
+    for (int pc = 1; pc <= 8 && pc <= st.n; ++pc) {
+      const double cost = (double)cdiv(units * pc, (int64_t)sms) / pc + 0.02 * pc;
+      if (cost < best - 1e-9) {
+        best = cost;
+        parts = pc;
+      }
+    }
+    float* Gp = sc.get<float>((size_t)parts * nq * dout);
+    const size_t smem = (size_t)kGStages * kGStageBytes;
+    GIFT_CUDA(cudaFuncSetAttribute(k_gather_views, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const dim3 grid((unsigned)cdiv(nq, (int64_t)kGRows), (unsigned)cdiv((int64_t)dout, (int64_t)kGCols),
+                    (unsigned)parts);
+    k_gather_views<<<grid, kGT, smem, s>>>(V16, amT, wU, nq, ldq, Np, nv, dout, st, Gp);
+    GIFT_LAUNCHED("k_gather_views");
+    k_tangent<<<(unsigned)cdiv(nq, 8), 256, 0, s>>>(P.U, P.uinv, Gp, parts, nq * dout, nq, dout, dU);
     GIFT_LAUNCHED("k_tangent");
   }
-  {
-    // the (shape, query view) entries grouped by their argmax database view, in
-    // ascending entry order (stable sorts), then one warp per database view
-    const int64_t ne = nq * (int64_t)Np;
-    GIFT_REQUIRE(ne < (int64_t)INT32_MAX && nr + 1 < (int64_t)INT32_MAX,
-                 "query views x database shapes must stay below 2^31 for the gradient");
-    int32_t* perm = sc.get<int32_t>((size_t)ne);
-    int64_t* beg = sc.get<int64_t>((size_t)nr);
-    int32_t* cnt = sc.get<int32_t>((size_t)nr);
-    if (nv <= kCsrMaxNv) {  // per shape: a counting sort over its N_v views
+  {  // H = A^T U, then dV
+    float* H = sc.get<float>((size_t)nr * dout);
+    if (nv <= kCsrMaxNv) {  // entries grouped per shape, then one warp per database view
+      const int64_t ne = ldq * (int64_t)Np;
+      GIFT_REQUIRE(ne < (int64_t)INT32_MAX, "query views x database shapes must stay below 2^31 for the gradient");
+      int32_t* perm = sc.get<int32_t>((size_t)ne);
+      int64_t* beg = sc.get<int64_t>((size_t)nr);
+      int32_t* cnt = sc.get<int32_t>((size_t)nr);
       const size_t smem = (size_t)33 * nv * sizeof(int);
       GIFT_CUDA(cudaFuncSetAttribute(k_onehot_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_onehot_csr<<<(unsigned)Np, kCsrT, smem, s>>>(amT, nq, nv, perm, beg, cnt);
+      k_onehot_csr<<<(unsigned)Np, kCsrT, smem, s>>>(amT, nq, ldq, nv, perm, beg, cnt);
       GIFT_LAUNCHED("k_onehot_csr");
-    } else {  // many views per shape: one radix sort of all entries by database view
-      int32_t* keys = sc.get<int32_t>((size_t)ne);
-      k_onehot_keys<<<(unsigned)cdiv(ne, (int64_t)256), 256, 0, s>>>(amT, nq, Np, nv, keys);
-      GIFT_LAUNCHED("k_onehot_keys");
-      int32_t* skeys = sc.get<int32_t>((size_t)ne);
-      stable_sort_by_key(keys, ne, (int32_t)(nr + 1), perm, skeys, sc, s);
-      int64_t* off = sc.get<int64_t>((size_t)nr + 2);
-      bin_offsets(skeys, ne, (int32_t)(nr + 1), off, s);
-      k_off_to_groups<<<(unsigned)cdiv(nr, (int64_t)256), 256, 0, s>>>(off, nr, beg, cnt);
-      GIFT_LAUNCHED("k_off_to_groups");
+      k_segment_rows_sum<<<(unsigned)cdiv(nr, (int64_t)8), 256, 0, s>>>(U16, perm, beg, cnt, wV, ldq, nr, dout, H);
+      GIFT_LAUNCHED("k_segment_rows_sum");
+    } else {  // larger shapes: the staged gather
+      const size_t smem = (size_t)kHStages * kHStageBytes;
+      GIFT_CUDA(cudaFuncSetAttribute(k_gather_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const dim3 grid((unsigned)cdiv(nr, (int64_t)kHRows), (unsigned)cdiv((int64_t)dout, (int64_t)kGCols));
+      k_gather_entries<<<grid, kHT, smem, s>>>(U16, amT, wV, nq, ldq, nr, nv, dout, H);
+      GIFT_LAUNCHED("k_gather_entries");
     }
-    k_segment_rows_sum<<<(unsigned)cdiv(nr, (int64_t)8), 256, 0, s>>>(P.U, perm, beg, cnt, wV, nq, nr, dout, G);
-    GIFT_LAUNCHED("k_segment_rows_sum");
-    k_tangent<<<(unsigned)cdiv(nr, 8), 256, 0, s>>>(P.V, P.vinv, G, nr, dout, dV);
+    k_tangent<<<(unsigned)cdiv(nr, 8), 256, 0, s>>>(P.V, P.vinv, H, 1, 0, nr, dout, dV);
     GIFT_LAUNCHED("k_tangent");
   }
   if (!W) return;

@@ -53,12 +53,14 @@ def test_backward_matches_oracle(gpu_lib, with_w):
         assert np.allclose(dW.cpu().numpy(), rW, rtol=1e-4, atol=1e-5 * np.abs(rW).max())
 
 
-@pytest.mark.parametrize("nv,dout,Np", [(70, 16, 6), (5, 144, 6), (1030, 16, 3)])
+@pytest.mark.parametrize("nv,dout,Np", [(70, 16, 6), (5, 144, 6), (1030, 16, 3), (17, 48, 23), (16, 16, 9),
+                                         (15, 32, 9)])
 def test_backward_ragged_widths(gpu_lib, nv, dout, Np):
-    """Gradients with database shapes of 70 views (more than one 64-view k-block of the query-side
-    GEMM), of 5 views, and of 1,030 views (the database side grouped by one sort over all entries
-    instead of per shape), and a projected width above 128 that is not a multiple of 128 (a partial
-    last column piece of the database-side segmented sum)."""
+    """Gradients with database shapes of 70 and 1,030 views (two and 17 staged 64-view pieces per
+    shape on the query side; the 1,030-view shapes take the staged database-side gather instead of
+    the per-shape grouping), of 5 views (eight whole shapes per staged step), of 15 to 17 views, and
+    projected widths that leave a partial last 128-column slice (16, 48, 144), with the query-side
+    step range split into several parts."""
     import torch
     Q, off, P, W, G = _tie_free(8, B=3, Np=Np, nv=nv, din=32, dout=dout, margin=1e-6, counts=(7, 12, 3))
     qd, pd, Wd = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(), torch.from_numpy(W).cuda()
