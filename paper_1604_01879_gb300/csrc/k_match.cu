@@ -133,24 +133,33 @@ __device__ __forceinline__ void cp_async_wait() {
 // GEMM. A block owns 256 query views x 128 columns (16 warps of 16 views, 4 columns
 // per lane, accumulators in registers) and walks the shapes in ascending order. A
 // step stages, in shared memory (cp.async, three stages), the rows of up to 64
-// database views restricted to the block's columns together with the argmax and
-// weight of the block's query views in those shapes: a row of V leaves L2 once per
-// block instead of once per entry, and each entry is one 512-byte shared-memory
-// read. A step is up to kGShapes whole shapes of at most 64 views together, or one
-// 64-view piece of a larger shape. The steps may be split into parts (blockIdx.z)
-// whose partial sums k_tangent adds in part order: the result does not depend on
-// the launch.
+// database views restricted to the block's columns together with the entry records
+// of the block's query views in those shapes: a row of V leaves L2 once per block
+// instead of once per entry, and each entry is one broadcast record read, one
+// 512-byte shared-memory read and four multiply-adds. A step is up to kGShapes whole
+// shapes of at most 64 views together, or one 64-view piece of a larger shape. The
+// steps may be split into parts (blockIdx.z) whose partial sums k_tangent adds in
+// part order: the result does not depend on the launch.
 constexpr int kGT = 512, kGRows = 256, kGCols = 128, kGStages = 3, kGViews = 64, kGShapes = 8;
-constexpr int kGAmOff = kGViews * kGCols * 4;                // 32,768: argmax [kGShapes][kGRows] int16
-constexpr int kGWOff = kGAmOff + kGShapes * kGRows * 2;       // 36,864: weight [kGShapes][kGRows] float
-constexpr int kGStageBytes = kGWOff + kGShapes * kGRows * 4;  // 45,056
-static_assert(kGStageBytes % 16 == 0, "stage alignment");
+constexpr int kGRecOff = (kGViews + 1) * kGCols * 4;            // 33,280: V rows + one zero row
+constexpr int kGStageBytes = kGRecOff + kGShapes * kGRows * 8;  // 49,664: + records [kGShapes][kGRows]
+static_assert(kGStageBytes % 16 == 0 && kGRecOff % 16 == 0, "stage alignment");
 
 struct GatherSteps {
   int spc;  // whole shapes per step (N_v <= 64); 0: 64-view pieces of one shape
   int nch;  // pieces per shape (N_v > 64)
   int n;    // steps
 };
+
+// entry record of (query view i, shape p) for the gather: the weight wU and
+//  - whole-shape steps (spc > 0): the staged row of the argmax view in float4
+//    units, ((p mod spc) N_v + j) * 32, or the zero row kGViews * 32 (weight 0)
+//    when the entry has no argmax;
+//  - 64-view pieces (spc = 0): the argmax view j, or -1.
+__device__ __forceinline__ float2 g_record(int spc, int64_t p, int nv, int j, float wu) {
+  if (spc > 0) return make_float2(wu, __int_as_float(j >= 0 ? ((int)(p % spc) * nv + j) * 32 : kGViews * 32));
+  return make_float2(wu, __int_as_float(j));
+}
 
 // shapes [p0, p0 + nps) and database views [vb, vb + nvs) of step s
 __device__ __forceinline__ void g_step(const GatherSteps& st, int s, int nv, int Np, int& p0, int& nps, int64_t& vb,
@@ -169,18 +178,28 @@ __device__ __forceinline__ void g_step(const GatherSteps& st, int s, int nv, int
   }
 }
 
-// amT, wU: [Np, ldq] (ldq a multiple of kGRows; argmax -1 and weight 0 past nq);
+// one entry: acc += w * staged row
+__device__ __forceinline__ void g_add(float (&acc)[4], float w, const float4 x) {
+  acc[0] = fmaf(w, x.x, acc[0]);
+  acc[1] = fmaf(w, x.y, acc[1]);
+  acc[2] = fmaf(w, x.z, acc[2]);
+  acc[3] = fmaf(w, x.w, acc[3]);
+}
+
+// gR: [Np, ldq] entry records (ldq a multiple of kGRows; no entry past nq);
 // V: [nr, dout] (16-byte aligned, dout % 4 == 0); Gp: [parts, nq, dout]
-__global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict__ V, const int16_t* __restrict__ amT,
-                                                         const float* __restrict__ wU, int64_t nq, int64_t ldq,
-                                                         int Np, int nv, int dout, GatherSteps st,
-                                                         float* __restrict__ Gp) {
+__global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict__ V, const float2* __restrict__ gR,
+                                                         int64_t nq, int64_t ldq, int Np, int nv, int dout,
+                                                         GatherSteps st, float* __restrict__ Gp) {
   extern __shared__ __align__(16) uint8_t g_sm[];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int64_t i0 = (int64_t)blockIdx.x * kGRows;
   const int c0 = blockIdx.y * kGCols;
   const int part = blockIdx.z, parts = gridDim.z;
   const int s0 = (int)((int64_t)st.n * part / parts), s1 = (int)((int64_t)st.n * (part + 1) / parts);
+  for (int t = tid; t < kGStages * 32; t += kGT)  // the zero row of every stage (never a copy target)
+    *reinterpret_cast<float4*>(g_sm + (t >> 5) * kGStageBytes + kGViews * kGCols * 4 + (t & 31) * 16) =
+        make_float4(0.f, 0.f, 0.f, 0.f);
   auto issue = [&](int s) {
     if (s < s1) {
       uint8_t* buf = g_sm + ((s - s0) % kGStages) * kGStageBytes;
@@ -191,13 +210,9 @@ __global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict
         const int row = t >> 5, q = t & 31, c = c0 + 4 * q;
         if (c < dout) cp_async16(buf + (row * kGCols + 4 * q) * 4, V + (vb + row) * dout + c);
       }
-      for (int t = tid; t < nps * 96; t += kGT) {  // per shape: 32 pieces of argmax, 64 of weight
-        const int ps = t / 96, q = t - ps * 96;
-        const int64_t e = (int64_t)(p0 + ps) * ldq + i0;
-        if (q < 32)
-          cp_async16(buf + kGAmOff + (ps * kGRows + 8 * q) * 2, amT + e + 8 * q);
-        else
-          cp_async16(buf + kGWOff + (ps * kGRows + 4 * (q - 32)) * 4, wU + e + 4 * (q - 32));
+      for (int t = tid; t < nps * 128; t += kGT) {  // per shape: 256 records, 128 pieces
+        const int ps = t >> 7, q = t & 127;
+        cp_async16(buf + kGRecOff + ps * (kGRows * 8) + 16 * q, gR + (int64_t)(p0 + ps) * ldq + i0 + 2 * q);
       }
     }
     cp_async_commit();  // empty groups past the last step keep the wait count uniform
@@ -214,36 +229,28 @@ __global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict
     __syncthreads();                // ... for every thread, and the step before is done with its buffer
     issue(s + kGStages - 1);
     const uint8_t* buf = g_sm + ((s - s0) % kGStages) * kGStageBytes;
-    const float4* vs = reinterpret_cast<const float4*>(buf);
+    const float4* vs = reinterpret_cast<const float4*>(buf) + lane;
     int p0, nps, nvs;
     int64_t vb;
     g_step(st, s, nv, Np, p0, nps, vb, nvs);
     for (int ps = 0; ps < nps; ++ps) {
-      // the warp's 16 argmax values and weights (broadcast reads)
-      const uint4* ap = reinterpret_cast<const uint4*>(buf + kGAmOff + (ps * kGRows + 16 * w) * 2);
-      const float4* wp = reinterpret_cast<const float4*>(buf + kGWOff + (ps * kGRows + 16 * w) * 4);
-      const uint4 a0 = ap[0], a1 = ap[1];
-      const uint32_t au[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float wt[16];
+      // the warp's 16 records, two per 16-byte broadcast read
+      const float4* rp = reinterpret_cast<const float4*>(buf + kGRecOff + (ps * kGRows + 16 * w) * 8);
+      if (st.spc > 0) {  // the record holds the staged row: no test
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 f = wp[q];
-        wt[4 * q] = f.x;
-        wt[4 * q + 1] = f.y;
-        wt[4 * q + 2] = f.z;
-        wt[4 * q + 3] = f.w;
-      }
-      const int base = (int)((int64_t)(p0 + ps) * nv - vb);  // staged row of view 0 of the shape
+        for (int q = 0; q < 8; ++q) {
+          const float4 r = rp[q];
+          g_add(acc[2 * q], r.x, vs[__float_as_int(r.y)]);
+          g_add(acc[2 * q + 1], r.z, vs[__float_as_int(r.w)]);
+        }
+      } else {  // 64-view piece of a shape: the argmax view must fall inside it
+        const int base = (int)((int64_t)p0 * nv - vb);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int j = (int)(int16_t)((k & 1) ? (au[k >> 1] >> 16) : (au[k >> 1] & 0xffffu));
-        const int loc = base + j;
-        if (j >= 0 && (unsigned)loc < (unsigned)nvs) {  // uniform over the warp
-          const float4 x = vs[loc * 32 + lane];
-          acc[k][0] = fmaf(wt[k], x.x, acc[k][0]);
-          acc[k][1] = fmaf(wt[k], x.y, acc[k][1]);
-          acc[k][2] = fmaf(wt[k], x.z, acc[k][2]);
-          acc[k][3] = fmaf(wt[k], x.w, acc[k][3]);
+        for (int q = 0; q < 8; ++q) {
+          const float4 r = rp[q];
+          const int l0 = base + __float_as_int(r.y), l1 = base + __float_as_int(r.w);
+          if ((unsigned)l0 < (unsigned)nvs) g_add(acc[2 * q], r.x, vs[l0 * 32]);
+          if ((unsigned)l1 < (unsigned)nvs) g_add(acc[2 * q + 1], r.z, vs[l1 * 32]);
         }
       }
     }
@@ -261,13 +268,13 @@ __global__ __launch_bounds__(kGT, 1) void k_gather_views(const float* __restrict
 }
 
 // shape-major argmax and one-hot weights, rows padded to ldq: for every (query view i,
-// shape p), j = argmax[i, p], wU = c / |v_{p nv + j}|, wV = c / |u_i| with
-// c = grad_S[b, p] / |V(x_b)|; j = -1 (no entry, zero weights) for an argmax outside
-// [0, N_v) and for the padding views nq <= i < ldq
-__global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, int64_t ldq, int Np, int nv,
+// shape p), j = argmax[i, p], the gather record of wU = c / |v_{p nv + j}| (g_record)
+// and wV = c / |u_i|, with c = grad_S[b, p] / |V(x_b)|; j = -1 (no entry, zero
+// weights) for an argmax outside [0, N_v) and for the padding views nq <= i < ldq
+__global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, int64_t ldq, int Np, int nv, int spc,
                               const int32_t* __restrict__ vquery, const float* __restrict__ vcoef,
                               const float* __restrict__ gS, const float* __restrict__ vinv,
-                              const float* __restrict__ uinv, int16_t* __restrict__ amT, float* __restrict__ wU,
+                              const float* __restrict__ uinv, int16_t* __restrict__ amT, float2* __restrict__ gR,
                               float* __restrict__ wV) {
   __shared__ int16_t t[32][33];
   const int64_t p0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
@@ -283,13 +290,13 @@ __global__ void k_onehot_prep(const int16_t* __restrict__ argmax, int64_t nq, in
     const int64_t e = p * ldq + i;
     if (j < 0 || j >= nv) {
       amT[e] = -1;
-      wU[e] = 0.f;
+      gR[e] = g_record(spc, p, nv, -1, 0.f);
       wV[e] = 0.f;
       continue;
     }
     const float c = gS[(int64_t)vquery[i] * Np + p] * vcoef[i];
     amT[e] = (int16_t)j;
-    wU[e] = c * vinv[p * nv + j];
+    gR[e] = g_record(spc, p, nv, j, c * vinv[p * nv + j]);
     wV[e] = c * uinv[i];
   }
 }
@@ -724,13 +731,25 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   float* vcoef = sc.get<float>(nq);
   k_view_coef<<<(unsigned)cdiv(nq, 256), 256, 0, s>>>(vquery, d_qoff, nq, vcoef);
   GIFT_LAUNCHED("k_view_coef");
-  // shape-major argmax and weights, query views padded to a multiple of the gather blocks
+  // steps of the query-side gather
+  GatherSteps st;
+  if (nv <= kGViews) {
+    st.spc = std::min(kGShapes, kGViews / nv);
+    st.nch = 1;
+    st.n = (int)cdiv((int64_t)Np, (int64_t)st.spc);
+  } else {
+    st.spc = 0;
+    st.nch = (int)cdiv((int64_t)nv, (int64_t)kGViews);
+    GIFT_REQUIRE((int64_t)Np * st.nch < INT32_MAX, "too many database views for the gradient");
+    st.n = Np * st.nch;
+  }
+  // shape-major argmax, gather records and weights, query views padded to a multiple of the gather blocks
   const int64_t ldq = cdiv(nq, (int64_t)kGRows) * kGRows;
   int16_t* amT = sc.get<int16_t>((size_t)ldq * Np);
-  float* wU = sc.get<float>((size_t)ldq * Np);
+  float2* gR = sc.get<float2>((size_t)ldq * Np);
   float* wV = sc.get<float>((size_t)ldq * Np);
   k_onehot_prep<<<dim3((unsigned)cdiv(Np, 32), (unsigned)cdiv(ldq, 32)), dim3(32, 8), 0, s>>>(
-      argmax, nq, ldq, Np, nv, vquery, vcoef, gS, P.vinv, P.uinv, amT, wU, wV);
+      argmax, nq, ldq, Np, nv, st.spc, vquery, vcoef, gS, P.vinv, P.uinv, amT, gR, wV);
   GIFT_LAUNCHED("k_onehot_prep");
   GIFT_REQUIRE(dout % 4 == 0, "projected width must be a multiple of 4");
   // the staged copies read 16-byte pieces of the rows of U and V
@@ -744,17 +763,6 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
   const float* V16 = aligned16(P.V, nr * dout);
   const int sms = device_sm_count();
   {  // G = A V, then dU
-    GatherSteps st;
-    if (nv <= kGViews) {
-      st.spc = std::min(kGShapes, kGViews / nv);
-      st.nch = 1;
-      st.n = (int)cdiv((int64_t)Np, (int64_t)st.spc);
-    } else {
-      st.spc = 0;
-      st.nch = (int)cdiv((int64_t)nv, (int64_t)kGViews);
-      GIFT_REQUIRE((int64_t)Np * st.nch < INT32_MAX, "too many database views for the gradient");
-      st.n = Np * st.nch;
-    }
     // parts of the step range: a block's time is ~ steps / parts, the launch takes
     // ceil(blocks x parts / SMs) rounds of one block per SM; partial rows cost a little
     const int64_t units = cdiv(nq, (int64_t)kGRows) * cdiv((int64_t)dout, (int64_t)kGCols);
@@ -772,7 +780,7 @@ void match_backward(const void* q, const std::vector<int32_t>& h_qoff, int32_t B
     GIFT_CUDA(cudaFuncSetAttribute(k_gather_views, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const dim3 grid((unsigned)cdiv(nq, (int64_t)kGRows), (unsigned)cdiv((int64_t)dout, (int64_t)kGCols),
                     (unsigned)parts);
-    k_gather_views<<<grid, kGT, smem, s>>>(V16, amT, wU, nq, ldq, Np, nv, dout, st, Gp);
+    k_gather_views<<<grid, kGT, smem, s>>>(V16, gR, nq, ldq, Np, nv, dout, st, Gp);
     GIFT_LAUNCHED("k_gather_views");
     k_tangent<<<(unsigned)cdiv(nq, 8), 256, 0, s>>>(P.U, P.uinv, Gp, parts, nq * dout, nq, dout, dU);
     GIFT_LAUNCHED("k_tangent");
