@@ -1054,7 +1054,8 @@ def bench_differentiation(gift, torch, dev, stream, reps=3, n_shapes=None, n_que
            "useful_tflop_fwd": (proj + sim) / 1e12, "useful_tflop_bwd": (proj + 2 * proj) / 1e12,
            "fwd_useful_tflops": (proj + sim) / (f_ms / 1e3) / 1e12,
            "bwd_useful_tflops": 3 * proj / (b_ms / 1e3) / 1e12,
-           "note": "similarity and gradient GEMMs run two-part BF16 (3 products); projections of BF16 inputs 1 product"}
+           "note": "similarity and dW/dQ/dP GEMMs run two-part BF16 (3 products); projections of BF16 inputs 1 product; "
+                    "the one-hot gradient products are FP32 gathers on the CUDA cores"}
     del q, p, W, G, S, am
     torch.cuda.empty_cache()
     return out
